@@ -1,0 +1,331 @@
+"""Benchmark: C = A*A over (+,x) in FP32 on an R-MAT scale-20 graph (edge factor 8,
+a=.57 b=c=.19 d=.05, duplicates merged, random symmetric relabelling), the
+SpGEMM hot path on one GB300.
+
+One step is one hs_spgemm call (flop count, binning, symbolic pass, scan,
+numeric pass; both host synchronisations included) with A resident in HBM.
+The metric is nonzero multiplications per second (flops counted as
+multiplications, sum over A(i,k) of nnz(B(k,:))); the roofline object reports
+the dominant kernel against the measured HBM copy bandwidth.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle
+(plain C Gustavson with a dense accumulator, all host cores) on a bounded
+sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "rmat20_ef8_AxA_plus_times_f32"
+METRIC = "nonzero_mults_per_s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target length of the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def make_input(scale):
+    from paper_1109_3739_gb300 import inputs as I
+    return I.rmat_matrix(scale, 8, 0.57, 0.19, 0.19, seed=2, dtype="f32")
+
+
+def row_flops(A):
+    deg = np.diff(A.rowptr)
+    rows = np.repeat(np.arange(A.m), deg)
+    f = np.zeros(A.m, np.int64)
+    np.add.at(f, rows, deg[A.col])
+    return f
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- CPU oracle
+def oracle_sample(A, f, seconds, nthreads):
+    """Time the oracle on rows [0, R) of the same product, R grown until the
+    sample takes about `seconds`; returns (mults/s, description, R)."""
+    import oracle
+    R = max(1, A.m // 256)
+    while True:
+        t0 = time.perf_counter()
+        oracle.spgemm("plus_times", A, A, r0=0, r1=R, nthreads=nthreads)
+        dt = time.perf_counter() - t0
+        mults = int(f[:R].sum())
+        if dt >= seconds * 0.5 or R >= A.m:
+            return mults / dt, f"rows 0..{R} of {A.m} ({mults} mults, {dt:.2f} s)", R
+        R = min(A.m, int(R * min(8.0, max(1.5, seconds / max(dt, 1e-3)))))
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    A = make_input(args.scale)
+    f = row_flops(A)
+    cores = os.cpu_count() or 1
+    per_step = max(2.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    rate, desc, R = oracle_sample(A, f, per_step, cores)
+    import oracle
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.spgemm("plus_times", A, A, r0=0, r1=R, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    mults = int(f[:R].sum())
+    value = mults * len(times) / sum(times)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "mults/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": desc},
+        "cpu_baseline": {"value": value, "unit": "mults/s", "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "mults/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ----------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    from paper_1109_3739_gb300 import hspgemm as h
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    A = make_input(args.scale)
+    f = row_flops(A)
+    flops = int(f.sum())
+    dA = h.DeviceCSR.from_host(A, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        return h.spgemm("plus_times", dA, dA, stream=stream)
+
+    C = None
+    for _ in range(args.warmup):
+        C = None
+        C = step()
+    torch.cuda.synchronize(dev)
+    nnz_c = C.nnz
+    c_rowptr = C.rowptr.cpu().numpy()
+    C = None
+
+    if dist:
+        dist.barrier()
+    h.profile_enable(True)
+    h.profile_reset()
+    l0 = h.launch_count()
+    times = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize(dev)
+        for _ in range(args.steps):
+            flush.fill_(1)  # evict L2 between steps (outside the timed events)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            C = step()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            C = None
+        torch.cuda.synchronize(dev)
+    launches = h.launch_count() - l0
+    prof = h.profile_read()
+    h.profile_enable(False)
+    total_ms = sum(times)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    value = flops * args.steps * world / (total_ms / 1000.0)
+
+    # ---- roofline of the dominant kernel (largest total time among the library's kernel phases)
+    hbm, peak_kind = peaks()
+    kernel_phases = {k: v for k, v in prof.items() if k.startswith(("numeric_", "symbolic_"))}
+    dom = max(kernel_phases, key=lambda k: kernel_phases[k][0])
+    dom_ms = kernel_phases[dom][0] / max(1, kernel_phases[dom][1])
+    # algorithmic bytes of one launch of the dominant kernel: the rows of its bin
+    # read their A entries (col + val) and row offsets once, the B rows they use
+    # once (bounded here by all of B), and write their C rows (col + val) and
+    # offsets once
+    cnt = np.diff(c_rowptr)
+    deg = np.diff(A.rowptr)
+    cap_large = 8192
+    in_bin = {
+        "numeric_heavy": (f > 512) & (cnt > cap_large),
+        "numeric_large": (f > 512) & (cnt > 2048) & (cnt <= cap_large),
+        "numeric_mid": (f > 512) & (cnt > 0) & (cnt <= 2048),
+        "numeric_warp": (f > 32) & (f <= 512),
+        "numeric_tiny": (f > 0) & (f <= 32),
+        "symbolic_heavy": f > 16384,
+        "symbolic_large": (f > 4096) & (f <= 16384),
+        "symbolic_mid": (f > 512) & (f <= 4096),
+        "symbolic_warp": (f > 32) & (f <= 512),
+        "symbolic_tiny": (f > 0) & (f <= 32),
+    }[dom]
+    vb = 4
+    b_bytes = (A.m + 1) * 8 + A.nnz * (4 + vb)
+    a_bytes = int(in_bin.sum()) * 8 + int(deg[in_bin].sum()) * (4 + vb)
+    if dom.startswith("numeric"):
+        c_bytes = int(in_bin.sum()) * 8 + int(cnt[in_bin].sum()) * (4 + vb)
+    else:
+        c_bytes = int(in_bin.sum()) * 8  # the symbolic pass writes one count per row
+    alg_bytes = a_bytes + b_bytes + c_bytes
+    achieved = alg_bytes / (dom_ms / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                "alg_bytes_per_launch": alg_bytes, "ms_per_launch": dom_ms}
+    # whole-product algorithmic bytes (read A and B once, write C once)
+    step_bytes = 2 * ((A.m + 1) * 8 + A.nnz * (4 + vb)) + (A.m + 1) * 8 + nnz_c * (4 + vb)
+    step_ms = total_ms / args.steps
+
+    # ---- end to end: pinned host A -> device, product, C -> pinned host
+    e2e = None
+    if args.e2e_steps > 0 and rank == 0:
+        hA = [torch.from_numpy(np.asarray(x)).pin_memory() for x in (A.rowptr, A.col, A.val)]
+        h2d = sum(t.numel() * t.element_size() for t in hA)
+        out_rp = torch.empty(A.m + 1, dtype=torch.int64, pin_memory=True)
+        out_j = torch.empty(nnz_c, dtype=torch.int32, pin_memory=True)
+        out_v = torch.empty(nnz_c, dtype=torch.float32, pin_memory=True)
+        d2h = out_rp.numel() * 8 + nnz_c * 8
+        etimes = []
+        for i in range(args.e2e_steps + 1):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            rp, cj, cv = (t.to(dev, non_blocking=True) for t in hA)
+            M = h.DeviceCSR(A.m, A.n, rp, cj, cv, "f32")
+            Cd = h.spgemm("plus_times", M, M, stream=stream)
+            out_rp.copy_(Cd.rowptr, non_blocking=True)
+            out_j.copy_(Cd.col, non_blocking=True)
+            out_v.copy_(Cd.val, non_blocking=True)
+            torch.cuda.synchronize(dev)
+            dt = time.perf_counter() - t0
+            Cd = M = None
+            if i > 0:
+                etimes.append(dt)
+        e2e = {"value": flops / statistics.median(etimes), "unit": "mults/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": 1000 * statistics.median(etimes)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        rate, desc, _ = oracle_sample(A, f, args.cpu_seconds, cores)
+        cpu = {"value": rate, "unit": "mults/s", "cores": cores, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "mults/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "scale": args.scale, "edge_factor": 8,
+                       "rmat": [0.57, 0.19, 0.19, 0.05], "flops_mults": flops, "nnz_A": A.nnz,
+                       "nnz_C": nnz_c, "l2": "flushed between steps (512 MB write)",
+                       "step_hbm_fraction": step_bytes / (step_ms / 1000.0) / 1e9 / hbm,
+                       "step_alg_bytes": step_bytes},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+            "gpu_launches": launches,
+            "phases_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        }), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,172 @@
+/*
+ * hspgemm.h -- C ABI of libhspgemm: sparse matrix-matrix multiplication over a
+ * semiring (SpGEMM), sparse indexing (SpRef) and sparse assignment (SpAsgn)
+ * on one NVIDIA GB300 GPU.
+ *
+ * The operations are those of Buluc & Gilbert, "Parallel Sparse Matrix-Matrix
+ * Multiplication and Indexing: Implementation and Experiments" (SIAM J. Sci.
+ * Comput. 2012):
+ *   - SpGEMM C = A*B over a semiring (Section 1; Algorithm 1; Section 2.1),
+ *   - SpRef  B = A(I,J) computed as the triple product R*A*Q with 0/1
+ *     selection matrices (Section 3.1, SpRef listing and Figure "spref"),
+ *   - SpAsgn A(I,J) = B computed as A + R*B*Q - S*A*T, the subtraction being
+ *     an elementwise product with the structural negation of S*A*T
+ *     (Section 3.1, SpAsgn listing and the theorem after it),
+ *   - Liu's extend-add A(I,J) = A(I,J) + B (Section 3).
+ *
+ * Conventions shared by every entry point
+ *   - Indices are 0-based (the paper is 1-based).  Column ids are int32, row
+ *     offsets int64, so nnz may exceed 2^31.
+ *   - Matrices are canonical: within a row, column ids strictly increase.
+ *     Outputs are always canonical.  Inputs are checked only when
+ *     HS_FLAG_VALIDATE is passed (then a violation returns HS_ENONCANON).
+ *   - All matrix arrays are DEVICE pointers on the current CUDA device.  The
+ *     library never modifies its inputs.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is stream ordered.  Each product performs two small
+ *     device->host reads of sizes and therefore two host synchronisations
+ *     with `stream` (after binning and after the symbolic pass).
+ *   - Outputs and temporaries are allocated through `alloc` (see
+ *     hs_allocator); with alloc == NULL the library uses cudaMallocAsync /
+ *     cudaFreeAsync on `stream`.  Output arrays are owned by the caller and
+ *     released with hs_mat_free (or by the caller's own allocator).
+ *   - Every call returns HS_OK (0) or a negative status; on failure no output
+ *     memory is left allocated.
+ */
+#ifndef HSPGEMM_H
+#define HSPGEMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Semirings (Section 1, "SpGEMM ... over a general semiring"; Section 3.1:
+ * SpRef/SpAsgn use "mixed-mode SpGEMM between a boolean matrix and a
+ * general-type matrix", here the two selector semirings). */
+typedef enum {
+  HS_PLUS_TIMES = 0, /* (+, x): F64, F32, I64                                  */
+  HS_OR_AND = 1,     /* (or, and): structure only; output dtype HS_BOOL         */
+  HS_MIN_PLUS = 2,   /* (min, +): F32, I32                                      */
+  HS_SELECT2ND = 3,  /* mul(a,b) = b: A is a 0/1 selector (any dtype, values
+                        ignored); every output entry must receive exactly one
+                        contribution, else which one is kept is unspecified   */
+  HS_SELECT1ST = 4   /* mul(a,b) = a: B is the selector; same rule            */
+} hs_semiring;
+
+/* Value types; HS_BOOL matrices carry no value array (val == NULL). */
+typedef enum { HS_F64 = 0, HS_F32 = 1, HS_I32 = 2, HS_I64 = 3, HS_BOOL = 4 } hs_dtype;
+
+/* Storage formats (Section 2.2).  HS_DCSR is the row analogue of DCSC: only
+ * non-empty rows are stored; ids[r] is the id of the r-th stored row and
+ * ptr has nzr+1 entries.  Accepted for the left operand A of hs_spgemm; all
+ * other operands and every output are HS_CSR. */
+typedef enum { HS_CSR = 0, HS_DCSR = 1 } hs_format;
+
+typedef struct hs_mat {
+  int32_t fmt;   /* hs_format                                           */
+  int32_t dtype; /* hs_dtype                                            */
+  int64_t m, n;  /* shape                                               */
+  int64_t nnz;   /* stored entries (== ptr[rows])                       */
+  int64_t nzr;   /* HS_DCSR: number of stored rows; ignored for HS_CSR  */
+  int64_t *ptr;  /* row offsets: m+1 (CSR) or nzr+1 (DCSR), int64       */
+  int32_t *idx;  /* column ids, nnz                                     */
+  int32_t *ids;  /* HS_DCSR: stored row ids, nzr, increasing; else NULL */
+  void *val;     /* values, nnz * sizeof(dtype); NULL for HS_BOOL       */
+} hs_mat;
+
+/* Stream-ordered device allocator.  alloc returns device memory usable on
+ * `stream` (NULL on failure -> HS_ENOMEM); free releases it on `stream`. */
+typedef struct hs_allocator {
+  void *(*alloc)(size_t bytes, void *stream, void *ctx);
+  void (*free)(void *ptr, size_t bytes, void *stream, void *ctx);
+  void *ctx;
+} hs_allocator;
+
+/* Status codes. */
+#define HS_OK 0
+#define HS_EINVAL -1       /* bad shape, dtype/semiring pair, pointer or index */
+#define HS_ENONCANON -2    /* input row not strictly increasing (validation)   */
+#define HS_EDUP -3         /* duplicate index in SpAsgn I or J                 */
+#define HS_ENOMEM -4       /* allocator returned NULL                          */
+#define HS_ETIMEDOUT -5    /* a bounded device-side wait expired               */
+#define HS_ECUDA -6        /* CUDA runtime error (see hs_last_cuda_error)      */
+#define HS_EUNSUPPORTED -7 /* valid request this build does not implement    */
+#define HS_EINTERNAL -8    /* device-side consistency check failed            */
+
+/* Flags. */
+#define HS_FLAG_VALIDATE 1u /* check canonical inputs and index ranges */
+
+/* C = A*B over `semiring` (Section 1; Algorithm 1 and Section 2.1).
+ * A: m x k, CSR or DCSR.  B: k x n, CSR.  C: m x n CSR, filled in by the
+ * call (C->ptr, C->idx, C->val allocated through `al`).  For HS_PLUS_TIMES
+ * and HS_MIN_PLUS, A and B share one dtype, which C gets; HS_OR_AND gives
+ * an HS_BOOL C; HS_SELECT2ND gives B's dtype, HS_SELECT1ST A's.
+ * Floating-point sums are formed in the input precision, in an unspecified
+ * order.  Explicit entries are never dropped: C's structure is the symbolic
+ * product of A's and B's structures.  Errors: HS_EINVAL (shapes, dtypes,
+ * NULL pointers), HS_ENONCANON (with HS_FLAG_VALIDATE), HS_ENOMEM, HS_ECUDA,
+ * HS_EINTERNAL. */
+int hs_spgemm(int semiring, const hs_mat *A, const hs_mat *B, hs_mat *C,
+              const hs_allocator *al, void *stream, uint32_t flags);
+
+/* B = A(I,J) (Section 3; SpRef listing of Section 3.1): B is len(I) x len(J),
+ * row t of B is row I[t] of A and column p of B is column J[p] of A.  I and J
+ * are int32 device arrays, any order, duplicates allowed (they repeat
+ * rows/columns).  Computed as (R*A)*Q with R = sparse(1:len(I), I, 1) and
+ * Q = sparse(J, 1:len(J), 1) through hs_spgemm with the selector semirings,
+ * so values are copied bit for bit.  Errors: HS_EINVAL (index out of range
+ * with HS_FLAG_VALIDATE, bad shapes), HS_ENOMEM, HS_ECUDA. */
+int hs_spref(const hs_mat *A, const int32_t *I, int64_t nI, const int32_t *J, int64_t nJ,
+             hs_mat *B, const hs_allocator *al, void *stream, uint32_t flags);
+
+/* C = A with A(I,J) = B (accumulate == 0; SpAsgn listing of Section 3.1) or
+ * A(I,J) = A(I,J) + B (accumulate != 0; extend-add).  A: m x n CSR,
+ * B: len(I) x len(J) CSR of A's dtype.  I and J: int32 device arrays without
+ * duplicates (HS_EDUP otherwise).  Assignment removes every entry of A inside
+ * the I x J block (the structural negation of S*A*T) and inserts B's entries
+ * (R*B*Q); extend-add combines colliding entries with `add_semiring`'s add
+ * (HS_PLUS_TIMES or HS_MIN_PLUS; HS_OR_AND for HS_BOOL).  Values are copied
+ * bit for bit except where extend-add combines two.  Errors: HS_EINVAL,
+ * HS_EDUP, HS_ENOMEM, HS_ECUDA. */
+int hs_spasgn(const hs_mat *A, const int32_t *I, int64_t nI, const int32_t *J, int64_t nJ,
+              const hs_mat *B, int accumulate, int add_semiring, hs_mat *C,
+              const hs_allocator *al, void *stream, uint32_t flags);
+
+/* Releases the arrays of a matrix produced by this library through `al` (the
+ * allocator it was produced with) and zeroes the descriptor. */
+void hs_mat_free(hs_mat *M, const hs_allocator *al, void *stream);
+
+/* Human-readable name of a status code (static storage). */
+const char *hs_strerror(int status);
+
+/* The cudaError_t value behind the last HS_ECUDA on this host thread. */
+int hs_last_cuda_error(void);
+
+/* A one-line description of the last failure on this host thread (the phase
+ * and the CUDA error or failed check), or "" (static thread-local storage). */
+const char *hs_last_error_detail(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int hs_version(void);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * threads, all devices); differences around a region count its launches. */
+int64_t hs_launch_count(void);
+
+/* Phase timing.  With hs_profile_enable(1) every later call records CUDA
+ * events on its stream around each phase; hs_profile_read copies the
+ * accumulated milliseconds, launch counts and names of up to `cap` phases
+ * and returns the number of phases.  hs_profile_reset clears the totals.
+ * Intended for benchmarking; adds event records, no synchronisation beyond
+ * the product's own. */
+void hs_profile_enable(int on);
+void hs_profile_reset(void);
+int hs_profile_read(double *ms, int64_t *launches, const char **names, int cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HSPGEMM_H */

@@ -1,0 +1,286 @@
+// analysis.cu -- integer work ahead of the products: per-row flop counts,
+// binning of rows, prefix sums and input validation.
+//
+// flops(A*B) for row i is the number of nonzero multiplications of that row
+// (Section 2 notation): sum over stored A(i,k) of nnz(B(k,:)).  Rows with no
+// products are left out of every bin, so no later kernel does work for empty
+// rows: the dimension-independent work list of the doubly compressed format
+// (Section 2.2), built on the fly.
+#include "common.cuh"
+#include "internal.h"
+
+namespace hs {
+
+static int g_sms = 0;
+static unsigned long long g_launches = 0;
+void count_launch() { __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED); }
+unsigned long long launch_total() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+cudaError_t &attr_error() {
+  static thread_local cudaError_t e = cudaSuccess;
+  return e;
+}
+void launch_sm_count_init() {
+  if (g_sms) return;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (g_sms <= 0) g_sms = 1;
+}
+int sm_count() {
+  launch_sm_count_init();
+  return g_sms;
+}
+
+static int grid_for(int64_t items, int per_block, int max_per_sm) {
+  int64_t g = (items + per_block - 1) / per_block;
+  int64_t cap = (int64_t)sm_count() * max_per_sm;
+  if (g > cap) g = cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
+// ------------------------------------------------------------------ flops
+// stats[0] += total flops, stats[1] = max row flops, stats[2] = max row nnz of A
+__global__ void k_flops(RowSet A, RightOp B, int64_t *f, int *key_cnt, unsigned long long *stats) {
+  __shared__ int hist[NKEYS];
+  __shared__ unsigned long long blk_tot, blk_max, blk_amax;
+  for (int i = threadIdx.x; i < NKEYS; i += blockDim.x) hist[i] = 0;
+  if (threadIdx.x == 0) blk_tot = blk_max = blk_amax = 0;
+  __syncthreads();
+  const int lane = lane_id();
+  const int64_t wpb = blockDim.x >> 5;
+  unsigned long long my_tot = 0, my_max = 0, my_amax = 0;
+  for (int64_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < A.nslots; r += (int64_t)gridDim.x * wpb) {
+    const int64_t q0 = A.p[r], q1 = A.p[r + 1];
+    long long s = 0;
+    for (int64_t q = q0 + lane; q < q1; q += 32) {
+      if (!HS_G(A.dbg, q >= 0 && q < A.nnz, 50, q)) break;
+      const int k = A.j[q];
+      if (HS_G(A.dbg, k >= 0 && k < B.m, 51, k)) s += B.p[k + 1] - B.p[k];
+    }
+    s = warp_sum(s);
+    if (lane == 0) {
+      f[r] = s;
+      const int key = sym_key(s);
+      if (key) atomicAdd(hist + key, 1);
+      my_tot += (unsigned long long)s;
+      my_max = max(my_max, (unsigned long long)s);
+      my_amax = max(my_amax, (unsigned long long)(q1 - q0));
+    }
+  }
+  if (lane == 0) {
+    atomicAdd(&blk_tot, my_tot);
+    atomicMax(&blk_max, my_max);
+    atomicMax(&blk_amax, my_amax);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < NKEYS; i += blockDim.x)
+    if (hist[i]) atomicAdd(key_cnt + i, hist[i]);
+  if (threadIdx.x == 0) {
+    atomicAdd(stats + 0, blk_tot);
+    atomicMax(stats + 1, blk_max);
+    atomicMax(stats + 2, blk_amax);
+  }
+}
+
+void launch_flops(const RowSet &A, const RightOp &B, int64_t *f, int *key_cnt, unsigned long long *stats,
+                  cudaStream_t st) {
+  if (A.nslots == 0) return;
+  count_launch();
+  k_flops<<<grid_for(A.nslots, 8, 16), 256, 0, st>>>(A, B, f, key_cnt, stats);
+}
+
+// one warp: exclusive scan of the NKEYS counters into offsets and cursors
+__global__ void k_key_offsets(const int *cnt, int *off, int *cur) {
+  const int lane = lane_id();
+  const int a = cnt[2 * lane], b = cnt[2 * lane + 1];
+  const int incl = warp_incl_scan(a + b);
+  const int ex = incl - a - b;
+  off[2 * lane] = ex;
+  off[2 * lane + 1] = ex + a;
+  cur[2 * lane] = ex;
+  cur[2 * lane + 1] = ex + a;
+  if (lane == 31) off[NKEYS] = incl;
+}
+static_assert(NKEYS == 64, "k_key_offsets assumes 64 keys");
+
+void launch_key_offsets(const int *key_cnt, int *key_off, int *key_cur, cudaStream_t st) {
+  count_launch();
+  k_key_offsets<<<1, 32, 0, st>>>(key_cnt, key_off, key_cur);
+}
+
+// append row r to the list of its key; lanes with equal keys share one atomic
+__device__ __forceinline__ void append_row(int key, int r, int *key_cur, int *list, int64_t cap, long long *dbg) {
+  const unsigned act = __activemask();
+  const unsigned grp = __match_any_sync(act, key);
+  const int leader = __ffs(grp) - 1;
+  int base = 0;
+  if (lane_id() == leader) base = atomicAdd(key_cur + key, __popc(grp));
+  base = __shfl_sync(grp, base, leader);
+  const int64_t at = base + __popc(grp & ((1u << lane_id()) - 1));
+  if (HS_G(dbg, at >= 0 && at < cap, 52, at)) list[at] = r;
+}
+
+__global__ void k_scatter_sym(RowSet A, const int64_t *f, int *key_cur, int *list, int32_t *hslot, int *nhist) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < A.nslots;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t fr = f[r];
+    const int key = sym_key(fr);
+    if (key) append_row(key, (int)r, key_cur, list, A.nslots, A.dbg);
+    // rows that may need column parts in the numeric pass get a histogram slot
+    const bool h = fr > SEG_W;
+    const unsigned act = __activemask();
+    const unsigned hm = __ballot_sync(act, h);
+    int base = 0;
+    const int leader = __ffs(act) - 1;
+    if (lane_id() == leader && hm) base = atomicAdd(nhist, __popc(hm));
+    base = __shfl_sync(act, base, leader);
+    hslot[r] = h ? base + __popc(hm & ((1u << lane_id()) - 1)) : -1;
+  }
+}
+
+void launch_scatter_sym(const RowSet &A, const int64_t *f, int *key_cur, int *list, int32_t *hslot, int *nhist,
+                        cudaStream_t st) {
+  if (A.nslots == 0) return;
+  count_launch();
+  k_scatter_sym<<<grid_for(A.nslots, 256, 8), 256, 0, st>>>(A, f, key_cur, list, hslot, nhist);
+}
+
+__device__ __forceinline__ int64_t out_count(const RowSet &A, const int64_t *Cp, int64_t r) {
+  const int64_t o = A.ids ? A.ids[r] : r;
+  return Cp[o + 1] - Cp[o];
+}
+
+__global__ void k_num_count(RowSet A, const int64_t *f, const int64_t *Cp, int cap_large, int *key_cnt) {
+  __shared__ int hist[NKEYS];
+  for (int i = threadIdx.x; i < NKEYS; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < A.nslots;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int key = num_key(f[r], out_count(A, Cp, r), cap_large);
+    if (key) atomicAdd(hist + key, 1);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < NKEYS; i += blockDim.x)
+    if (hist[i]) atomicAdd(key_cnt + i, hist[i]);
+}
+
+void launch_num_count(const RowSet &A, const int64_t *f, const int64_t *Cp, int cap_large, int *key_cnt,
+                      cudaStream_t st) {
+  if (A.nslots == 0) return;
+  count_launch();
+  k_num_count<<<grid_for(A.nslots, 256, 8), 256, 0, st>>>(A, f, Cp, cap_large, key_cnt);
+}
+
+__global__ void k_scatter_num(RowSet A, const int64_t *f, const int64_t *Cp, int cap_large, int *key_cur,
+                              int *list) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < A.nslots;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int key = num_key(f[r], out_count(A, Cp, r), cap_large);
+    if (key) append_row(key, (int)r, key_cur, list, A.nslots, A.dbg);
+  }
+}
+
+void launch_scatter_num(const RowSet &A, const int64_t *f, const int64_t *Cp, int cap_large, int *key_cur,
+                        int *list, cudaStream_t st) {
+  if (A.nslots == 0) return;
+  count_launch();
+  k_scatter_num<<<grid_for(A.nslots, 256, 8), 256, 0, st>>>(A, f, Cp, cap_large, key_cur, list);
+}
+
+// ------------------------------------------------------------------- scan
+// Inclusive prefix sum of an int64 array, in place: tiles of SCAN_TILE
+// elements are scanned by one CTA each; the tile totals are scanned
+// recursively and added back.
+constexpr int SCAN_NT = 256, SCAN_PER = 8, SCAN_TILE = SCAN_NT * SCAN_PER;
+
+__global__ void k_scan_tiles(int64_t *a, int64_t n, int64_t *tot) {
+  __shared__ long long wsum[SCAN_NT / 32 + 1];
+  const int64_t base = blockIdx.x * (int64_t)SCAN_TILE + threadIdx.x * SCAN_PER;
+  long long v[SCAN_PER];
+  long long s = 0;
+#pragma unroll
+  for (int i = 0; i < SCAN_PER; ++i) {
+    v[i] = (base + i < n) ? a[base + i] : 0;
+    s += v[i];
+  }
+  long long incl = warp_incl_scan(s);
+  if (lane_id() == 31) wsum[threadIdx.x >> 5] = incl;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    long long w = threadIdx.x < SCAN_NT / 32 ? wsum[threadIdx.x] : 0;
+    long long wi = warp_incl_scan(w);
+    if (threadIdx.x < SCAN_NT / 32) wsum[threadIdx.x] = wi - w;
+    if (threadIdx.x == 31) wsum[SCAN_NT / 32] = wi;
+  }
+  __syncthreads();
+  long long run = incl - s + wsum[threadIdx.x >> 5];
+#pragma unroll
+  for (int i = 0; i < SCAN_PER; ++i) {
+    run += v[i];
+    if (base + i < n) a[base + i] = run;
+  }
+  if (threadIdx.x == 0 && tot) tot[blockIdx.x] = wsum[SCAN_NT / 32];
+}
+
+__global__ void k_scan_add(int64_t *a, int64_t n, const int64_t *tot) {
+  if (blockIdx.x == 0) return;
+  const int64_t add = tot[blockIdx.x - 1];
+  const int64_t base = blockIdx.x * (int64_t)SCAN_TILE;
+  for (int i = threadIdx.x; i < SCAN_TILE; i += blockDim.x)
+    if (base + i < n) a[base + i] += add;
+}
+
+int64_t scan_tmp_elems(int64_t n) {
+  int64_t t = 0;
+  while (n > SCAN_TILE) {
+    n = (n + SCAN_TILE - 1) / SCAN_TILE;
+    t += n;
+  }
+  return t + 1;
+}
+
+void launch_scan_i64(int64_t *a, int64_t n, int64_t *tmp, cudaStream_t st) {
+  if (n <= 0) return;
+  const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (tiles == 1) {
+    count_launch();
+    k_scan_tiles<<<1, SCAN_NT, 0, st>>>(a, n, nullptr);
+    return;
+  }
+  count_launch();
+  k_scan_tiles<<<(unsigned)tiles, SCAN_NT, 0, st>>>(a, n, tmp);
+  launch_scan_i64(tmp, tiles, tmp + tiles, st);
+  count_launch();
+  k_scan_add<<<(unsigned)tiles, SCAN_NT, 0, st>>>(a, n, tmp);
+}
+
+// -------------------------------------------------------------- validation
+// flag bit 1: a column id outside [0, ncols); bit 2: a row not strictly
+// increasing; bit 4: row offsets decreasing.
+__global__ void k_validate(const int64_t *p, const int32_t *j, int64_t rows, int64_t ncols, int *flag) {
+  const int lane = lane_id();
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < rows; r += (int64_t)gridDim.x * wpb) {
+    const int64_t q0 = p[r], q1 = p[r + 1];
+    if (q1 < q0) {
+      if (lane == 0) atomicOr(flag, 4);
+      continue;
+    }
+    int bad = 0;
+    for (int64_t q = q0 + lane; q < q1; q += 32) {
+      const int c = j[q];
+      if (c < 0 || c >= ncols) bad |= 1;
+      if (q > q0 && j[q - 1] >= c) bad |= 2;
+    }
+    bad = __reduce_or_sync(FULL, bad);
+    if (lane == 0 && bad) atomicOr(flag, bad);
+  }
+}
+
+void launch_validate(const int64_t *p, const int32_t *j, int64_t rows, int64_t ncols, int *flag, cudaStream_t st) {
+  if (rows <= 0) return;
+  count_launch();
+  k_validate<<<grid_for(rows, 8, 16), 256, 0, st>>>(p, j, rows, ncols, flag);
+}
+
+}  // namespace hs

@@ -1,0 +1,274 @@
+// index.cu -- device pieces of SpRef and SpAsgn (Section 3.1).
+//
+// The selection matrices of the SpRef and SpAsgn listings are built on the
+// device in CSR form (the constructor sparse(i, j, 1, m, n) for their
+// special shapes):
+//   SpRef  R = sparse(1:len(I), I, 1, len(I), m)  -> row t holds column I[t]
+//          Q = sparse(J, 1:len(J), 1, n, len(J))  -> row k holds every p with
+//                                                    J[p] == k, increasing
+//   SpAsgn R = sparse(I, 1:mb, 1, ma, mb)         -> row I[q] holds column q
+//          Q = sparse(1:nb, J, 1, nb, na)         -> row q holds column J[q]
+// and the final step of SpAsgn, the elementwise product of A with the
+// structural negation of S*A*T plus R*B*Q: an entry (r, c) of A is in the
+// structure of S*A*T exactly when r is in I and c is in J, so the negation is
+// applied through the inverse index maps rpos/cpos without forming S*A*T
+// ("without explicitly forming the negated matrix", Section 3.1).
+#include "common.cuh"
+#include "internal.h"
+
+namespace hs {
+
+static int grid1(int64_t n, int nt = 256) {
+  int64_t g = (n + nt - 1) / nt;
+  int64_t cap = (int64_t)sm_count() * 16;
+  if (g > cap) g = cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
+#define GRID_STRIDE(i, n) \
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+__global__ void k_iota_i64(int64_t *p, int64_t n) { GRID_STRIDE(i, n) p[i] = i; }
+
+__global__ void k_fill_i32(int32_t *a, int64_t n, int32_t v) { GRID_STRIDE(i, n) a[i] = v; }
+void launch_fill_i32(int32_t *a, int64_t n, int32_t v, cudaStream_t st) {
+  if (n > 0) {
+    count_launch();
+    k_fill_i32<<<grid1(n), 256, 0, st>>>(a, n, v);
+  }
+}
+
+// R of SpRef: offsets 0..nI (the column ids are I itself)
+void launch_build_R(const int32_t *, int64_t nI, int64_t *Rp, int32_t *, cudaStream_t st) {
+  count_launch();
+  k_iota_i64<<<grid1(nI + 1), 256, 0, st>>>(Rp, nI + 1);
+}
+
+// Q of SpRef: counts per row k go to Qp[k+1]
+__global__ void k_count_idx(const int32_t *X, int64_t n, int64_t *cnt) {
+  GRID_STRIDE(i, n) atomicAdd(reinterpret_cast<unsigned long long *>(cnt + X[i] + 1), 1ull);
+}
+void launch_build_Q_count(const int32_t *J, int64_t nJ, int64_t *Qp_counts, cudaStream_t st) {
+  if (nJ > 0) {
+    count_launch();
+    k_count_idx<<<grid1(nJ), 256, 0, st>>>(J, nJ, Qp_counts);
+  }
+}
+
+// Q of SpRef: cur holds the row offsets on entry and is advanced by atomics;
+// rows are then put in increasing order of p by an insertion sort (rows of Q
+// hold one entry per repetition of k in J, usually one)
+__global__ void k_fill_idx(const int32_t *X, int64_t n, int64_t *cur, int32_t *out) {
+  GRID_STRIDE(i, n) {
+    const unsigned long long at = atomicAdd(reinterpret_cast<unsigned long long *>(cur + X[i]), 1ull);
+    out[at] = (int32_t)i;
+  }
+}
+__global__ void k_sort_short_rows(const int64_t *ptr, int32_t *j, int64_t rows) {
+  GRID_STRIDE(r, rows) {
+    const int64_t b = ptr[r], e = ptr[r + 1];
+    for (int64_t x = b + 1; x < e; ++x) {
+      const int32_t v = j[x];
+      int64_t y = x - 1;
+      while (y >= b && j[y] > v) {
+        j[y + 1] = j[y];
+        --y;
+      }
+      j[y + 1] = v;
+    }
+  }
+}
+// Qcur: a copy of the finished offsets (length n+1); Qj is sorted per row
+// using the offsets that precede Qcur in the caller's layout (Qcur - (n+1))
+void launch_build_Q_fill(const int32_t *J, int64_t nJ, int64_t *Qcur, int32_t *Qj, cudaStream_t st) {
+  if (nJ > 0) {
+    count_launch();
+    k_fill_idx<<<grid1(nJ), 256, 0, st>>>(J, nJ, Qcur, Qj);
+  }
+}
+void launch_sort_short_rows(const int64_t *ptr, int32_t *j, int64_t rows, cudaStream_t st) {
+  if (rows > 0) {
+    count_launch();
+    k_sort_short_rows<<<grid1(rows), 256, 0, st>>>(ptr, j, rows);
+  }
+}
+
+// flag bit 1: an index outside [0, bound)
+__global__ void k_check_range(const int32_t *X, int64_t n, int64_t bound, int *flag) {
+  GRID_STRIDE(i, n) {
+    const int32_t v = X[i];
+    if (v < 0 || v >= bound) atomicOr(flag, 1);
+  }
+}
+void launch_check_range(const int32_t *X, int64_t n, int64_t bound, int *flag, cudaStream_t st) {
+  if (n > 0) {
+    count_launch();
+    k_check_range<<<grid1(n), 256, 0, st>>>(X, n, bound, flag);
+  }
+}
+
+// pos[X[i]] = i (pos pre-filled with -1) for indices inside [0, bound);
+// flag bit 1: an index out of range (skipped), bit 2: a repeated index.
+__global__ void k_mark_positions(const int32_t *X, int64_t n, int64_t bound, int32_t *pos, int *flag) {
+  GRID_STRIDE(i, n) {
+    const int32_t v = X[i];
+    if (v < 0 || v >= bound) {
+      atomicOr(flag, 1);
+      continue;
+    }
+    const int32_t old = atomicExch(pos + v, (int32_t)i);
+    if (old != -1) atomicOr(flag, 2);
+  }
+}
+void launch_mark_positions(const int32_t *X, int64_t n, int64_t bound, int32_t *pos, int *flag, cudaStream_t st) {
+  if (n > 0) {
+    count_launch();
+    k_mark_positions<<<grid1(n), 256, 0, st>>>(X, n, bound, pos, flag);
+  }
+}
+
+// SpAsgn R = sparse(I, 1:mb, 1, ma, mb) from rpos: counts, then entries
+__global__ void k_rows_from_pos(const int32_t *pos, int64_t m, int64_t *cnt) {
+  GRID_STRIDE(r, m) cnt[r + 1] = pos[r] >= 0 ? 1 : 0;
+}
+__global__ void k_fill_from_pos(const int32_t *pos, int64_t m, const int64_t *ptr, int32_t *out) {
+  GRID_STRIDE(r, m) if (pos[r] >= 0) out[ptr[r]] = pos[r];
+}
+void launch_rows_from_pos(const int32_t *pos, int64_t m, int64_t *cnt, cudaStream_t st) {
+  if (m > 0) {
+    count_launch();
+    k_rows_from_pos<<<grid1(m), 256, 0, st>>>(pos, m, cnt);
+  }
+}
+void launch_fill_from_pos(const int32_t *pos, int64_t m, const int64_t *ptr, int32_t *out, cudaStream_t st) {
+  if (m > 0) {
+    count_launch();
+    k_fill_from_pos<<<grid1(m), 256, 0, st>>>(pos, m, ptr, out);
+  }
+}
+void launch_iota_i64(int64_t *p, int64_t n, cudaStream_t st) {
+  if (n > 0) {
+    count_launch();
+    k_iota_i64<<<grid1(n), 256, 0, st>>>(p, n);
+  }
+}
+
+// ------------------------------------------------------------ SpAsgn merge
+__device__ __forceinline__ void copy_val(void *dst, int64_t di, const void *src, int64_t si, int vb) {
+  if (vb == 8) reinterpret_cast<unsigned long long *>(dst)[di] = reinterpret_cast<const unsigned long long *>(src)[si];
+  else if (vb == 4) reinterpret_cast<uint32_t *>(dst)[di] = reinterpret_cast<const uint32_t *>(src)[si];
+}
+
+// extend-add collision: x (from A) (+) y (from B) in the semiring's add
+__device__ void combine_val(const AsgnArgs &a, int64_t di, int64_t ai, int64_t xi) {
+  const bool mn = a.add_kind == MIN_PLUS;
+  switch (a.dtype) {
+    case 0: {
+      const double x = ((const double *)a.Av)[ai], y = ((const double *)a.Xv)[xi];
+      ((double *)a.Cv)[di] = mn ? (y < x ? y : x) : x + y;
+      break;
+    }
+    case 1: {
+      const float x = ((const float *)a.Av)[ai], y = ((const float *)a.Xv)[xi];
+      ((float *)a.Cv)[di] = mn ? (y < x ? y : x) : __fadd_rn(x, y);
+      break;
+    }
+    case 2: {
+      const int32_t x = ((const int32_t *)a.Av)[ai], y = ((const int32_t *)a.Xv)[xi];
+      ((int32_t *)a.Cv)[di] = mn ? (y < x ? y : x) : (int32_t)((uint32_t)x + (uint32_t)y);
+      break;
+    }
+    case 3: {
+      const int64_t x = ((const int64_t *)a.Av)[ai], y = ((const int64_t *)a.Xv)[xi];
+      ((int64_t *)a.Cv)[di] = mn ? (y < x ? y : x) : (int64_t)((unsigned long long)x + (unsigned long long)y);
+      break;
+    }
+    default: break;
+  }
+}
+
+// count: output entries of row r go to Cp[r+1]
+__global__ void k_asgn_count(AsgnArgs a) {
+  const int lane = lane_id();
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < a.m; r += (int64_t)gridDim.x * wpb) {
+    const int64_t a0 = a.Ap[r], a1 = a.Ap[r + 1];
+    const int64_t x0 = a.Xp[r], x1 = a.Xp[r + 1];
+    int64_t cnt;
+    if (a.rpos[r] < 0) {
+      cnt = a1 - a0;  // r is not in I: R*B*Q's row is empty
+    } else if (!a.accumulate) {
+      long long kept = 0;
+      for (int64_t q = a0 + lane; q < a1; q += 32) kept += a.cpos[a.Aj[q]] < 0;
+      kept = warp_sum(kept);
+      cnt = kept + (x1 - x0);
+    } else {
+      long long both = 0;  // columns present in A(r,:) and in R*B*Q(r,:)
+      for (int64_t x = x0 + lane; x < x1; x += 32) {
+        const int c = a.Xj[x];
+        const int64_t at = lower_bound_col(a.Aj, a0, a1, c);
+        both += (at < a1 && a.Aj[at] == c);
+      }
+      both = warp_sum(both);
+      cnt = (a1 - a0) + (x1 - x0) - both;
+    }
+    if (lane == 0) a.Cp[r + 1] = cnt;
+  }
+}
+
+__global__ void k_asgn_fill(AsgnArgs a) {
+  const int lane = lane_id();
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < a.m; r += (int64_t)gridDim.x * wpb) {
+    const int64_t a0 = a.Ap[r], a1 = a.Ap[r + 1];
+    const int64_t x0 = a.Xp[r], x1 = a.Xp[r + 1];
+    const int64_t o = a.Cp[r];
+    if (a.rpos[r] < 0) {  // copy the row
+      for (int64_t q = lane; q < a1 - a0; q += 32) {
+        a.Cj[o + q] = a.Aj[a0 + q];
+        copy_val(a.Cv, o + q, a.Av, a0 + q, a.vbytes);
+      }
+      continue;
+    }
+    if (lane != 0) continue;
+    // merge A(r,:) (minus the I x J block when assigning) with R*B*Q(r,:)
+    int64_t i = a0, x = x0, w = o;
+    while (true) {
+      if (!a.accumulate)
+        while (i < a1 && a.cpos[a.Aj[i]] >= 0) ++i;
+      const bool ha = i < a1, hx = x < x1;
+      if (!ha && !hx) break;
+      const int ca = ha ? a.Aj[i] : 0x7fffffff, cx = hx ? a.Xj[x] : 0x7fffffff;
+      if (ca < cx) {
+        a.Cj[w] = ca;
+        copy_val(a.Cv, w, a.Av, i, a.vbytes);
+        ++i;
+      } else if (cx < ca) {
+        a.Cj[w] = cx;
+        copy_val(a.Cv, w, a.Xv, x, a.vbytes);
+        ++x;
+      } else {  // only with accumulate
+        a.Cj[w] = ca;
+        combine_val(a, w, i, x);
+        ++i;
+        ++x;
+      }
+      ++w;
+    }
+  }
+}
+
+void launch_asgn_count(const AsgnArgs &a, cudaStream_t st) {
+  if (a.m > 0) {
+    count_launch();
+    k_asgn_count<<<grid1(a.m * 32), 256, 0, st>>>(a);
+  }
+}
+void launch_asgn_fill(const AsgnArgs &a, cudaStream_t st) {
+  if (a.m > 0) {
+    count_launch();
+    k_asgn_fill<<<grid1(a.m * 32), 256, 0, st>>>(a);
+  }
+}
+
+}  // namespace hs

@@ -1,0 +1,173 @@
+// internal.h -- declarations shared by the library's translation units
+// (host launchers of the kernels and the bin layout).  Not part of the ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hs {
+
+// ---------------------------------------------------------------- bins
+// Rows are binned by their product count f (flops) before the symbolic pass
+// and by (f, output count c) before the numeric pass.  A bin "key" orders the
+// concatenated row lists; heavy rows get one key per power of two of f,
+// largest first, so dynamic scheduling hands out the longest rows first.
+constexpr int NKEYS = 64;
+constexpr int KEY_TINY = 1;   // f <= 32: warp, one product per lane
+constexpr int KEY_WARP = 2;   // f <= 512: warp, private shared hash table
+constexpr int KEY_MID = 3;    // symbolic: f <= 4096;  numeric: c <= CAP_MID
+constexpr int KEY_LARGE = 4;  // symbolic: f <= 16384; numeric: c <= cap_large
+constexpr int KEY_HEAVY = 5;  // 5 + (62 - floor(log2 f)): symbolic bitmap / numeric column parts
+constexpr int F_TINY = 32, F_WARP = 512, F_MID = 4096, F_LARGE = 16384;
+constexpr int CAP_MID = 2048;
+// Column segments recorded for rows that may need column parts: width SEG_W
+// (a multiple of 1024, at most every numeric table's capacity).
+constexpr int SEG_W = 4096;
+constexpr int BITMAP_COLS = 1 << 20;  // columns covered by the heavy symbolic bitmap
+
+__host__ __device__ inline int floor_log2_u64(uint64_t x) {
+#ifdef __CUDA_ARCH__
+  return 63 - __clzll((long long)x);
+#else
+  return 63 - __builtin_clzll(x);
+#endif
+}
+__host__ __device__ inline int heavy_key(int64_t f) { return KEY_HEAVY + (62 - floor_log2_u64((uint64_t)f)); }
+__host__ __device__ inline int sym_key(int64_t f) {
+  if (f <= 0) return 0;
+  if (f <= F_TINY) return KEY_TINY;
+  if (f <= F_WARP) return KEY_WARP;
+  if (f <= F_MID) return KEY_MID;
+  if (f <= F_LARGE) return KEY_LARGE;
+  return heavy_key(f);
+}
+__host__ __device__ inline int num_key(int64_t f, int64_t c, int cap_large) {
+  if (c <= 0) return 0;
+  if (f <= F_TINY) return KEY_TINY;
+  if (f <= F_WARP) return KEY_WARP;
+  if (c <= CAP_MID) return KEY_MID;
+  if (c <= cap_large) return KEY_LARGE;
+  return heavy_key(f);
+}
+
+// ---------------------------------------------------------- device views
+struct RowSet {          // the left operand's stored rows
+  const int64_t *p;      // offsets, nslots+1
+  const int32_t *j;      // column ids
+  const void *v;         // values or null
+  const int32_t *ids;    // DCSR row ids (null for CSR: slot == row)
+  int64_t nslots;
+  int64_t nnz;
+  int64_t m;             // rows of A (and of C)
+  long long *dbg;        // guard record (guarded builds)
+};
+struct RightOp {
+  const int64_t *p;
+  const int32_t *j;
+  const void *v;
+  int64_t n;    // columns
+  int64_t m;    // rows
+  int64_t nnz;
+  long long *dbg;
+};
+
+// kernel launches issued by this library (all threads), for benchmarks
+void count_launch();
+unsigned long long launch_total();
+
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) with the failure kept for
+// the driver to report (launchers return void)
+cudaError_t &attr_error();
+template <class K> inline void set_smem_attr(K kernel, size_t bytes) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) attr_error() = e;
+}
+
+// --------------------------------------------------------------- launchers
+// analysis.cu
+void launch_flops(const RowSet &A, const RightOp &B, int64_t *f, int *key_cnt, unsigned long long *stats,
+                  cudaStream_t st);
+void launch_key_offsets(const int *key_cnt, int *key_off, int *key_cur, cudaStream_t st);
+void launch_scatter_sym(const RowSet &A, const int64_t *f, int *key_cur, int *list, int32_t *hslot,
+                        int *nhist, cudaStream_t st);
+void launch_num_count(const RowSet &A, const int64_t *f, const int64_t *Cp, int cap_large, int *key_cnt,
+                      cudaStream_t st);
+void launch_scatter_num(const RowSet &A, const int64_t *f, const int64_t *Cp, int cap_large, int *key_cur,
+                        int *list, cudaStream_t st);
+void launch_scan_i64(int64_t *a, int64_t n, int64_t *tmp, cudaStream_t st);  // exclusive, in place
+int64_t scan_tmp_elems(int64_t n);
+void launch_validate(const int64_t *p, const int32_t *j, int64_t rows, int64_t ncols, int *flag, cudaStream_t st);
+void launch_sm_count_init();
+int sm_count();
+
+// symbolic.cu: counts go to cnt[out_row + 1] (int64)
+struct SymArgs {
+  RowSet A;
+  RightOp B;
+  const int64_t *f;        // flops per row slot
+  const int *list;         // rows of the bin
+  int count;               // rows in the bin
+  int64_t *cnt;            // per output row
+  const int32_t *hslot;    // segment-histogram slot per row (-1 none)
+  uint32_t *hist;          // nhist x nseg
+  int nseg;
+  int *dyn;                // dynamic row counter (heavy)
+  int *err;
+};
+void launch_sym_tiny(const SymArgs &a, cudaStream_t st);
+void launch_sym_warp(const SymArgs &a, cudaStream_t st);
+void launch_sym_mid(const SymArgs &a, cudaStream_t st);
+void launch_sym_large(const SymArgs &a, cudaStream_t st);
+void launch_sym_heavy(const SymArgs &a, cudaStream_t st);
+
+// numeric_*.cu
+struct NumArgs {
+  RowSet A;
+  RightOp B;
+  const int64_t *f;
+  const int *list;
+  int count;
+  const int64_t *Cp;
+  int32_t *Cj;
+  void *Cv;
+  const int32_t *hslot;
+  const uint32_t *hist;
+  int nseg;
+  int *dyn;
+  int *err;
+};
+// kind: 0 tiny, 1 warp, 2 mid, 3 large, 4 heavy.  dtype codes as in the ABI.
+bool launch_numeric_pt(int dtype, int kind, const NumArgs &a, cudaStream_t st);
+bool launch_numeric_mp(int dtype, int kind, const NumArgs &a, cudaStream_t st);
+bool launch_numeric_oa(int kind, const NumArgs &a, cudaStream_t st);
+bool launch_numeric_sel(int second, int vbytes, int kind, const NumArgs &a, cudaStream_t st);
+
+// index.cu: selection matrices and the SpAsgn merge
+void launch_build_R(const int32_t *I, int64_t nI, int64_t *Rp, int32_t *Rj, cudaStream_t st);
+void launch_build_Q_count(const int32_t *J, int64_t nJ, int64_t *Qp_counts, cudaStream_t st);
+void launch_build_Q_fill(const int32_t *J, int64_t nJ, int64_t *Qcur, int32_t *Qj, cudaStream_t st);
+void launch_sort_short_rows(const int64_t *ptr, int32_t *j, int64_t rows, cudaStream_t st);
+void launch_check_range(const int32_t *X, int64_t n, int64_t bound, int *flag, cudaStream_t st);
+// pos[X[i]] = i for in-range X[i] (bit 1 of flag: out of range; bit 2: repeated)
+void launch_mark_positions(const int32_t *X, int64_t n, int64_t bound, int32_t *pos, int *flag, cudaStream_t st);
+void launch_fill_i32(int32_t *a, int64_t n, int32_t v, cudaStream_t st);
+void launch_rows_from_pos(const int32_t *pos, int64_t m, int64_t *cnt, cudaStream_t st);
+void launch_fill_from_pos(const int32_t *pos, int64_t m, const int64_t *ptr, int32_t *out, cudaStream_t st);
+void launch_iota_i64(int64_t *p, int64_t n, cudaStream_t st);
+struct AsgnArgs {
+  const int64_t *Ap; const int32_t *Aj; const void *Av;   // A (m x n)
+  const int64_t *Xp; const int32_t *Xj; const void *Xv;   // X = R*B*Q (m x n)
+  const int32_t *rpos;  // m: row in I or -1
+  const int32_t *cpos;  // n: column in J or -1
+  int64_t m;
+  int vbytes;           // value width (0 for bool)
+  int accumulate;
+  int add_kind;         // semiring for extend-add collisions
+  int dtype;
+  int64_t *Cp;          // counts then offsets
+  int32_t *Cj;
+  void *Cv;
+};
+void launch_asgn_count(const AsgnArgs &a, cudaStream_t st);
+void launch_asgn_fill(const AsgnArgs &a, cudaStream_t st);
+
+}  // namespace hs

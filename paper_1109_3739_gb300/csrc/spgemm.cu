@@ -1,0 +1,679 @@
+// spgemm.cu -- host driver and C ABI (include/hspgemm.h).
+//
+// hs_spgemm runs the phases of the row-wise SpGEMM on one stream:
+//   1. flops per row and binning of the non-empty rows by flops
+//      (one device->host read: bin sizes, total flops, validation flags);
+//   2. symbolic pass per bin: output nonzeros per row;
+//   3. inclusive scan of the counts into C's row offsets, binning of the rows
+//      again by (flops, output count) for the numeric pass
+//      (second device->host read: nnz(C) and the bin sizes);
+//   4. allocation of C's column ids and values, numeric pass per bin.
+// hs_spref and hs_spasgn build their 0/1 selection matrices on the device and
+// call the same driver with the selector semirings (Section 3.1).
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/hspgemm.h"
+#include "internal.h"
+
+namespace hs {
+
+static thread_local int t_last_cuda = 0;
+static thread_local char t_detail[256] = "";
+
+// Checking mode: HS_DEBUG_SYNC=1 in the environment synchronises after every
+// phase, so a CUDA error or a failed index check is attributed to the phase
+// that raised it.  Without it, failed checks are reported at the product's
+// second host synchronisation (or at the end with HS_FLAG_VALIDATE).
+static bool debug_sync() {
+  static int v = -1;
+  if (v < 0) {
+    const char *e = getenv("HS_DEBUG_SYNC");
+    v = (e && *e && *e != '0') ? 1 : 0;
+  }
+  return v == 1;
+}
+
+// ---------------------------------------------------------------- profiling
+struct Prof {
+  std::mutex mu;
+  bool on = false;
+  std::vector<std::string> names;
+  std::vector<double> ms;
+  std::vector<int64_t> launches;
+  struct Pending {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  int phase_id(const char *nm) {
+    for (size_t i = 0; i < names.size(); ++i)
+      if (names[i] == nm) return (int)i;
+    names.push_back(nm);
+    ms.push_back(0);
+    launches.push_back(0);
+    return (int)names.size() - 1;
+  }
+  void drain() {
+    for (auto &p : pending) {
+      cudaEventSynchronize(p.b);
+      float t = 0;
+      cudaEventElapsedTime(&t, p.a, p.b);
+      ms[p.phase] += t;
+      launches[p.phase] += 1;
+      cudaEventDestroy(p.a);
+      cudaEventDestroy(p.b);
+    }
+    pending.clear();
+  }
+};
+static Prof g_prof;
+
+struct PhaseTimer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  int phase = -1;
+  cudaStream_t st;
+  PhaseTimer(const char *nm, cudaStream_t s, bool active = true) : st(s) {
+    if (!g_prof.on || !active) return;
+    std::lock_guard<std::mutex> g(g_prof.mu);
+    phase = g_prof.phase_id(nm);
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, st);
+  }
+  ~PhaseTimer() {
+    if (phase < 0) return;
+    cudaEventRecord(b, st);
+    std::lock_guard<std::mutex> g(g_prof.mu);
+    g_prof.pending.push_back({phase, a, b});
+  }
+};
+
+// --------------------------------------------------------------- allocation
+struct Mem {
+  const hs_allocator *al;
+  cudaStream_t st;
+  struct Blk {
+    void *p;
+    size_t n;
+  };
+  std::vector<Blk> scratch;
+  bool failed = false;
+
+  void *raw(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (al && al->alloc) {
+      p = al->alloc(bytes, (void *)st, al->ctx);
+    } else if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    if (!p) failed = true;
+    return p;
+  }
+  void release(void *p, size_t bytes) {
+    if (!p) return;
+    if (bytes == 0) bytes = 16;
+    if (al && al->free) al->free(p, bytes, (void *)st, al->ctx);
+    else if (!al || !al->alloc) cudaFreeAsync(p, st);
+  }
+  template <typename T> T *tmp(size_t count) {
+    T *p = (T *)raw(sizeof(T) * count);
+    if (p) scratch.push_back({p, sizeof(T) * count});
+    return p;
+  }
+  ~Mem() {
+    for (auto &b : scratch) release(b.p, b.n);
+  }
+};
+
+static int vbytes_of(int dt) {
+  switch (dt) {
+    case HS_F64: case HS_I64: return 8;
+    case HS_F32: case HS_I32: return 4;
+    default: return 0;
+  }
+}
+
+// pinned staging for the small device->host reads
+struct Pinned {
+  void *p = nullptr;
+  ~Pinned() {
+    if (p) cudaFreeHost(p);
+  }
+};
+static thread_local Pinned t_pin;
+static void *pinned(size_t bytes) {
+  if (!t_pin.p && cudaMallocHost(&t_pin.p, 8192) != cudaSuccess) {
+    t_pin.p = nullptr;
+    return nullptr;
+  }
+  return bytes <= 8192 ? t_pin.p : nullptr;
+}
+
+#define CK(call)                          \
+  do {                                    \
+    cudaError_t e_ = (call);              \
+    if (e_ != cudaSuccess) {              \
+      t_last_cuda = (int)e_;              \
+      cudaGetLastError();                 \
+      return HS_ECUDA;                    \
+    }                                     \
+  } while (0)
+
+static int check_launch() {
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && attr_error() != cudaSuccess) {
+    e = attr_error();
+    attr_error() = cudaSuccess;
+  }
+  if (e != cudaSuccess) {
+    t_last_cuda = (int)e;
+    snprintf(t_detail, sizeof(t_detail), "%s (%d)", cudaGetErrorName(e), (int)e);
+    return HS_ECUDA;
+  }
+  return HS_OK;
+}
+
+struct SmallBlock;
+static int phase_check(const char *phase, cudaStream_t st, const long long *dbg_dev);
+
+static bool dtype_ok(int dt) { return dt >= HS_F64 && dt <= HS_BOOL; }
+
+static void free_mat(hs_mat *M, Mem &mem) {
+  if (!M) return;
+  const int64_t rows = M->m;
+  mem.release(M->ptr, sizeof(int64_t) * (size_t)(rows + 1));
+  mem.release(M->idx, sizeof(int32_t) * (size_t)M->nnz);
+  if (M->val) mem.release(M->val, (size_t)vbytes_of(M->dtype) * (size_t)M->nnz);
+  memset(M, 0, sizeof(*M));
+}
+
+// ----------------------------------------------------------------- SpGEMM
+struct SmallBlock {  // device counters, read back in one copy
+  int key_cnt[NKEYS];
+  int key_off[NKEYS + 1];
+  int key_cur[NKEYS];
+  int dyn[2];
+  int nhist;
+  int err;
+  int valflag;
+  int pad;
+  unsigned long long stats[4];
+  long long nnz;
+  long long dbg[2];  // guarded builds: first failed check (code, index)
+};
+
+static int phase_check(const char *phase, cudaStream_t st, const long long *dbg_dev) {
+  if (int e = check_launch()) {
+    char tmp[256];
+    snprintf(tmp, sizeof(tmp), "%s: %s", phase, t_detail);
+    snprintf(t_detail, sizeof(t_detail), "%s", tmp);
+    return e;
+  }
+  if (!debug_sync()) return HS_OK;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    t_last_cuda = (int)e;
+    snprintf(t_detail, sizeof(t_detail), "%s: %s (%d)", phase, cudaGetErrorName(e), (int)e);
+    cudaGetLastError();
+    return HS_ECUDA;
+  }
+  if (dbg_dev) {
+    long long d[2] = {0, 0};
+    cudaMemcpy(d, dbg_dev, sizeof(d), cudaMemcpyDeviceToHost);
+    if (d[0]) {
+      snprintf(t_detail, sizeof(t_detail), "%s: guard %lld failed at index %lld", phase, d[0], d[1]);
+      return HS_EINTERNAL;
+    }
+  }
+  return HS_OK;
+}
+
+static bool numeric_supported(int sr, int adt, int bdt, int &out_dt) {
+  switch (sr) {
+    case HS_PLUS_TIMES:
+      out_dt = adt;
+      return adt == bdt && (adt == HS_F64 || adt == HS_F32 || adt == HS_I64);
+    case HS_MIN_PLUS:
+      out_dt = adt;
+      return adt == bdt && (adt == HS_F32 || adt == HS_I32);
+    case HS_OR_AND:
+      out_dt = HS_BOOL;
+      return true;
+    case HS_SELECT2ND:
+      out_dt = bdt;
+      return true;
+    case HS_SELECT1ST:
+      out_dt = adt;
+      return true;
+  }
+  return false;
+}
+
+static int cap_large_of(int out_dt) { return vbytes_of(out_dt) == 8 ? 4096 : 8192; }
+
+static bool launch_num(int sr, int out_dt, int kind, const NumArgs &a, cudaStream_t st) {
+  switch (sr) {
+    case HS_PLUS_TIMES: return launch_numeric_pt(out_dt, kind, a, st);
+    case HS_MIN_PLUS: return launch_numeric_mp(out_dt, kind, a, st);
+    case HS_OR_AND: return launch_numeric_oa(kind, a, st);
+    case HS_SELECT2ND: return launch_numeric_sel(1, vbytes_of(out_dt), kind, a, st);
+    case HS_SELECT1ST: return launch_numeric_sel(0, vbytes_of(out_dt), kind, a, st);
+  }
+  return false;
+}
+
+static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem &mem, Mem &outmem,
+                       uint32_t flags) {
+  cudaStream_t st = mem.st;
+  if (!A || !B || !C) return HS_EINVAL;
+  if (A->fmt != HS_CSR && A->fmt != HS_DCSR) return HS_EINVAL;
+  if (B->fmt != HS_CSR) return HS_EINVAL;
+  if (!dtype_ok(A->dtype) || !dtype_ok(B->dtype)) return HS_EINVAL;
+  if (A->n != B->m || A->m < 0 || B->n < 0 || A->nnz < 0 || B->nnz < 0) return HS_EINVAL;
+  if (B->n > 0x7fffffffLL || A->n > 0x7fffffffLL) return HS_EINVAL;
+  int out_dt = 0;
+  if (!numeric_supported(sr, A->dtype, B->dtype, out_dt)) return HS_EINVAL;
+  const int vb = vbytes_of(out_dt);
+  if ((sr == HS_PLUS_TIMES || sr == HS_MIN_PLUS) && ((A->nnz && !A->val) || (B->nnz && !B->val))) return HS_EINVAL;
+  if (sr == HS_SELECT2ND && vb && B->nnz && !B->val) return HS_EINVAL;
+  if (sr == HS_SELECT1ST && vb && A->nnz && !A->val) return HS_EINVAL;
+  const int64_t m = A->m, n = B->n;
+  const int64_t nslots = A->fmt == HS_DCSR ? A->nzr : A->m;
+  if (nslots < 0 || (A->fmt == HS_DCSR && nslots > 0 && !A->ids)) return HS_EINVAL;
+  if ((nslots > 0 && !A->ptr) || (B->m >= 0 && !B->ptr && B->m > 0)) return HS_EINVAL;
+  if (nslots > 0x7fffffffLL) return HS_EUNSUPPORTED;
+
+  memset(C, 0, sizeof(*C));
+  C->fmt = HS_CSR;
+  C->dtype = out_dt;
+  C->m = m;
+  C->n = n;
+  int64_t *Cp = (int64_t *)outmem.raw(sizeof(int64_t) * (size_t)(m + 1));
+  if (!Cp) return HS_ENOMEM;
+  C->ptr = Cp;
+  CK(cudaMemsetAsync(Cp, 0, sizeof(int64_t) * (size_t)(m + 1), st));
+  if (nslots == 0 || A->nnz == 0 || B->nnz == 0 || n == 0) {
+    C->idx = (int32_t *)outmem.raw(4);
+    if (!C->idx) return HS_ENOMEM;
+    if (vb) {  // typed outputs always carry a (here empty) value array
+      C->val = outmem.raw((size_t)vb);
+      if (!C->val) return HS_ENOMEM;
+    }
+    return check_launch();
+  }
+
+  int64_t *f = mem.tmp<int64_t>(nslots);
+  int *list = mem.tmp<int>(nslots);
+  int32_t *hslot = mem.tmp<int32_t>(nslots);
+  SmallBlock *sb = mem.tmp<SmallBlock>(1);
+  if (mem.failed) return HS_ENOMEM;
+  RowSet rs{A->ptr, A->idx, A->val, A->fmt == HS_DCSR ? A->ids : nullptr, nslots, A->nnz, m, sb->dbg};
+  RightOp rb{B->ptr, B->idx, B->val, n, B->m, B->nnz, sb->dbg};
+  SmallBlock *hb = (SmallBlock *)pinned(sizeof(SmallBlock));
+  if (!hb) return HS_ECUDA;
+  CK(cudaMemsetAsync(sb, 0, sizeof(SmallBlock), st));
+
+  {
+    PhaseTimer t("analysis", st);
+    if (flags & HS_FLAG_VALIDATE) {
+      launch_validate(A->ptr, A->idx, nslots, A->n, &sb->valflag, st);
+      launch_validate(B->ptr, B->idx, B->m, B->n, &sb->valflag, st);
+    }
+    launch_flops(rs, rb, f, sb->key_cnt, sb->stats, st);
+    launch_key_offsets(sb->key_cnt, sb->key_off, sb->key_cur, st);
+    launch_scatter_sym(rs, f, sb->key_cur, list, hslot, &sb->nhist, st);
+  }
+  if (int e = phase_check("analysis", st, sb->dbg)) return e;
+  CK(cudaMemcpyAsync(hb, sb, sizeof(SmallBlock), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (hb->valflag & 4) return HS_EINVAL;
+  if (hb->valflag & 1) return HS_EINVAL;
+  if (hb->valflag & 2) return HS_ENONCANON;
+  if (hb->stats[1] >= (1ull << 31)) return HS_EUNSUPPORTED;  // one row's products must fit int32
+  int key_off[NKEYS + 1];
+  memcpy(key_off, hb->key_off, sizeof(key_off));
+  const int nhist = hb->nhist;
+  const int nseg = (int)((n + SEG_W - 1) / SEG_W);
+
+  uint32_t *hist = nullptr;
+  if (nhist > 0) {
+    hist = mem.tmp<uint32_t>((size_t)nhist * nseg);
+    if (!hist) return HS_ENOMEM;
+    CK(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)nhist * nseg, st));
+  }
+
+  // ---- symbolic
+  SymArgs sa{rs, rb, f, nullptr, 0, Cp, hslot, hist, nseg, &sb->dyn[0], &sb->err};
+  auto sym_bin = [&](int k0, int k1) {
+    sa.list = list + key_off[k0];
+    sa.count = key_off[k1] - key_off[k0];
+  };
+  {
+    PhaseTimer t("symbolic", st);
+    sym_bin(KEY_TINY, KEY_TINY + 1);
+    { PhaseTimer t2("symbolic_tiny", st, sa.count > 0); launch_sym_tiny(sa, st); }
+    if (int e = phase_check("symbolic_tiny", st, sb->dbg)) return e;
+    sym_bin(KEY_WARP, KEY_WARP + 1);
+    { PhaseTimer t2("symbolic_warp", st, sa.count > 0); launch_sym_warp(sa, st); }
+    if (int e = phase_check("symbolic_warp", st, sb->dbg)) return e;
+    sym_bin(KEY_MID, KEY_MID + 1);
+    { PhaseTimer t2("symbolic_mid", st, sa.count > 0); launch_sym_mid(sa, st); }
+    if (int e = phase_check("symbolic_mid", st, sb->dbg)) return e;
+    sym_bin(KEY_LARGE, KEY_LARGE + 1);
+    { PhaseTimer t2("symbolic_large", st, sa.count > 0); launch_sym_large(sa, st); }
+    if (int e = phase_check("symbolic_large", st, sb->dbg)) return e;
+    sym_bin(KEY_HEAVY, NKEYS);
+    { PhaseTimer t2("symbolic_heavy", st, sa.count > 0); launch_sym_heavy(sa, st); }
+    if (int e = phase_check("symbolic_heavy", st, sb->dbg)) return e;
+  }
+
+  // ---- offsets and numeric bins
+  const int cap_large = cap_large_of(out_dt);
+  int64_t *scan_tmp = mem.tmp<int64_t>(scan_tmp_elems(m + 1));
+  if (!scan_tmp) return HS_ENOMEM;
+  {
+    PhaseTimer t("scan_bin", st);
+    launch_scan_i64(Cp, m + 1, scan_tmp, st);
+    CK(cudaMemsetAsync(sb->key_cnt, 0, sizeof(int) * NKEYS, st));
+    launch_num_count(rs, f, Cp, cap_large, sb->key_cnt, st);
+    launch_key_offsets(sb->key_cnt, sb->key_off, sb->key_cur, st);
+    launch_scatter_num(rs, f, Cp, cap_large, sb->key_cur, list, st);
+    CK(cudaMemcpyAsync(&sb->nnz, Cp + m, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+  }
+  if (int e = phase_check("scan_bin", st, sb->dbg)) return e;
+  CK(cudaMemcpyAsync(hb, sb, sizeof(SmallBlock), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (hb->dbg[0]) {
+    snprintf(t_detail, sizeof(t_detail), "index check %lld failed at %lld", hb->dbg[0], hb->dbg[1]);
+    return HS_EINTERNAL;
+  }
+  if (hb->err) {
+    snprintf(t_detail, sizeof(t_detail), "device consistency check %d", hb->err);
+    return HS_EINTERNAL;
+  }
+  const int64_t nnz = hb->nnz;
+  memcpy(key_off, hb->key_off, sizeof(key_off));
+  C->nnz = nnz;
+  C->idx = (int32_t *)outmem.raw(sizeof(int32_t) * (size_t)nnz);
+  if (!C->idx) return HS_ENOMEM;
+  if (vb) {
+    C->val = outmem.raw((size_t)vb * (size_t)nnz);
+    if (!C->val) return HS_ENOMEM;
+  }
+
+  // ---- numeric
+  NumArgs na{rs, rb, f, nullptr, 0, Cp, C->idx, C->val, hslot, hist, nseg, &sb->dyn[1], &sb->err};
+  const char *names[5] = {"numeric_tiny", "numeric_warp", "numeric_mid", "numeric_large", "numeric_heavy"};
+  const int k0s[5] = {KEY_TINY, KEY_WARP, KEY_MID, KEY_LARGE, KEY_HEAVY};
+  const int k1s[5] = {KEY_TINY + 1, KEY_WARP + 1, KEY_MID + 1, KEY_LARGE + 1, NKEYS};
+  {
+    PhaseTimer t("numeric", st);
+    for (int kind = 0; kind < 5; ++kind) {
+      na.list = list + key_off[k0s[kind]];
+      na.count = key_off[k1s[kind]] - key_off[k0s[kind]];
+      {
+        PhaseTimer t2(names[kind], st, na.count > 0);
+        if (na.count > 0 && !launch_num(sr, out_dt, kind, na, st)) return HS_EINVAL;
+      }
+      if (int e = phase_check(names[kind], st, sb->dbg)) return e;
+    }
+  }
+  if (flags & HS_FLAG_VALIDATE) {
+    CK(cudaMemcpyAsync(hb, sb, sizeof(SmallBlock), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (hb->dbg[0]) {
+      snprintf(t_detail, sizeof(t_detail), "index check %lld failed at %lld", hb->dbg[0], hb->dbg[1]);
+      return HS_EINTERNAL;
+    }
+    if (hb->err) {
+      snprintf(t_detail, sizeof(t_detail), "device consistency check %d", hb->err);
+      return HS_EINTERNAL;
+    }
+  }
+  return HS_OK;
+}
+
+// runs fn; on failure releases whatever fn allocated for C
+template <class F> static int with_output(hs_mat *C, Mem &outmem, F &&fn) {
+  int e = fn();
+  if (e != HS_OK && C) free_mat(C, outmem);
+  return e;
+}
+
+static int spref_impl(const hs_mat *A, const int32_t *I, int64_t nI, const int32_t *J, int64_t nJ, hs_mat *Bout,
+                      Mem &mem, Mem &outmem, uint32_t flags) {
+  cudaStream_t st = mem.st;
+  if (!A || !Bout || A->fmt != HS_CSR || nI < 0 || nJ < 0) return HS_EINVAL;
+  if ((nI > 0 && !I) || (nJ > 0 && !J)) return HS_EINVAL;
+  if (nI > 0x7fffffffLL || nJ > 0x7fffffffLL) return HS_EUNSUPPORTED;
+  // index ranges are always checked: they address A's rows and columns
+  int *flag = mem.tmp<int>(2);
+  int *hflag = (int *)pinned(8);
+  if (!flag || !hflag) return HS_ENOMEM;
+  CK(cudaMemsetAsync(flag, 0, 8, st));
+  launch_check_range(I, nI, A->m, flag, st);
+  launch_check_range(J, nJ, A->n, flag, st);
+  CK(cudaMemcpyAsync(hflag, flag, 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (hflag[0]) return HS_EINVAL;
+
+  // R = sparse(1:len(I), I, 1, len(I), m): row t holds column I[t]
+  int64_t *Rp = mem.tmp<int64_t>(nI + 1);
+  // Q = sparse(J, 1:len(J), 1, n, len(J)): row k holds every p with J[p] == k
+  int64_t *Qp = mem.tmp<int64_t>(A->n + 1);
+  int64_t *Qcur = mem.tmp<int64_t>(A->n + 1);
+  int32_t *Qj = mem.tmp<int32_t>(nJ > 0 ? nJ : 1);
+  int64_t *scan_tmp = mem.tmp<int64_t>(scan_tmp_elems(A->n + 1));
+  if (mem.failed) return HS_ENOMEM;
+  {
+    PhaseTimer t("spref_build", st);
+    launch_iota_i64(Rp, nI + 1, st);
+    CK(cudaMemsetAsync(Qp, 0, sizeof(int64_t) * (size_t)(A->n + 1), st));
+    launch_build_Q_count(J, nJ, Qp, st);
+    launch_scan_i64(Qp, A->n + 1, scan_tmp, st);
+    CK(cudaMemcpyAsync(Qcur, Qp, sizeof(int64_t) * (size_t)(A->n + 1), cudaMemcpyDeviceToDevice, st));
+    launch_build_Q_fill(J, nJ, Qcur, Qj, st);
+    launch_sort_short_rows(Qp, Qj, A->n, st);
+  }
+  if (int e = check_launch()) return e;
+  hs_mat R{HS_CSR, HS_BOOL, nI, A->m, nI, 0, Rp, const_cast<int32_t *>(I), nullptr, nullptr};
+  hs_mat Q{HS_CSR, HS_BOOL, A->n, nJ, nJ, 0, Qp, Qj, nullptr, nullptr};
+  hs_mat RA;
+  memset(&RA, 0, sizeof(RA));
+  int e = spgemm_impl(HS_SELECT2ND, &R, A, &RA, mem, mem, flags & ~HS_FLAG_VALIDATE);
+  if (e) {
+    free_mat(&RA, mem);
+    return e;
+  }
+  e = spgemm_impl(HS_SELECT1ST, &RA, &Q, Bout, mem, outmem, flags & ~HS_FLAG_VALIDATE);
+  free_mat(&RA, mem);
+  return e;
+}
+
+static int spasgn_impl(const hs_mat *A, const int32_t *I, int64_t nI, const int32_t *J, int64_t nJ,
+                       const hs_mat *B, int accumulate, int add_sr, hs_mat *C, Mem &mem, Mem &outmem,
+                       uint32_t flags) {
+  cudaStream_t st = mem.st;
+  if (!A || !B || !C || A->fmt != HS_CSR || B->fmt != HS_CSR) return HS_EINVAL;
+  if (nI < 0 || nJ < 0 || B->m != nI || B->n != nJ || A->dtype != B->dtype) return HS_EINVAL;
+  if ((nI > 0 && !I) || (nJ > 0 && !J)) return HS_EINVAL;
+  if (accumulate && A->dtype != HS_BOOL && add_sr != HS_PLUS_TIMES && add_sr != HS_MIN_PLUS) return HS_EINVAL;
+  const int vb = vbytes_of(A->dtype);
+  const int64_t m = A->m, n = A->n;
+  int32_t *rpos = mem.tmp<int32_t>(m > 0 ? m : 1);
+  int32_t *cpos = mem.tmp<int32_t>(n > 0 ? n : 1);
+  int *flag = mem.tmp<int>(2);
+  int *hflag = (int *)pinned(8);
+  if (mem.failed || !hflag) return HS_ENOMEM;
+  CK(cudaMemsetAsync(flag, 0, 8, st));
+  launch_fill_i32(rpos, m, -1, st);
+  launch_fill_i32(cpos, n, -1, st);
+  launch_mark_positions(I, nI, m, rpos, flag, st);
+  launch_mark_positions(J, nJ, n, cpos, flag, st);
+  CK(cudaMemcpyAsync(hflag, flag, 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (hflag[0] & 1) return HS_EINVAL;
+  if (hflag[0] & 2) return HS_EDUP;
+
+  // R = sparse(I, 1:mb, 1, ma, mb) and Q = sparse(1:nb, J, 1, nb, na)
+  int64_t *Rp = mem.tmp<int64_t>(m + 1);
+  int32_t *Rj = mem.tmp<int32_t>(nI > 0 ? nI : 1);
+  int64_t *Qp = mem.tmp<int64_t>(nJ + 1);
+  int64_t *scan_tmp = mem.tmp<int64_t>(scan_tmp_elems((m > n ? m : n) + 1));
+  if (mem.failed) return HS_ENOMEM;
+  {
+    PhaseTimer t("spasgn_build", st);
+    CK(cudaMemsetAsync(Rp, 0, sizeof(int64_t), st));
+    launch_rows_from_pos(rpos, m, Rp, st);
+    launch_scan_i64(Rp, m + 1, scan_tmp, st);
+    launch_fill_from_pos(rpos, m, Rp, Rj, st);
+    launch_iota_i64(Qp, nJ + 1, st);
+  }
+  hs_mat R{HS_CSR, HS_BOOL, m, nI, nI, 0, Rp, Rj, nullptr, nullptr};
+  hs_mat Q{HS_CSR, HS_BOOL, nJ, n, nJ, 0, Qp, const_cast<int32_t *>(J), nullptr, nullptr};
+  hs_mat RB, X;
+  memset(&RB, 0, sizeof(RB));
+  memset(&X, 0, sizeof(X));
+  int e = spgemm_impl(HS_SELECT2ND, &R, B, &RB, mem, mem, flags & ~HS_FLAG_VALIDATE);
+  if (!e) e = spgemm_impl(HS_SELECT1ST, &RB, &Q, &X, mem, mem, flags & ~HS_FLAG_VALIDATE);
+  free_mat(&RB, mem);
+  if (e) {
+    free_mat(&X, mem);
+    return e;
+  }
+  // C = A .* not(S*A*T) + R*B*Q  (or A + R*B*Q for extend-add)
+  memset(C, 0, sizeof(*C));
+  C->fmt = HS_CSR;
+  C->dtype = A->dtype;
+  C->m = m;
+  C->n = n;
+  C->ptr = (int64_t *)outmem.raw(sizeof(int64_t) * (size_t)(m + 1));
+  if (!C->ptr) {
+    free_mat(&X, mem);
+    return HS_ENOMEM;
+  }
+  AsgnArgs aa{A->ptr, A->idx, A->val, X.ptr, X.idx, X.val, rpos, cpos, m, vb, accumulate, add_sr, A->dtype,
+              C->ptr, nullptr, nullptr};
+  int64_t *hnnz = (int64_t *)pinned(8);
+  {
+    PhaseTimer t("spasgn_merge", st);
+    CK(cudaMemsetAsync(C->ptr, 0, sizeof(int64_t), st));
+    launch_asgn_count(aa, st);
+    launch_scan_i64(C->ptr, m + 1, scan_tmp, st);
+  }
+  CK(cudaMemcpyAsync(hnnz, C->ptr + m, 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  C->nnz = *hnnz;
+  C->idx = (int32_t *)outmem.raw(sizeof(int32_t) * (size_t)C->nnz);
+  if (vb) C->val = outmem.raw((size_t)vb * (size_t)C->nnz);
+  if (!C->idx || (vb && !C->val)) {
+    free_mat(&X, mem);
+    return HS_ENOMEM;
+  }
+  aa.Cj = C->idx;
+  aa.Cv = C->val;
+  {
+    PhaseTimer t("spasgn_merge", st);
+    launch_asgn_fill(aa, st);
+  }
+  free_mat(&X, mem);
+  return check_launch();
+}
+
+}  // namespace hs
+
+using namespace hs;
+
+extern "C" {
+
+int hs_spgemm(int semiring, const hs_mat *A, const hs_mat *B, hs_mat *C, const hs_allocator *al, void *stream,
+              uint32_t flags) {
+  if (!C) return HS_EINVAL;
+  memset(C, 0, sizeof(*C));
+  t_detail[0] = 0;
+  Mem mem{al, (cudaStream_t)stream};
+  Mem out{al, (cudaStream_t)stream};
+  return with_output(C, out, [&] { return spgemm_impl(semiring, A, B, C, mem, out, flags); });
+}
+
+int hs_spref(const hs_mat *A, const int32_t *I, int64_t nI, const int32_t *J, int64_t nJ, hs_mat *B,
+             const hs_allocator *al, void *stream, uint32_t flags) {
+  if (!B) return HS_EINVAL;
+  memset(B, 0, sizeof(*B));
+  Mem mem{al, (cudaStream_t)stream};
+  Mem out{al, (cudaStream_t)stream};
+  return with_output(B, out, [&] { return spref_impl(A, I, nI, J, nJ, B, mem, out, flags); });
+}
+
+int hs_spasgn(const hs_mat *A, const int32_t *I, int64_t nI, const int32_t *J, int64_t nJ, const hs_mat *B,
+              int accumulate, int add_semiring, hs_mat *C, const hs_allocator *al, void *stream, uint32_t flags) {
+  if (!C) return HS_EINVAL;
+  memset(C, 0, sizeof(*C));
+  Mem mem{al, (cudaStream_t)stream};
+  Mem out{al, (cudaStream_t)stream};
+  return with_output(C, out, [&] {
+    return spasgn_impl(A, I, nI, J, nJ, B, accumulate, add_semiring, C, mem, out, flags);
+  });
+}
+
+void hs_mat_free(hs_mat *M, const hs_allocator *al, void *stream) {
+  if (!M) return;
+  Mem mem{al, (cudaStream_t)stream};
+  free_mat(M, mem);
+}
+
+const char *hs_strerror(int s) {
+  switch (s) {
+    case HS_OK: return "success";
+    case HS_EINVAL: return "invalid argument (shape, dtype, semiring, pointer or index)";
+    case HS_ENONCANON: return "input matrix row not strictly increasing";
+    case HS_EDUP: return "duplicate index in SpAsgn I or J";
+    case HS_ENOMEM: return "allocation failed";
+    case HS_ETIMEDOUT: return "bounded device wait expired";
+    case HS_ECUDA: return "CUDA runtime error";
+    case HS_EUNSUPPORTED: return "unsupported request";
+    case HS_EINTERNAL: return "internal consistency check failed";
+  }
+  return "unknown status";
+}
+
+int hs_last_cuda_error(void) { return t_last_cuda; }
+
+const char *hs_last_error_detail(void) { return t_detail; }
+
+int hs_version(void) { return 100; }
+
+int64_t hs_launch_count(void) { return (int64_t)launch_total(); }
+
+void hs_profile_enable(int on) {
+  std::lock_guard<std::mutex> g(g_prof.mu);
+  g_prof.on = on != 0;
+}
+
+void hs_profile_reset(void) {
+  std::lock_guard<std::mutex> g(g_prof.mu);
+  g_prof.drain();
+  for (auto &x : g_prof.ms) x = 0;
+  for (auto &x : g_prof.launches) x = 0;
+}
+
+int hs_profile_read(double *ms, int64_t *launches, const char **names, int cap) {
+  std::lock_guard<std::mutex> g(g_prof.mu);
+  g_prof.drain();
+  const int n = (int)g_prof.names.size();
+  for (int i = 0; i < n && i < cap; ++i) {
+    if (ms) ms[i] = g_prof.ms[i];
+    if (launches) launches[i] = g_prof.launches[i];
+    if (names) names[i] = g_prof.names[i].c_str();
+  }
+  return n;
+}
+
+}  // extern "C"

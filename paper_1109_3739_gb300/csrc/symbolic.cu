@@ -1,0 +1,235 @@
+// symbolic.cu -- output nonzeros per row of C = A*B (structure only).
+//
+// The row-wise form of Algorithm 1 with the sparse accumulator of Figure 1
+// reduced to its occupancy part: each row's distinct output columns are
+// counted by the accumulator its bin selects.
+//   tiny  (f <= 32)    one warp, one product per lane, equal columns found
+//                      with __match_any_sync;
+//   warp  (f <= 512)   one warp, private shared-memory hash set;
+//   mid   (f <= 4096)  one CTA, shared hash set of 2f..8192 slots;
+//   large (f <= 16384) one CTA, shared hash set of up to 32768 slots, and
+//                      per-column-segment counts for the numeric pass;
+//   heavy (f > 16384)  one CTA, a bitmap over 2^20 columns (occupancy SPA in
+//                      shared memory), rows handed out largest first.
+// Counts go to cnt[row + 1] so an inclusive scan turns them into row offsets.
+#include "common.cuh"
+#include "internal.h"
+
+namespace hs {
+
+using StructSR = Semiring<OR_AND, NoVal>;
+
+__device__ __forceinline__ DevCsr dev_a(const RowSet &A) { return DevCsr{A.p, A.j, A.v, A.nslots, A.nnz, A.dbg}; }
+__device__ __forceinline__ DevCsr dev_b(const RightOp &B) { return DevCsr{B.p, B.j, B.v, B.m, B.nnz, B.dbg}; }
+// count of output row o goes to cnt[o + 1]
+__device__ __forceinline__ void put_count(const SymArgs &a, int64_t o, int64_t v) {
+  if (HS_G(a.A.dbg, o >= 0 && o < a.A.m, 30, o)) a.cnt[o + 1] = v;
+}
+__device__ __forceinline__ int64_t out_row(const RowSet &A, int r) { return A.ids ? (int64_t)A.ids[r] : (int64_t)r; }
+
+// --------------------------------------------------------------- tiny
+constexpr int TINY_WPB = 8;
+__global__ void __launch_bounds__(TINY_WPB * 32) k_sym_tiny(SymArgs a) {
+  __shared__ int scol[TINY_WPB][32];
+  const int w = threadIdx.x >> 5, lane = lane_id();
+  const DevCsr A = dev_a(a.A), B = dev_b(a.B);
+  for (int idx = blockIdx.x * TINY_WPB + w; idx < a.count; idx += gridDim.x * TINY_WPB) {
+    const int r = a.list[idx];
+    if (!HS_G(a.A.dbg, r >= 0 && r < a.A.nslots, 35, r)) continue;
+    const int64_t q0 = A.p[r], q1 = A.p[r + 1];
+    int nprod = 0;
+    for (int64_t qb = q0; qb < q1; qb += 32) {
+      const int64_t q = qb + lane;
+      int64_t s = 0, e = 0;
+      if (q < q1) entry_segment(A, B, q, false, 0, 0, s, e);
+      auto put = [&](int col, NoVal, int p) {
+        if (HS_G(a.A.dbg, nprod + p < 32, 34, nprod + p)) scol[w][nprod + p] = col;
+      };
+      nprod += warp_expand<StructSR>(B, s, (int)(e - s), NoVal{}, put);
+    }
+    __syncwarp();
+    const bool have = lane < nprod && lane < 32;
+    const int col = have ? scol[w][lane] : 0;
+    const unsigned act = __ballot_sync(FULL, have);
+    bool first = false;
+    if (have) {
+      const unsigned grp = __match_any_sync(act, col);
+      first = lane == __ffs(grp) - 1;
+    }
+    const int cnt = __popc(__ballot_sync(FULL, first));
+    if (lane == 0) {
+      put_count(a, out_row(a.A, r), cnt);
+      if (nprod > 32) atomicExch(a.err, 2);
+    }
+    __syncwarp();
+  }
+}
+
+// --------------------------------------------------------------- warp
+constexpr int WARP_WPB = 8, WARP_SLOTS = 1024;
+__global__ void __launch_bounds__(WARP_WPB * 32) k_sym_warp(SymArgs a) {
+  __shared__ int tables[WARP_WPB][WARP_SLOTS];
+  const int w = threadIdx.x >> 5, lane = lane_id();
+  int *keys = tables[w];
+  const DevCsr A = dev_a(a.A), B = dev_b(a.B);
+  for (int idx = blockIdx.x * WARP_WPB + w; idx < a.count; idx += gridDim.x * WARP_WPB) {
+    const int r = a.list[idx];
+    if (!HS_G(a.A.dbg, r >= 0 && r < a.A.nslots, 35, r)) continue;
+    const int slots = max(64, min(WARP_SLOTS, next_pow2(2 * (int)a.f[r])));
+    for (int s = lane; s < slots; s += 32) keys[s] = EMPTY;
+    __syncwarp();
+    int cnt = 0;
+    const unsigned mask = slots - 1;
+    warp_products<StructSR>(A, B, A.p[r], A.p[r + 1],
+                            [&](int col, NoVal, int) { cnt += hash_insert_key(keys, mask, col); });
+    cnt = warp_sum(cnt);
+    if (lane == 0) put_count(a, out_row(a.A, r), cnt);
+    __syncwarp();
+  }
+}
+
+// ----------------------------------------------------------- mid / large
+constexpr int CH = 1024;  // A entries per expansion round
+
+template <int SLOTS, bool HIST> struct SymCtaSmem {
+  int keys[SLOTS];
+  CtaExpandSmem<NoVal, CH> ex;
+  int wtmp[33];
+  int total;
+};
+
+template <int SLOTS, bool HIST>
+__global__ void __launch_bounds__(HIST ? 512 : 256) k_sym_cta(SymArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto &sm = *reinterpret_cast<SymCtaSmem<SLOTS, HIST> *>(smem_raw);
+  const DevCsr A = dev_a(a.A), B = dev_b(a.B);
+  for (int idx = blockIdx.x; idx < a.count; idx += gridDim.x) {
+    const int r = a.list[idx];
+    if (!HS_G(a.A.dbg, r >= 0 && r < a.A.nslots, 35, r)) continue;
+    const int slots = max(64, min(SLOTS, next_pow2(2 * (int)a.f[r])));
+    const unsigned mask = slots - 1;
+    for (int s = threadIdx.x; s < slots; s += blockDim.x) sm.keys[s] = EMPTY;
+    if (threadIdx.x == 0) sm.total = 0;
+    __syncthreads();
+    int cnt = 0;
+    cta_products<StructSR, CH>(A, B, A.p[r], A.p[r + 1], false, 0, 0, sm.ex, sm.wtmp,
+                               [&](int col, NoVal, int) { cnt += hash_insert_key(sm.keys, mask, col); });
+    cnt = warp_sum(cnt);
+    if (lane_id() == 0 && cnt) atomicAdd(&sm.total, cnt);
+    if (HIST) {
+      const int h = a.hslot[r];
+      if (h >= 0) {
+        uint32_t *hist = a.hist + (int64_t)h * a.nseg;
+        for (int s = threadIdx.x; s < slots; s += blockDim.x) {
+          const int k = sm.keys[s];
+          if (k != EMPTY && HS_G(a.A.dbg, k / SEG_W < a.nseg, 31, k)) atomicAdd(hist + k / SEG_W, 1u);
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) put_count(a, out_row(a.A, r), sm.total);
+    __syncthreads();
+  }
+}
+
+// --------------------------------------------------------------- heavy
+struct SymHeavySmem {
+  CtaExpandSmem<NoVal, CH> ex;
+  int wtmp[33];
+  int total;
+  int row;
+  unsigned bitmap[BITMAP_COLS / 32];
+};
+
+__global__ void __launch_bounds__(1024) k_sym_heavy(SymArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto &sm = *reinterpret_cast<SymHeavySmem *>(smem_raw);
+  const DevCsr A = dev_a(a.A), B = dev_b(a.B);
+  const int64_t n = a.B.n;
+  const int nchunk = (int)((n + BITMAP_COLS - 1) / BITMAP_COLS);
+  const int lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  while (true) {
+    if (threadIdx.x == 0) {
+      sm.row = atomicAdd(a.dyn, 1);
+      sm.total = 0;
+    }
+    __syncthreads();
+    const int idx = sm.row;
+    if (idx >= a.count) break;
+    const int r0 = a.list[idx];
+    // a bad row id (guarded builds) runs no chunk, so the loop still reaches its closing barriers
+    const bool r_ok = HS_G(a.A.dbg, r0 >= 0 && r0 < a.A.nslots, 35, r0);
+    const int r = r_ok ? r0 : 0;
+    const int h = r_ok ? a.hslot[r] : -1;
+    uint32_t *hist = h >= 0 ? a.hist + (int64_t)h * a.nseg : nullptr;
+    int cnt = 0;
+    for (int ch = 0; ch < (r_ok ? nchunk : 0); ++ch) {
+      const int lo = ch * BITMAP_COLS;
+      const int hi = (int)min((int64_t)lo + BITMAP_COLS, n);
+      const int words = (hi - lo + 31) >> 5;
+      for (int wd = threadIdx.x; wd < words; wd += blockDim.x) sm.bitmap[wd] = 0u;
+      __syncthreads();
+      cta_products<StructSR, CH>(A, B, A.p[r], A.p[r + 1], nchunk > 1, lo, hi, sm.ex, sm.wtmp,
+                                 [&](int col, NoVal, int) {
+                                   const int x = col - lo;
+                                   if (HS_G(a.A.dbg, x >= 0 && x < hi - lo, 33, col))
+                                     atomicOr(sm.bitmap + (x >> 5), 1u << (x & 31));
+                                 });
+      // count: each warp takes 32 consecutive words (1024 columns, inside one segment)
+      for (int wb = warp * 32; wb < words; wb += nw * 32) {
+        const int wd = wb + lane;
+        int c = wd < words ? __popc(sm.bitmap[wd]) : 0;
+        c = warp_sum(c);
+        if (lane == 0 && c) {
+          cnt += c;
+          if (hist && HS_G(a.A.dbg, (lo + wb * 32) / SEG_W < a.nseg, 32, wb)) atomicAdd(hist + (lo + wb * 32) / SEG_W, (uint32_t)c);
+        }
+      }
+      __syncthreads();
+    }
+    if (lane == 0 && cnt) atomicAdd(&sm.total, cnt);
+    __syncthreads();
+    if (threadIdx.x == 0 && r_ok) put_count(a, out_row(a.A, r), sm.total);
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------- launchers
+static int grid_cap(int items, int per_block, int per_sm) {
+  int g = (items + per_block - 1) / per_block;
+  int cap = sm_count() * per_sm;
+  return g < cap ? (g < 1 ? 1 : g) : cap;
+}
+
+void launch_sym_tiny(const SymArgs &a, cudaStream_t st) {
+  if (a.count <= 0) return;
+  count_launch();
+  k_sym_tiny<<<grid_cap(a.count, TINY_WPB, 8), TINY_WPB * 32, 0, st>>>(a);
+}
+void launch_sym_warp(const SymArgs &a, cudaStream_t st) {
+  if (a.count <= 0) return;
+  count_launch();
+  k_sym_warp<<<grid_cap(a.count, WARP_WPB, 6), WARP_WPB * 32, 0, st>>>(a);
+}
+
+template <int SLOTS, bool HIST> static void launch_sym_cta(const SymArgs &a, int nt, int per_sm, cudaStream_t st) {
+  if (a.count <= 0) return;
+  const size_t bytes = sizeof(SymCtaSmem<SLOTS, HIST>);
+  set_smem_attr(k_sym_cta<SLOTS, HIST>, bytes);
+  count_launch();
+  k_sym_cta<SLOTS, HIST><<<grid_cap(a.count, 1, per_sm), nt, bytes, st>>>(a);
+}
+void launch_sym_mid(const SymArgs &a, cudaStream_t st) { launch_sym_cta<8192, false>(a, 256, 4, st); }
+void launch_sym_large(const SymArgs &a, cudaStream_t st) { launch_sym_cta<32768, true>(a, 512, 1, st); }
+
+void launch_sym_heavy(const SymArgs &a, cudaStream_t st) {
+  if (a.count <= 0) return;
+  const int64_t words = (a.B.n + 31) / 32;
+  const size_t bytes = offsetof(SymHeavySmem, bitmap) +
+                       sizeof(unsigned) * (size_t)(words < BITMAP_COLS / 32 ? words : BITMAP_COLS / 32);
+  set_smem_attr(k_sym_heavy, sizeof(SymHeavySmem));
+  count_launch();
+  k_sym_heavy<<<grid_cap(a.count, 1, 1), 1024, bytes, st>>>(a);
+}
+
+}  // namespace hs

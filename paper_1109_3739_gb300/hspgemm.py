@@ -1,0 +1,290 @@
+"""Python binding of libhspgemm (the C ABI in include/hspgemm.h).
+
+Argument marshalling only: every step of SpGEMM / SpRef / SpAsgn runs in the
+library's CUDA kernels.  PyTorch supplies device memory (through the ABI's
+allocator callbacks, backed by the caching allocator) and the stream.  There
+is no fallback: if the library is not built, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhspgemm.so")
+
+SEMIRING = {"plus_times": 0, "or_and": 1, "min_plus": 2, "select2nd": 3, "select1st": 4}
+DTYPE = {"f64": 0, "f32": 1, "i32": 2, "i64": 3, "bool": 4}
+DTYPE_NAME = {v: k for k, v in DTYPE.items()}
+VBYTES = {"f64": 8, "f32": 4, "i32": 4, "i64": 8, "bool": 0}
+FLAG_VALIDATE = 1
+STATUS = {0: "HS_OK", -1: "HS_EINVAL", -2: "HS_ENONCANON", -3: "HS_EDUP", -4: "HS_ENOMEM",
+          -5: "HS_ETIMEDOUT", -6: "HS_ECUDA", -7: "HS_EUNSUPPORTED", -8: "HS_EINTERNAL"}
+
+
+class HsError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        L = _lib()
+        detail = L.hs_last_error_detail().decode()
+        super().__init__(f"{what}: {STATUS.get(code, code)} ({L.hs_strerror(code).decode()})"
+                         + (f" [{detail}]" if detail else ""))
+
+
+class hs_mat(ctypes.Structure):
+    _fields_ = [("fmt", ctypes.c_int32), ("dtype", ctypes.c_int32), ("m", ctypes.c_int64),
+                ("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("nzr", ctypes.c_int64),
+                ("ptr", ctypes.c_void_p), ("idx", ctypes.c_void_p), ("ids", ctypes.c_void_p),
+                ("val", ctypes.c_void_p)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class hs_allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
+_lock = threading.Lock()
+_L = None
+
+
+def _lib():
+    global _L
+    if _L is not None:
+        return _L
+    with _lock:
+        if _L is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1109_3739_gb300.build.build()")
+            # torch first: its CUDA runtime must be the one the library binds to
+            # (libhspgemm needs libcudart.so.13; if the system copy were loaded
+            # first, torch would map a second runtime into the process)
+            _torch()
+            L = ctypes.CDLL(LIB_PATH)
+            P = ctypes.POINTER
+            vp, i64, ci, u32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint32
+            L.hs_spgemm.argtypes = [ci, P(hs_mat), P(hs_mat), P(hs_mat), P(hs_allocator), vp, u32]
+            L.hs_spgemm.restype = ci
+            L.hs_spref.argtypes = [P(hs_mat), vp, i64, vp, i64, P(hs_mat), P(hs_allocator), vp, u32]
+            L.hs_spref.restype = ci
+            L.hs_spasgn.argtypes = [P(hs_mat), vp, i64, vp, i64, P(hs_mat), ci, ci, P(hs_mat),
+                                    P(hs_allocator), vp, u32]
+            L.hs_spasgn.restype = ci
+            L.hs_mat_free.argtypes = [P(hs_mat), P(hs_allocator), vp]
+            L.hs_mat_free.restype = None
+            L.hs_strerror.argtypes = [ci]
+            L.hs_strerror.restype = ctypes.c_char_p
+            L.hs_last_cuda_error.restype = ci
+            L.hs_last_error_detail.restype = ctypes.c_char_p
+            L.hs_version.restype = ci
+            L.hs_launch_count.restype = ctypes.c_int64
+            L.hs_profile_enable.argtypes = [ci]
+            L.hs_profile_reset.argtypes = []
+            L.hs_profile_read.argtypes = [P(ctypes.c_double), P(ctypes.c_int64), P(ctypes.c_char_p), ci]
+            L.hs_profile_read.restype = ci
+            _L = L
+    return _L
+
+
+def library():
+    """The loaded ctypes library (raises if it has not been built)."""
+    return _lib()
+
+
+def _torch():
+    import torch
+    return torch
+
+
+# ------------------------------------------------------------------ memory
+class _TorchAlloc:
+    """Allocator callbacks backed by torch's caching allocator.
+
+    Each allocation is a uint8 tensor kept alive in a dict keyed by its device
+    address until the library frees it or the binding adopts it as an output.
+    """
+
+    def __init__(self, device):
+        self.device = device
+        self.live: dict[int, object] = {}
+        self._a = ALLOC_FN(self._alloc)
+        self._f = FREE_FN(self._free)
+        self.struct = hs_allocator(self._a, self._f, None)
+
+    def _alloc(self, nbytes, stream, ctx):
+        try:
+            t = _torch().empty(int(nbytes), dtype=_torch().uint8, device=self.device)
+        except Exception:
+            return None
+        p = t.data_ptr()
+        self.live[p] = t
+        return p
+
+    def _free(self, ptr, nbytes, stream, ctx):
+        self.live.pop(int(ptr) if ptr else 0, None)
+
+    def adopt(self, ptr, count, dtype):
+        """Take ownership of a library output as a typed tensor of `count` elements."""
+        t = self.live.pop(int(ptr))
+        return t.view(dtype)[:count]
+
+
+class DeviceCSR:
+    """A CSR (or DCSR) matrix in device memory: torch tensors + shape + dtype name."""
+
+    def __init__(self, m, n, rowptr, col, val, dtype, ids=None):
+        self.m, self.n = int(m), int(n)
+        self.rowptr, self.col, self.val, self.dtype, self.ids = rowptr, col, val, dtype, ids
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.numel())
+
+    @property
+    def fmt(self) -> str:
+        return "dcsr" if self.ids is not None else "csr"
+
+    @classmethod
+    def from_host(cls, A, device="cuda", dcsr: bool = False, non_blocking: bool = False):
+        """Copy an inputs.CSR (numpy) to the device; dcsr=True stores only non-empty rows."""
+        torch = _torch()
+        rowptr = np.asarray(A.rowptr, np.int64)
+        ids = None
+        if dcsr:
+            nz = np.nonzero(np.diff(rowptr))[0]
+            ids = torch.from_numpy(nz.astype(np.int32)).to(device, non_blocking=non_blocking)
+            rowptr = np.concatenate([rowptr[nz], rowptr[-1:]])
+        val = None if A.val is None else torch.from_numpy(np.ascontiguousarray(A.val)).to(device, non_blocking=non_blocking)
+        return cls(A.m, A.n, torch.from_numpy(rowptr).to(device, non_blocking=non_blocking),
+                   torch.from_numpy(np.asarray(A.col, np.int32)).to(device, non_blocking=non_blocking),
+                   val, A.dtype if A.val is not None else "bool", ids)
+
+    def to_host(self):
+        """inputs.CSR copy on the host (CSR form)."""
+        from .inputs import CSR
+        rp = self.rowptr.cpu().numpy()
+        col = self.col.cpu().numpy()
+        val = None if self.val is None else self.val.cpu().numpy()
+        if self.ids is not None:
+            full = np.zeros(self.m + 1, np.int64)
+            ids = self.ids.cpu().numpy()
+            counts = np.zeros(self.m, np.int64)
+            counts[ids] = np.diff(rp)
+            np.cumsum(counts, out=full[1:])
+            rp = full
+        return CSR(self.m, self.n, rp, col, val, self.dtype)
+
+    def desc(self) -> hs_mat:
+        nzr = 0 if self.ids is None else int(self.ids.numel())
+        return hs_mat(1 if self.ids is not None else 0, DTYPE[self.dtype], self.m, self.n, self.nnz, nzr,
+                      self.rowptr.data_ptr(), self.col.data_ptr(),
+                      None if self.ids is None else self.ids.data_ptr(),
+                      None if self.val is None else self.val.data_ptr())
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def _adopt_output(al: _TorchAlloc, C: hs_mat) -> DeviceCSR:
+    torch = _torch()
+    dt = DTYPE_NAME[C.dtype]
+    rowptr = al.adopt(C.ptr, C.m + 1, torch.int64)
+    col = al.adopt(C.idx, C.nnz, torch.int32)
+    val = None
+    if dt != "bool":
+        tdt = {"f64": torch.float64, "f32": torch.float32, "i32": torch.int32, "i64": torch.int64}[dt]
+        val = al.adopt(C.val, C.nnz, tdt) if C.val else torch.empty(0, dtype=tdt, device=rowptr.device)
+    return DeviceCSR(C.m, C.n, rowptr, col, val, dt)
+
+
+def _device_of(A: DeviceCSR):
+    return A.rowptr.device
+
+
+# -------------------------------------------------------------- operations
+def spgemm(semiring: str, A: DeviceCSR, B: DeviceCSR, validate: bool = False, stream=None) -> DeviceCSR:
+    """C = A*B over `semiring` (hs_spgemm)."""
+    L = _lib()
+    al = _TorchAlloc(_device_of(A))
+    a, b, c = A.desc(), B.desc(), hs_mat()
+    st = L.hs_spgemm(SEMIRING[semiring], ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                     ctypes.byref(al.struct), _stream_ptr(stream), FLAG_VALIDATE if validate else 0)
+    if st != 0:
+        raise HsError(st, "hs_spgemm")
+    return _adopt_output(al, c)
+
+
+def _idx(x, device):
+    torch = _torch()
+    if isinstance(x, torch.Tensor):
+        return x.to(device=device, dtype=torch.int32).contiguous()
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(x, np.int32))).to(device)
+
+
+def spref(A: DeviceCSR, I, J, validate: bool = False, stream=None) -> DeviceCSR:
+    """B = A(I, J) (hs_spref)."""
+    L = _lib()
+    dev = _device_of(A)
+    It, Jt = _idx(I, dev), _idx(J, dev)
+    al = _TorchAlloc(dev)
+    a, b = A.desc(), hs_mat()
+    st = L.hs_spref(ctypes.byref(a), It.data_ptr() if It.numel() else None, It.numel(),
+                    Jt.data_ptr() if Jt.numel() else None, Jt.numel(), ctypes.byref(b),
+                    ctypes.byref(al.struct), _stream_ptr(stream), FLAG_VALIDATE if validate else 0)
+    if st != 0:
+        raise HsError(st, "hs_spref")
+    return _adopt_output(al, b)
+
+
+def spasgn(A: DeviceCSR, I, J, B: DeviceCSR, accumulate: bool = False, add: str = "plus_times",
+           validate: bool = False, stream=None) -> DeviceCSR:
+    """C = A with A(I,J) = B, or A(I,J) += B with accumulate (hs_spasgn)."""
+    L = _lib()
+    dev = _device_of(A)
+    It, Jt = _idx(I, dev), _idx(J, dev)
+    al = _TorchAlloc(dev)
+    a, b, c = A.desc(), B.desc(), hs_mat()
+    st = L.hs_spasgn(ctypes.byref(a), It.data_ptr() if It.numel() else None, It.numel(),
+                     Jt.data_ptr() if Jt.numel() else None, Jt.numel(), ctypes.byref(b), int(accumulate),
+                     SEMIRING[add], ctypes.byref(c), ctypes.byref(al.struct), _stream_ptr(stream),
+                     FLAG_VALIDATE if validate else 0)
+    if st != 0:
+        raise HsError(st, "hs_spasgn")
+    return _adopt_output(al, c)
+
+
+# --------------------------------------------------------------- profiling
+def profile_enable(on: bool = True):
+    _lib().hs_profile_enable(1 if on else 0)
+
+
+def profile_reset():
+    _lib().hs_profile_reset()
+
+
+def profile_read() -> dict:
+    """{phase: (total ms, launches)} accumulated since the last reset."""
+    L = _lib()
+    cap = 64
+    ms = (ctypes.c_double * cap)()
+    ln = (ctypes.c_int64 * cap)()
+    nm = (ctypes.c_char_p * cap)()
+    n = L.hs_profile_read(ms, ln, nm, cap)
+    return {nm[i].decode(): (ms[i], ln[i]) for i in range(min(n, cap))}
+
+
+def version() -> int:
+    return _lib().hs_version()
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(_lib().hs_launch_count())

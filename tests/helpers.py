@@ -77,3 +77,29 @@ def assert_within(C, R, bound, dtype, what=""):
     bad = np.nonzero(err > lim)[0]
     assert len(bad) == 0, (f"{what}: {len(bad)} entries outside tolerance; worst ratio "
                            f"{(err / np.maximum(lim, 1e-300)).max():.3g} at {bad[:5]}")
+
+
+def rand_sparse(m, n, density, seed, dtype, kind="signed"):
+    """Random pattern with each entry present with the given probability."""
+    u = I.uniform_f64(I.draws(seed, 11, 0, m * n)).reshape(m, n) if m * n else np.zeros((m, n))
+    P = u < density
+    vals = I.random_values(m * n, dtype, seed, stream=12, kind=kind)
+    D = np.zeros((m, n)) if vals is None else vals.reshape(m, n)
+    return from_dense(D, dtype, pattern=P)
+
+
+def rows_of(C, rows):
+    """CSR of the listed rows of C (host arrays)."""
+    rp = np.asarray(C.rowptr)
+    parts_j, parts_v, counts = [], [], []
+    for r in rows:
+        a, b = int(rp[r]), int(rp[r + 1])
+        parts_j.append(np.asarray(C.col[a:b]))
+        if C.val is not None:
+            parts_v.append(np.asarray(C.val[a:b]))
+        counts.append(b - a)
+    rowptr = np.zeros(len(rows) + 1, np.int64)
+    np.cumsum(counts, out=rowptr[1:])
+    col = np.concatenate(parts_j) if parts_j else np.zeros(0, np.int32)
+    val = None if C.val is None else (np.concatenate(parts_v) if parts_v else np.zeros(0))
+    return I.CSR(len(rows), C.n, rowptr, col.astype(np.int32), val, C.dtype)
