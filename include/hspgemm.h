@@ -95,6 +95,9 @@ typedef struct hs_allocator {
 #define HS_ECUDA -6        /* CUDA runtime error (see hs_last_cuda_error)      */
 #define HS_EUNSUPPORTED -7 /* valid request this build does not implement    */
 #define HS_EINTERNAL -8    /* device-side consistency check failed            */
+#define HS_ESCRATCH -9     /* hs_spgemm_noalloc: the product needs more scratch
+                              than HS_NOALLOC_SCRATCH_MAX bytes                */
+#define HS_ECAPACITY -10   /* hs_spgemm_noalloc: output capacity too small     */
 
 /* Flags. */
 #define HS_FLAG_VALIDATE 1u /* check canonical inputs and index ranges */
@@ -134,6 +137,34 @@ int hs_spref(const hs_mat *A, const int32_t *I, int64_t nI, const int32_t *J, in
 int hs_spasgn(const hs_mat *A, const int32_t *I, int64_t nI, const int32_t *J, int64_t nJ,
               const hs_mat *B, int accumulate, int add_semiring, hs_mat *C,
               const hs_allocator *al, void *stream, uint32_t flags);
+
+/* SpGEMM for callers that cannot allocate device memory while they run (the
+ * paper has no counterpart): for example code that has given the GPU's memory
+ * to its own pool and must keep its footprint fixed, or code running where a
+ * cudaMalloc is not allowed.  Same operation, semirings, dtypes and results
+ * as hs_spgemm, but this call allocates nothing: the caller passes C with
+ * C->ptr (A->m + 1 int64), C->idx (capacity int32) and, for typed results,
+ * C->val (capacity values) already allocated on the device.  The call fills
+ * C->ptr, C->idx, C->val and sets C's shape, dtype and nnz.  Temporaries come
+ * from one fixed device array of HS_NOALLOC_SCRATCH_MAX bytes inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits; host-side readbacks use ordinary host memory.
+ *   - HS_ESCRATCH: the product needs more scratch than the maximum (roughly
+ *     16 bytes per row of A plus 4 bytes per 4096 columns for every row with
+ *     more than 4096 products); nothing is written but C->ptr.
+ *   - HS_ECAPACITY: nnz(C) > capacity; C->ptr is complete and C->nnz holds
+ *     the capacity needed, so the caller can provide larger arrays and call
+ *     again.  C->idx and C->val are not touched.
+ * The first call on a device looks up the fixed array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call shares the array and leaves its
+ * contents behind; each call clears what must start at zero.  Calls that
+ * overlap on the GPU (two streams or two host threads on one device) race on
+ * the array and must be serialised by the caller.  The call synchronises
+ * with `stream` three times (sizes, nnz(C), final error check). */
+#define HS_NOALLOC_SCRATCH_MAX (32u * 1024u * 1024u)
+int hs_spgemm_noalloc(int semiring, const hs_mat *A, const hs_mat *B, hs_mat *C, int64_t capacity,
+                      void *stream);
 
 /* Releases the arrays of a matrix produced by this library through `al` (the
  * allocator it was produced with) and zeroes the descriptor. */

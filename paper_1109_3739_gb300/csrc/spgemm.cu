@@ -640,6 +640,8 @@ const char *hs_strerror(int s) {
     case HS_ECUDA: return "CUDA runtime error";
     case HS_EUNSUPPORTED: return "unsupported request";
     case HS_EINTERNAL: return "internal consistency check failed";
+    case HS_ESCRATCH: return "product needs more scratch than the no-allocation entry point's fixed array";
+    case HS_ECAPACITY: return "output capacity too small (C->nnz holds the size needed)";
   }
   return "unknown status";
 }

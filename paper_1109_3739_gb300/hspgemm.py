@@ -22,7 +22,8 @@ DTYPE_NAME = {v: k for k, v in DTYPE.items()}
 VBYTES = {"f64": 8, "f32": 4, "i32": 4, "i64": 8, "bool": 0}
 FLAG_VALIDATE = 1
 STATUS = {0: "HS_OK", -1: "HS_EINVAL", -2: "HS_ENONCANON", -3: "HS_EDUP", -4: "HS_ENOMEM",
-          -5: "HS_ETIMEDOUT", -6: "HS_ECUDA", -7: "HS_EUNSUPPORTED", -8: "HS_EINTERNAL"}
+          -5: "HS_ETIMEDOUT", -6: "HS_ECUDA", -7: "HS_EUNSUPPORTED", -8: "HS_EINTERNAL",
+          -9: "HS_ESCRATCH", -10: "HS_ECAPACITY"}
 
 
 class HsError(RuntimeError):
@@ -75,6 +76,8 @@ def _lib():
             L.hs_spasgn.argtypes = [P(hs_mat), vp, i64, vp, i64, P(hs_mat), ci, ci, P(hs_mat),
                                     P(hs_allocator), vp, u32]
             L.hs_spasgn.restype = ci
+            L.hs_spgemm_noalloc.argtypes = [ci, P(hs_mat), P(hs_mat), P(hs_mat), i64, vp]
+            L.hs_spgemm_noalloc.restype = ci
             L.hs_mat_free.argtypes = [P(hs_mat), P(hs_allocator), vp]
             L.hs_mat_free.restype = None
             L.hs_strerror.argtypes = [ci]
@@ -220,6 +223,35 @@ def spgemm(semiring: str, A: DeviceCSR, B: DeviceCSR, validate: bool = False, st
     if st != 0:
         raise HsError(st, "hs_spgemm")
     return _adopt_output(al, c)
+
+
+def spgemm_noalloc(semiring: str, A: DeviceCSR, B: DeviceCSR, capacity: int, stream=None) -> DeviceCSR:
+    """C = A*B through hs_spgemm_noalloc: the library allocates nothing.
+
+    The output arrays are allocated here, by the caller (torch), with room
+    for `capacity` entries; the library takes every temporary from its fixed
+    scratch array.  Raises HsError (HS_ECAPACITY, with .nnz_needed) when
+    nnz(C) exceeds capacity.
+    """
+    torch = _torch()
+    L = _lib()
+    dev = _device_of(A)
+    out_dt = "bool" if semiring == "or_and" else (B.dtype if semiring == "select2nd" else A.dtype)
+    tdt = {"f64": torch.float64, "f32": torch.float32, "i32": torch.int32, "i64": torch.int64}.get(out_dt)
+    rowptr = torch.empty(A.m + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev)
+    val = None if tdt is None else torch.empty(max(capacity, 1), dtype=tdt, device=dev)
+    a, b = A.desc(), B.desc()
+    c = hs_mat(0, 0, 0, 0, 0, 0, rowptr.data_ptr(), col.data_ptr(), None,
+               None if val is None else val.data_ptr())
+    st = L.hs_spgemm_noalloc(SEMIRING[semiring], ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                             int(capacity), _stream_ptr(stream))
+    if st != 0:
+        err = HsError(st, "hs_spgemm_noalloc")
+        err.nnz_needed = int(c.nnz)
+        raise err
+    nnz = int(c.nnz)
+    return DeviceCSR(c.m, c.n, rowptr, col[:nnz], None if val is None else val[:nnz], DTYPE_NAME[c.dtype])
 
 
 def _idx(x, device):
