@@ -150,8 +150,10 @@ int hs_spasgn(const hs_mat *A, const int32_t *I, int64_t nI, const int32_t *J, i
  * library, which every GPU that loads the library holds until the process
  * exits; host-side readbacks use ordinary host memory.
  *   - HS_ESCRATCH: the product needs more scratch than the maximum (roughly
- *     16 bytes per row of A plus 4 bytes per 4096 columns for every row with
- *     more than 4096 products); nothing is written but C->ptr.
+ *     16 bytes per row of A, plus 4 bytes per 4096 columns for every row with
+ *     more than 4096 (8-byte values) or 8192 (other types) products and 8
+ *     bytes per entry of A when such rows exist); nothing is written but
+ *     C->ptr.
  *   - HS_ECAPACITY: nnz(C) > capacity; C->ptr is complete and C->nnz holds
  *     the capacity needed, so the caller can provide larger arrays and call
  *     again.  C->idx and C->val are not touched.

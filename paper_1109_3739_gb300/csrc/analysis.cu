@@ -120,14 +120,15 @@ __device__ __forceinline__ void append_row(int key, int r, int *key_cur, int *li
   if (HS_G(dbg, at >= 0 && at < cap, 52, at)) list[at] = r;
 }
 
-__global__ void k_scatter_sym(RowSet A, const int64_t *f, int *key_cur, int *list, int32_t *hslot, int *nhist) {
+__global__ void k_scatter_sym(RowSet A, const int64_t *f, int *key_cur, int *list, int32_t *hslot, int *nhist,
+                              int hist_threshold) {
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < A.nslots;
        r += (int64_t)gridDim.x * blockDim.x) {
     const int64_t fr = f[r];
     const int key = sym_key(fr);
     if (key) append_row(key, (int)r, key_cur, list, A.nslots, A.dbg);
     // rows that may need column parts in the numeric pass get a histogram slot
-    const bool h = fr > SEG_W;
+    const bool h = fr > hist_threshold;
     const unsigned act = __activemask();
     const unsigned hm = __ballot_sync(act, h);
     int base = 0;
@@ -139,10 +140,10 @@ __global__ void k_scatter_sym(RowSet A, const int64_t *f, int *key_cur, int *lis
 }
 
 void launch_scatter_sym(const RowSet &A, const int64_t *f, int *key_cur, int *list, int32_t *hslot, int *nhist,
-                        cudaStream_t st) {
+                        int hist_threshold, cudaStream_t st) {
   if (A.nslots == 0) return;
   count_launch();
-  k_scatter_sym<<<grid_for(A.nslots, 256, 8), 256, 0, st>>>(A, f, key_cur, list, hslot, nhist);
+  k_scatter_sym<<<grid_for(A.nslots, 256, 8), 256, 0, st>>>(A, f, key_cur, list, hslot, nhist, hist_threshold);
 }
 
 __device__ __forceinline__ int64_t out_count(const RowSet &A, const int64_t *Cp, int64_t r) {

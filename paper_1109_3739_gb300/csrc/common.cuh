@@ -311,6 +311,66 @@ template <typename T, int CH> struct CtaExpandSmem {
   T aval[CH];
 };
 
+// The products of n staged B-row segments (start sbeg[e], exclusive length
+// prefix excl[e], excl[n] = total, left values aval[e]) spread evenly over
+// the warps of the CTA: each warp takes one contiguous range of the products
+// and deals it one product per lane (warp_expand).  Reads the staged arrays
+// only; all threads of the CTA must call it together.
+template <class SR, class Visit>
+__device__ __forceinline__ void cta_expand_staged(const DevCsr &B, const int64_t *sbeg, const int *excl,
+                                                  const typename SR::val_t *aval, int n, int total,
+                                                  Visit &visit) {
+  using T = typename SR::val_t;
+  const int lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int pb = (int)(((int64_t)total * warp) / nw);
+  const int pe = (int)(((int64_t)total * (warp + 1)) / nw);
+  if (pb >= pe) return;
+  // last entry whose exclusive start is <= pb
+  int l = 0, h = n;
+  while (l < h) {
+    const int mid = (l + h) >> 1;
+    if (excl[mid] <= pb) l = mid + 1;
+    else h = mid;
+  }
+  for (int eb = l - 1; eb < n; eb += 32) {
+    const int e = eb + lane;
+    int64_t s = 0;
+    int len = 0;
+    T a{};
+    if (e < n) {
+      const int x0 = excl[e], x1 = excl[e + 1];
+      const int cb = max(x0, pb), ce = min(x1, pe);
+      if (ce > cb) {
+        len = ce - cb;
+        s = sbeg[e] + (cb - x0);
+        if constexpr (SR::needs_a) a = aval[e];
+      }
+    }
+    warp_expand<SR>(B, s, len, a, visit);
+    if (eb + 32 >= n || excl[eb + 32] >= pe) break;
+  }
+}
+
+// First position in [s, e) whose column is >= x: probe s, s+1, s+3, s+7, ...
+// (galloping) and finish with a binary search, so a short distance costs few
+// loads whatever the row's length.
+__device__ __forceinline__ int64_t gallop_lower_bound(const int32_t *j, int64_t s, int64_t e, int x) {
+  if (s >= e || __ldg(j + s) >= x) return s;
+  int64_t lo = s + 1, step = 1, hi = s + 1;
+  while (hi < e && __ldg(j + hi) < x) {
+    lo = hi + 1;
+    step <<= 1;
+    hi = s + step;
+  }
+  if (hi > e) hi = e;
+  while (lo < hi) {
+    const int64_t mid = lo + ((hi - lo) >> 1);
+    if (__ldg(j + mid) < x) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
 // Every product of one row (or of the part of it inside columns [lo, hi)),
 // spread evenly over the warps of the CTA.  A entries are taken CH at a time;
 // their B segments' lengths are scanned across the CTA, the products of the
@@ -322,7 +382,7 @@ __device__ void cta_products(const DevCsr &A, const DevCsr &B, int64_t q0, int64
                              int lo, int hi, CtaExpandSmem<typename SR::val_t, CH> &sm, int *wtmp,
                              Visit &&visit) {
   using T = typename SR::val_t;
-  const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5, nw = blockDim.x >> 5;
+  const int tid = threadIdx.x;
   for (int64_t c0 = q0; c0 < q1; c0 += CH) {
     const int n = (int)min((int64_t)CH, q1 - c0);
     for (int e = tid; e < CH; e += blockDim.x) {
@@ -338,34 +398,7 @@ __device__ void cta_products(const DevCsr &A, const DevCsr &B, int64_t q0, int64
     const int total = group_excl_scan<CtaGroup>(sm.excl, CH, wtmp);
     if (tid == 0) sm.excl[CH] = total;
     __syncthreads();
-    const int pb = (int)(((int64_t)total * warp) / nw);
-    const int pe = (int)(((int64_t)total * (warp + 1)) / nw);
-    if (pb < pe) {
-      // last entry whose exclusive start is <= pb
-      int l = 0, h = n;
-      while (l < h) {
-        const int mid = (l + h) >> 1;
-        if (sm.excl[mid] <= pb) l = mid + 1;
-        else h = mid;
-      }
-      for (int eb = l - 1; eb < n; eb += 32) {
-        const int e = eb + lane;
-        int64_t s = 0;
-        int len = 0;
-        T a{};
-        if (e < n) {
-          const int x0 = sm.excl[e], x1 = sm.excl[e + 1];
-          const int cb = max(x0, pb), ce = min(x1, pe);
-          if (ce > cb) {
-            len = ce - cb;
-            s = sm.sbeg[e] + (cb - x0);
-            if constexpr (SR::needs_a) a = sm.aval[e];
-          }
-        }
-        warp_expand<SR>(B, s, len, a, visit);
-        if (eb + 32 >= n || sm.excl[eb + 32] >= pe) break;
-      }
-    }
+    cta_expand_staged<SR>(B, sm.sbeg, sm.excl, sm.aval, n, total, visit);
     __syncthreads();
   }
 }

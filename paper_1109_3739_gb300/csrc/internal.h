@@ -23,6 +23,7 @@ constexpr int CAP_MID = 2048;
 // (a multiple of 1024, at most every numeric table's capacity).
 constexpr int SEG_W = 4096;
 constexpr int BITMAP_COLS = 1 << 20;  // columns covered by the heavy symbolic bitmap
+constexpr int SEG_SMEM = 1024;        // segment counters kept in shared memory when nseg <= this
 
 __host__ __device__ inline int floor_log2_u64(uint64_t x) {
 #ifdef __CUDA_ARCH__
@@ -87,8 +88,9 @@ template <class K> inline void set_smem_attr(K kernel, size_t bytes) {
 void launch_flops(const RowSet &A, const RightOp &B, int64_t *f, int *key_cnt, unsigned long long *stats,
                   cudaStream_t st);
 void launch_key_offsets(const int *key_cnt, int *key_off, int *key_cur, cudaStream_t st);
+// rows with more than hist_threshold products get a column-segment histogram slot
 void launch_scatter_sym(const RowSet &A, const int64_t *f, int *key_cur, int *list, int32_t *hslot,
-                        int *nhist, cudaStream_t st);
+                        int *nhist, int hist_threshold, cudaStream_t st);
 void launch_num_count(const RowSet &A, const int64_t *f, const int64_t *Cp, int cap_large, int *key_cnt,
                       cudaStream_t st);
 void launch_scatter_num(const RowSet &A, const int64_t *f, const int64_t *Cp, int cap_large, int *key_cur,
@@ -134,6 +136,8 @@ struct NumArgs {
   int nseg;
   int *dyn;
   int *err;
+  int32_t *gcur;  // heavy bin: per-A-entry cursor into its B row (nnz(A) entries)
+  int32_t *gend;  // heavy bin: end of the current part's segment
 };
 // kind: 0 tiny, 1 warp, 2 mid, 3 large, 4 heavy.  dtype codes as in the ABI.
 bool launch_numeric_pt(int dtype, int kind, const NumArgs &a, cudaStream_t st);

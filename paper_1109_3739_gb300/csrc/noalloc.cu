@@ -184,7 +184,7 @@ static int spgemm_noalloc_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat 
   NA_CK(cudaMemsetAsync(sb, 0, sizeof(NaBlock), st));
   launch_flops(rs, rb, f, sb->key_cnt, sb->stats, st);
   launch_key_offsets(sb->key_cnt, sb->key_off, sb->key_cur, st);
-  launch_scatter_sym(rs, f, sb->key_cur, list, hslot, &sb->nhist, st);
+  launch_scatter_sym(rs, f, sb->key_cur, list, hslot, &sb->nhist, vb == 8 ? 4096 : 8192, st);
   if (int e = check_last()) return e;
   NA_CK(cudaMemcpyAsync(&hb, sb, sizeof(NaBlock), cudaMemcpyDeviceToHost, st));
   NA_CK(cudaStreamSynchronize(st));
@@ -232,7 +232,13 @@ static int spgemm_noalloc_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat 
   if (hb.nnz > capacity) return HS_ECAPACITY;  // C->ptr is complete, C->nnz is the size needed
   memcpy(key_off, hb.key_off, sizeof(key_off));
 
-  NumArgs na{rs, rb, f, nullptr, 0, Cp, C->idx, C->val, hslot, hist, nseg, &sb->dyn[1], &sb->err};
+  int32_t *gcur = nullptr, *gend = nullptr;
+  if (key_off[NKEYS] > key_off[KEY_HEAVY]) {
+    gcur = ar.take<int32_t>((size_t)A->nnz);
+    gend = ar.take<int32_t>((size_t)A->nnz);
+    if (ar.over) return HS_ESCRATCH;
+  }
+  NumArgs na{rs, rb, f, nullptr, 0, Cp, C->idx, C->val, hslot, hist, nseg, &sb->dyn[1], &sb->err, gcur, gend};
   const int k0s[5] = {KEY_TINY, KEY_WARP, KEY_MID, KEY_LARGE, KEY_HEAVY};
   const int k1s[5] = {KEY_TINY + 1, KEY_WARP + 1, KEY_MID + 1, KEY_LARGE + 1, NKEYS};
   for (int kind = 0; kind < 5; ++kind) {

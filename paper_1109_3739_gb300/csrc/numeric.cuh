@@ -11,12 +11,10 @@
 //                          slots, then sorted emission;
 //   mid   (c <= 2048)      one CTA of 256; shared hash table of 2c slots;
 //   large (c <= CAP)       one CTA of 1024; shared hash table of 2c slots;
-//   heavy (c > CAP)        one CTA of 1024 per row, rows handed out largest
-//                          first; the row's columns are cut into parts of at
-//                          most CAP outputs using the per-segment counts of
-//                          the symbolic pass, and each part runs the large
-//                          kernel's accumulator over the products that fall
-//                          in its column range.
+//   heavy (c > CAP)        one CTA of 512 per row (two per SM), rows handed
+//                          out largest first; column parts accumulated with
+//                          a bitmap + rank-indexed value array (see
+//                          k_num_heavy).
 // The shared hash table is the sparse accumulator of Figure 1 with the dense
 // value array replaced by open addressing (keys + values), so its size
 // follows the row's output, not the matrix dimension (Section 2.1's argument
@@ -37,6 +35,9 @@ template <typename T> constexpr int vbytes() { return sizeof(T); }
 template <> constexpr int vbytes<NoVal>() { return 0; }
 
 template <typename T> constexpr int cap_large() { return vbytes<T>() == 8 ? 4096 : 8192; }
+
+// the structure-only view of a semiring (same iteration, no values)
+template <class SR> using StructOf = Semiring<OR_AND, NoVal>;
 
 // --------------------------------------------------------------- tiny
 constexpr int NTINY_WPB = 8;
@@ -168,8 +169,8 @@ template <typename T, int SLOTS, int CAP> struct CtaNumLayout {
   static constexpr size_t bytes = tail_off + sizeof(Tail);
 };
 
-template <class SR, int SLOTS, int CAP, bool PARTS>
-__global__ void __launch_bounds__(PARTS || CAP > 2048 ? 1024 : 256) k_num_cta(NumArgs a) {
+template <class SR, int SLOTS, int CAP>
+__global__ void __launch_bounds__(CAP > 2048 ? 1024 : 256) k_num_cta(NumArgs a) {
   using T = typename SR::val_t;
   using L = CtaNumLayout<T, SLOTS, CAP>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -181,79 +182,262 @@ __global__ void __launch_bounds__(PARTS || CAP > 2048 ? 1024 : 256) k_num_cta(Nu
   auto &tl = *reinterpret_cast<typename L::Tail *>(smem_raw + L::tail_off);
   const DevCsr A = ndev_a(a.A), B = ndev_b(a.B);
   T *Cv = reinterpret_cast<T *>(a.Cv);
-  const int64_t n = a.B.n;
-
-  // one part: columns [lo, hi) of row r holding pc outputs, written at out
-  auto run_part = [&](int r, bool restrict_cols, int lo, int hi, int pc, int64_t out) {
-    const int slots = max(64, min(SLOTS, next_pow2(2 * min(pc, CAP))));
+  for (int idx = blockIdx.x; idx < a.count; idx += gridDim.x) {
+    const int r = a.list[idx];
+    if (!HS_G(a.A.dbg, r >= 0 && r < a.A.nslots, 36, r)) continue;  // uniform: every thread skips
+    const int64_t o = nout_row(a.A, r);
+    const int64_t cb = a.Cp[o];
+    const int c = (int)(a.Cp[o + 1] - cb);
+    const int slots = max(64, min(SLOTS, next_pow2(2 * min(c, CAP))));
     const unsigned mask = slots - 1;
     for (int s = threadIdx.x; s < slots; s += blockDim.x) {
       keys[s] = EMPTY;
       if constexpr (SR::has_val) vals[s] = SR::identity();
     }
     __syncthreads();
-    cta_products<SR, NCH>(A, B, A.p[r], A.p[r + 1], restrict_cols, lo, hi, ex, tl.wtmp,
+    cta_products<SR, NCH>(A, B, A.p[r], A.p[r + 1], false, 0, 0, ex, tl.wtmp,
                           [&](int col, T v, int) { hash_insert_val<SR>(keys, vals, mask, col, v, a.err); });
-    group_sort_emit<CtaGroup, T, SR::has_val>(keys, vals, slots, pc, ck, cv, smem_raw, tl.wtmp, &tl.es,
-                                              a.Cj + out, SR::has_val ? Cv + out : nullptr, a.err, CAP, a.A.dbg);
-  };
+    group_sort_emit<CtaGroup, T, SR::has_val>(keys, vals, slots, c, ck, cv, smem_raw, tl.wtmp, &tl.es,
+                                              a.Cj + cb, SR::has_val ? Cv + cb : nullptr, a.err, CAP, a.A.dbg);
+    __syncthreads();
+  }
+}
 
-  if constexpr (!PARTS) {
-    for (int idx = blockIdx.x; idx < a.count; idx += gridDim.x) {
-      const int r = a.list[idx];
-      if (!HS_G(a.A.dbg, r >= 0 && r < a.A.nslots, 36, r)) continue;  // uniform: every thread skips
-      const int64_t o = nout_row(a.A, r);
-      const int64_t cb = a.Cp[o];
-      const int c = (int)(a.Cp[o + 1] - cb);
-      run_part(r, false, 0, 0, c, cb);
-      __syncthreads();
-    }
-  } else {
-    const int nseg = (int)((n + SEG_W - 1) / SEG_W);
-    while (true) {
-      if (threadIdx.x == 0) tl.row = atomicAdd(a.dyn, 1);
-      __syncthreads();
-      const int idx = tl.row;
-      if (idx >= a.count) break;
-      const int r0 = a.list[idx];
-      // a bad row id (guarded builds) is processed as an empty row so that the
-      // loop still reaches its closing barrier
-      const bool r_ok = HS_G(a.A.dbg, r0 >= 0 && r0 < a.A.nslots, 36, r0);
-      const int r = r_ok ? r0 : 0;
-      const int64_t o = nout_row(a.A, r);
-      const int64_t cb = a.Cp[o];
-      const int64_t c = r_ok ? a.Cp[o + 1] - cb : 0;
-      const int h = r_ok ? a.hslot[r] : -1;
-      const uint32_t *hist = a.hist + (int64_t)(h < 0 ? 0 : h) * a.nseg;
-      if (r_ok && h < 0 && threadIdx.x == 0) atomicExch(a.err, 4);
-      int64_t done = 0;
-      int seg = 0;
-      while (seg < nseg && h >= 0) {
-        if (threadIdx.x == 0) {
-          // greedy: extend the part while it stays within CAP outputs
-          int e = seg, sum = 0;
-          while (e < nseg && sum + (int)hist[e] <= CAP) sum += (int)hist[e++];
-          if (e == seg) {  // a single over-full segment cannot happen (SEG_W <= CAP)
-            atomicExch(a.err, 5);
-            e = nseg;
-          }
-          tl.part_end = e;
-          tl.part_cnt = sum;
+// ------------------------------------------------------------------ heavy
+// Rows whose output exceeds one shared table.  The row's columns are cut into
+// parts (consecutive 4096-column segments, using the symbolic pass's segment
+// counts) holding at most HEAVY_CAP outputs and spanning at most HV_WMAX
+// columns.  Each part is accumulated with the sparse accumulator of Figure 1
+// split in two: its occupancy as a bitmap over the part's columns, its values
+// as a compact array indexed by the column's rank among the part's set bits:
+//   pass 1  every product in the part ORs its column's bit;
+//   rank    a per-word prefix of set bits (warp scans) gives each word the
+//           number of output columns before it;
+//   pass 2  every product adds its value at rank(col) = prefix(word) +
+//           popcount(bits of the word below col);
+//   emit    the bitmap is walked in order (ascending columns, coalesced
+//           stores) and the value array is copied out as is.
+// No hashing and no sorting.  The B-row segment of each A entry for a part
+// continues where the previous part's ended: per-entry cursors (gcur, and
+// gend for the part's end) live in global scratch indexed like A's entries,
+// and each part's end is found by a galloping search from the cursor.
+constexpr int HV_NT = 512;          // threads per CTA; two CTAs share an SM
+constexpr int HV_WMAX = 1 << 18;    // columns per part: a 32 KB bitmap
+constexpr int HV_WORDS = HV_WMAX / 32;
+constexpr int HV_CH = 512;          // A entries staged per expansion round
+
+template <typename T> constexpr int heavy_cap() {
+  return vbytes<T>() == 8 ? 4096 : (vbytes<T>() == 0 ? 16384 : 8192);
+}
+
+template <typename T> struct HeavySmem {
+  unsigned bitmap[HV_WORDS];
+  uint16_t wpre[HV_WORDS];          // set bits before word w within the part
+  int wtot[HV_NT / 32 + 1];         // per-warp totals, then their exclusive scan
+  int excl[HV_CH + 1];
+  int64_t sbeg[HV_CH];
+  T aval[HV_CH];
+  T vals[heavy_cap<T>()];
+  int wtmp[33];
+  int row, part_end, part_cnt, total;
+};
+
+template <class SR>
+__global__ void __launch_bounds__(HV_NT, 2) k_num_heavy(NumArgs a) {
+  using T = typename SR::val_t;
+  constexpr int CAPH = heavy_cap<T>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto &sm = *reinterpret_cast<HeavySmem<T> *>(smem_raw);
+  const DevCsr A = ndev_a(a.A), B = ndev_b(a.B);
+  T *Cv = reinterpret_cast<T *>(a.Cv);
+  int32_t *gcur = a.gcur, *gend = a.gend;
+  const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5, nw = HV_NT / 32;
+  const int64_t n = a.B.n;
+  const int nseg = (int)((n + SEG_W - 1) / SEG_W);
+  long long *dbg = a.A.dbg;
+
+  while (true) {
+    if (tid == 0) sm.row = atomicAdd(a.dyn, 1);
+    __syncthreads();
+    const int idx = sm.row;
+    if (idx >= a.count) break;
+    const int r0 = a.list[idx];
+    // a bad row id is processed as an empty row so the loop reaches its barriers
+    const bool r_ok = HS_G(dbg, r0 >= 0 && r0 < a.A.nslots, 36, r0);
+    const int r = r_ok ? r0 : 0;
+    const int64_t o = nout_row(a.A, r);
+    const int64_t cb = a.Cp[o];
+    const int64_t c = r_ok ? a.Cp[o + 1] - cb : 0;
+    const int h = r_ok ? a.hslot[r] : -1;
+    if (r_ok && h < 0 && tid == 0) atomicExch(a.err, 4);
+    const uint32_t *hist = a.hist + (int64_t)(h < 0 ? 0 : h) * a.nseg;
+    const int64_t q0 = A.p[r], q1 = r_ok ? A.p[r + 1] : q0;
+    const int nrounds = (int)((q1 - q0 + HV_CH - 1) / HV_CH);
+    for (int64_t q = q0 + tid; q < q1; q += HV_NT) gcur[q] = 0;
+    int64_t done = 0;
+    int seg = 0;
+    while (seg < nseg && h >= 0) {
+      if (tid == 0) {
+        int e = seg, sum = 0;
+        while (e < nseg && e - seg < HV_WMAX / SEG_W && sum + (int)hist[e] <= CAPH) sum += (int)hist[e++];
+        if (e == seg) {  // cannot happen: a segment holds at most SEG_W <= CAPH outputs
+          atomicExch(a.err, 5);
+          e = nseg;
         }
-        __syncthreads();
-        const int pe = tl.part_end, pc = tl.part_cnt;
-        if (pc > 0) {
-          const int lo = seg * SEG_W;
-          const int hi = (int)min((int64_t)pe * SEG_W, n);
-          run_part(r, true, lo, hi, pc, cb + done);
-          done += pc;
-        }
-        seg = pe;
-        __syncthreads();
+        sm.part_end = e;
+        sm.part_cnt = sum;
       }
-      if (threadIdx.x == 0 && done != c) atomicExch(a.err, 6);
+      __syncthreads();  // also orders the cursor reset before the first part's reads
+      const int pe = sm.part_end, pc = sm.part_cnt;
+      if (pc > 0) {
+        const int lo = seg * SEG_W;
+        const int hi = (int)min((int64_t)pe * SEG_W, n);
+        const int words = (hi - lo + 31) >> 5;
+        for (int w = tid; w < words; w += HV_NT) sm.bitmap[w] = 0u;
+        // ---- pass 1: occupancy
+        int total = 0;
+        for (int rd = 0; rd < nrounds; ++rd) {
+          const int64_t rq0 = q0 + (int64_t)rd * HV_CH;
+          const int cnt = (int)min((int64_t)HV_CH, q1 - rq0);
+          __syncthreads();
+          for (int e = tid; e < HV_CH; e += HV_NT) {
+            int64_t s = 0;
+            int len = 0;
+            if (e < cnt) {
+              const int64_t q = rq0 + e;
+              const int k = __ldg(A.j + q);
+              if (HS_G(dbg, k >= 0 && k < B.rows, 2, k)) {
+                const int64_t base = __ldg(B.p + k), end = __ldg(B.p + k + 1);
+                s = base + gcur[q];
+                const int64_t se = gallop_lower_bound(B.j, s, end, hi);
+                len = (int)(se - s);
+                gend[q] = (int32_t)(se - base);
+                if (nrounds == 1) {
+                  gcur[q] = (int32_t)(se - base);
+                  if constexpr (SR::needs_a) sm.aval[e] = load_val<T>(A.v, q);
+                }
+              }
+            }
+            sm.excl[e] = len;
+            sm.sbeg[e] = s;
+          }
+          __syncthreads();
+          total = group_excl_scan<CtaGroup>(sm.excl, HV_CH, sm.wtmp);
+          if (tid == 0) sm.excl[HV_CH] = total;
+          __syncthreads();
+          auto set_bit = [&](int col, NoVal, int) {
+            const int x = col - lo;
+            if (HS_G(dbg, x >= 0 && x < hi - lo, 60, col)) atomicOr(sm.bitmap + (x >> 5), 1u << (x & 31));
+          };
+          cta_expand_staged<StructOf<SR>>(B, sm.sbeg, sm.excl, reinterpret_cast<const NoVal *>(sm.aval), cnt,
+                                          total, set_bit);
+        }
+        __syncthreads();
+        // ---- rank: prefix of set bits per word, in runs of 32 words per warp
+        {
+          const int wpw = ((words + nw - 1) / nw + 31) & ~31;
+          const int w0 = warp * wpw, w1 = min(words, w0 + wpw);
+          int carry = 0;
+          for (int wb = w0; wb < w1; wb += 32) {
+            const int w = wb + lane;
+            const int pc_w = w < w1 ? __popc(sm.bitmap[w]) : 0;
+            const int incl = warp_incl_scan(pc_w);
+            if (w < w1) sm.wpre[w] = (uint16_t)(carry + incl - pc_w);
+            carry += __shfl_sync(FULL, incl, 31);
+          }
+          if (lane == 0) sm.wtot[warp] = carry;
+          __syncthreads();
+          if (warp == 0) {
+            const int t = lane < nw ? sm.wtot[lane] : 0;
+            const int ti = warp_incl_scan(t);
+            if (lane < nw) sm.wtot[lane] = ti - t;
+            if (lane == nw - 1) sm.total = ti;
+          }
+          __syncthreads();
+          const int add = sm.wtot[warp];
+          for (int w = w0 + lane; w < w1; w += 32) sm.wpre[w] = (uint16_t)(sm.wpre[w] + add);
+          if constexpr (SR::has_val)
+            for (int i = tid; i < pc; i += HV_NT) sm.vals[i] = SR::identity();
+        }
+        __syncthreads();
+        const bool consistent = sm.total == pc;
+        if (!consistent && tid == 0) atomicExch(a.err, 9);
+        // ---- pass 2: values at their rank
+        if constexpr (SR::has_val) {
+          for (int rd = 0; rd < nrounds; ++rd) {
+            if (nrounds > 1) {
+              const int64_t rq0 = q0 + (int64_t)rd * HV_CH;
+              const int cnt = (int)min((int64_t)HV_CH, q1 - rq0);
+              __syncthreads();
+              for (int e = tid; e < HV_CH; e += HV_NT) {
+                int64_t s = 0;
+                int len = 0;
+                if (e < cnt) {
+                  const int64_t q = rq0 + e;
+                  const int k = __ldg(A.j + q);
+                  if (HS_G(dbg, k >= 0 && k < B.rows, 2, k)) {
+                    const int64_t base = __ldg(B.p + k);
+                    s = base + gcur[q];
+                    len = gend[q] - gcur[q];
+                    gcur[q] = gend[q];
+                    if constexpr (SR::needs_a) sm.aval[e] = load_val<T>(A.v, q);
+                  }
+                }
+                sm.excl[e] = len;
+                sm.sbeg[e] = s;
+              }
+              __syncthreads();
+              total = group_excl_scan<CtaGroup>(sm.excl, HV_CH, sm.wtmp);
+              if (tid == 0) sm.excl[HV_CH] = total;
+              __syncthreads();
+              auto add_val = [&](int col, T v, int) {
+                const int x = col - lo;
+                if (!HS_G(dbg, x >= 0 && x < hi - lo, 60, col)) return;
+                const int w = x >> 5;
+                const int rank = sm.wpre[w] + __popc(sm.bitmap[w] & ((1u << (x & 31)) - 1u));
+                if (HS_G(dbg, rank < pc, 61, rank)) SR::add_atomic(sm.vals + rank, v);
+              };
+              cta_expand_staged<SR>(B, sm.sbeg, sm.excl, sm.aval, cnt, total, add_val);
+            } else {
+              auto add_val = [&](int col, T v, int) {
+                const int x = col - lo;
+                if (!HS_G(dbg, x >= 0 && x < hi - lo, 60, col)) return;
+                const int w = x >> 5;
+                const int rank = sm.wpre[w] + __popc(sm.bitmap[w] & ((1u << (x & 31)) - 1u));
+                if (HS_G(dbg, rank < pc, 61, rank)) SR::add_atomic(sm.vals + rank, v);
+              };
+              const int cnt = (int)(q1 - q0);
+              cta_expand_staged<SR>(B, sm.sbeg, sm.excl, sm.aval, cnt, total, add_val);
+            }
+          }
+          __syncthreads();
+        } else if (nrounds > 1) {
+          // structure only: still advance the cursors past this part
+          for (int64_t q = q0 + tid; q < q1; q += HV_NT) gcur[q] = gend[q];
+        }
+        // ---- emit: columns in bitmap order, values in rank order
+        const int64_t out = cb + done;
+        if (consistent && HS_G(dbg, done + pc <= c, 62, done + pc)) {
+          for (int w = tid; w < words; w += HV_NT) {
+            unsigned bits = sm.bitmap[w];
+            int pos = sm.wpre[w];
+            while (bits) {
+              const int b = __ffs(bits) - 1;
+              a.Cj[out + pos] = lo + (w << 5) + b;
+              ++pos;
+              bits &= bits - 1;
+            }
+          }
+          if constexpr (SR::has_val)
+            for (int i = tid; i < pc; i += HV_NT) Cv[out + i] = sm.vals[i];
+        }
+        done += pc;
+      }
+      seg = pe;
       __syncthreads();
     }
+    if (tid == 0 && r_ok && done != c) atomicExch(a.err, 6);
+    __syncthreads();
   }
 }
 
@@ -282,23 +466,23 @@ template <class SR> void launch_numeric_sr(int kind, const NumArgs &a, cudaStrea
     }
     case 2: {
       using L = CtaNumLayout<T, 2 * CAP_MID, CAP_MID>;
-      set_smem_attr(k_num_cta<SR, 2 * CAP_MID, CAP_MID, false>, L::bytes);
+      set_smem_attr(k_num_cta<SR, 2 * CAP_MID, CAP_MID>, L::bytes);
       count_launch();
-      k_num_cta<SR, 2 * CAP_MID, CAP_MID, false><<<ngrid_cap(a.count, 1, 3), 256, L::bytes, st>>>(a);
+      k_num_cta<SR, 2 * CAP_MID, CAP_MID><<<ngrid_cap(a.count, 1, 3), 256, L::bytes, st>>>(a);
       break;
     }
     case 3: {
       using L = CtaNumLayout<T, 2 * CAPL, CAPL>;
-      set_smem_attr(k_num_cta<SR, 2 * CAPL, CAPL, false>, L::bytes);
+      set_smem_attr(k_num_cta<SR, 2 * CAPL, CAPL>, L::bytes);
       count_launch();
-      k_num_cta<SR, 2 * CAPL, CAPL, false><<<ngrid_cap(a.count, 1, 1), 1024, L::bytes, st>>>(a);
+      k_num_cta<SR, 2 * CAPL, CAPL><<<ngrid_cap(a.count, 1, 1), 1024, L::bytes, st>>>(a);
       break;
     }
     case 4: {
-      using L = CtaNumLayout<T, 2 * CAPL, CAPL>;
-      set_smem_attr(k_num_cta<SR, 2 * CAPL, CAPL, true>, L::bytes);
+      const size_t bytes = sizeof(HeavySmem<T>);
+      set_smem_attr(k_num_heavy<SR>, bytes);
       count_launch();
-      k_num_cta<SR, 2 * CAPL, CAPL, true><<<ngrid_cap(a.count, 1, 1), 1024, L::bytes, st>>>(a);
+      k_num_heavy<SR><<<ngrid_cap(a.count, 1, 2), HV_NT, bytes, st>>>(a);
       break;
     }
   }

@@ -328,7 +328,7 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
     }
     launch_flops(rs, rb, f, sb->key_cnt, sb->stats, st);
     launch_key_offsets(sb->key_cnt, sb->key_off, sb->key_cur, st);
-    launch_scatter_sym(rs, f, sb->key_cur, list, hslot, &sb->nhist, st);
+    launch_scatter_sym(rs, f, sb->key_cur, list, hslot, &sb->nhist, cap_large_of(out_dt), st);
   }
   if (int e = phase_check("analysis", st, sb->dbg)) return e;
   CK(cudaMemcpyAsync(hb, sb, sizeof(SmallBlock), cudaMemcpyDeviceToHost, st));
@@ -409,7 +409,14 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
   }
 
   // ---- numeric
-  NumArgs na{rs, rb, f, nullptr, 0, Cp, C->idx, C->val, hslot, hist, nseg, &sb->dyn[1], &sb->err};
+  // heavy bin: per-A-entry cursors into B rows (relative offsets)
+  int32_t *gcur = nullptr, *gend = nullptr;
+  if (key_off[NKEYS] > key_off[KEY_HEAVY]) {
+    gcur = mem.tmp<int32_t>((size_t)A->nnz);
+    gend = mem.tmp<int32_t>((size_t)A->nnz);
+    if (!gcur || !gend) return HS_ENOMEM;
+  }
+  NumArgs na{rs, rb, f, nullptr, 0, Cp, C->idx, C->val, hslot, hist, nseg, &sb->dyn[1], &sb->err, gcur, gend};
   const char *names[5] = {"numeric_tiny", "numeric_warp", "numeric_mid", "numeric_large", "numeric_heavy"};
   const int k0s[5] = {KEY_TINY, KEY_WARP, KEY_MID, KEY_LARGE, KEY_HEAVY};
   const int k1s[5] = {KEY_TINY + 1, KEY_WARP + 1, KEY_MID + 1, KEY_LARGE + 1, NKEYS};

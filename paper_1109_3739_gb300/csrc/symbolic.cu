@@ -96,6 +96,7 @@ template <int SLOTS, bool HIST> struct SymCtaSmem {
   CtaExpandSmem<NoVal, CH> ex;
   int wtmp[33];
   int total;
+  unsigned segcnt[HIST ? SEG_SMEM : 1];  // per-segment counts of the current row
 };
 
 template <int SLOTS, bool HIST>
@@ -116,13 +117,25 @@ __global__ void __launch_bounds__(HIST ? 512 : 256) k_sym_cta(SymArgs a) {
                                [&](int col, NoVal, int) { cnt += hash_insert_key(sm.keys, mask, col); });
     cnt = warp_sum(cnt);
     if (lane_id() == 0 && cnt) atomicAdd(&sm.total, cnt);
-    if (HIST) {
+    if constexpr (HIST) {
       const int h = a.hslot[r];
       if (h >= 0) {
         uint32_t *hist = a.hist + (int64_t)h * a.nseg;
-        for (int s = threadIdx.x; s < slots; s += blockDim.x) {
-          const int k = sm.keys[s];
-          if (k != EMPTY && HS_G(a.A.dbg, k / SEG_W < a.nseg, 31, k)) atomicAdd(hist + k / SEG_W, 1u);
+        if (a.nseg <= SEG_SMEM) {
+          // count in shared memory, then write the row's histogram once
+          for (int g = threadIdx.x; g < a.nseg; g += blockDim.x) sm.segcnt[g] = 0u;
+          __syncthreads();
+          for (int s = threadIdx.x; s < slots; s += blockDim.x) {
+            const int k = sm.keys[s];
+            if (k != EMPTY && HS_G(a.A.dbg, k / SEG_W < a.nseg, 31, k)) atomicAdd(sm.segcnt + k / SEG_W, 1u);
+          }
+          __syncthreads();
+          for (int g = threadIdx.x; g < a.nseg; g += blockDim.x) hist[g] = sm.segcnt[g];
+        } else {
+          for (int s = threadIdx.x; s < slots; s += blockDim.x) {
+            const int k = sm.keys[s];
+            if (k != EMPTY && HS_G(a.A.dbg, k / SEG_W < a.nseg, 31, k)) atomicAdd(hist + k / SEG_W, 1u);
+          }
         }
       }
     }
@@ -138,6 +151,7 @@ struct SymHeavySmem {
   int wtmp[33];
   int total;
   int row;
+  unsigned segcnt[SEG_SMEM];  // per-segment counts of the current row (nseg <= SEG_SMEM)
   unsigned bitmap[BITMAP_COLS / 32];
 };
 
@@ -162,6 +176,9 @@ __global__ void __launch_bounds__(1024) k_sym_heavy(SymArgs a) {
     const int r = r_ok ? r0 : 0;
     const int h = r_ok ? a.hslot[r] : -1;
     uint32_t *hist = h >= 0 ? a.hist + (int64_t)h * a.nseg : nullptr;
+    const bool seg_smem = a.nseg <= SEG_SMEM;
+    if (hist && seg_smem)
+      for (int g = threadIdx.x; g < a.nseg; g += blockDim.x) sm.segcnt[g] = 0u;
     int cnt = 0;
     for (int ch = 0; ch < (r_ok ? nchunk : 0); ++ch) {
       const int lo = ch * BITMAP_COLS;
@@ -182,13 +199,19 @@ __global__ void __launch_bounds__(1024) k_sym_heavy(SymArgs a) {
         c = warp_sum(c);
         if (lane == 0 && c) {
           cnt += c;
-          if (hist && HS_G(a.A.dbg, (lo + wb * 32) / SEG_W < a.nseg, 32, wb)) atomicAdd(hist + (lo + wb * 32) / SEG_W, (uint32_t)c);
+          const int g = (lo + wb * 32) / SEG_W;
+          if (hist && HS_G(a.A.dbg, g < a.nseg, 32, wb)) {
+            if (seg_smem) atomicAdd(sm.segcnt + g, (unsigned)c);
+            else atomicAdd(hist + g, (uint32_t)c);
+          }
         }
       }
       __syncthreads();
     }
     if (lane == 0 && cnt) atomicAdd(&sm.total, cnt);
     __syncthreads();
+    if (hist && seg_smem)
+      for (int g = threadIdx.x; g < a.nseg; g += blockDim.x) hist[g] = sm.segcnt[g];
     if (threadIdx.x == 0 && r_ok) put_count(a, out_row(a.A, r), sm.total);
     __syncthreads();
   }
