@@ -222,11 +222,15 @@ template <> __device__ __forceinline__ NoVal load_val<NoVal>(const void *, int64
 template <typename T> __device__ __forceinline__ T shfl_val(T x, int src) { return __shfl_sync(FULL, x, src); }
 template <> __device__ __forceinline__ NoVal shfl_val<NoVal>(NoVal x, int) { return x; }
 
-// Deal the products of up to 32 B-row segments (one per lane: start s, length
-// len, left value a) one per lane: lane l takes product base+l and finds its
-// segment by a binary search over the inclusive length scan (shuffles only).
-// visit(col, prod, p) runs on every lane that holds a product, p being the
-// product's index among this call's products.  Returns the number of
+// Visit the products of up to 32 B-row segments (one per lane: start s,
+// length len, left value a).  Segments of at least 32 products are walked by
+// the whole warp, one segment at a time, with consecutive lanes on
+// consecutive entries of B (coalesced, no search).  The remaining short
+// segments are dealt one product per lane: lane l takes product base+l of
+// their concatenation and finds its segment by a binary search over the
+// inclusive length scan (shuffles only).  visit(col, prod, p) runs on every
+// lane that holds a product, p being the product's index in the order of the
+// segments (as if they were walked lane by lane).  Returns the number of
 // products.  All 32 lanes must call this together.
 template <class SR, class Visit>
 __device__ __forceinline__ int warp_expand(const DevCsr &B, int64_t s, int len, typename SR::val_t a,
@@ -235,26 +239,63 @@ __device__ __forceinline__ int warp_expand(const DevCsr &B, int64_t s, int len, 
   const int lane = lane_id();
   const int incl = warp_incl_scan(len);
   const int total = __shfl_sync(FULL, incl, 31);
-  for (int base = 0; base < total; base += 32) {
+  const int ex_full = incl - len;
+  // long segments: the whole warp on one segment
+  unsigned longm = __ballot_sync(FULL, len >= 32);
+  while (longm) {
+    const int l = __ffs(longm) - 1;
+    longm &= longm - 1;
+    const int64_t sl = __shfl_sync(FULL, s, l);
+    const int ll = __shfl_sync(FULL, len, l);
+    const int el = __shfl_sync(FULL, ex_full, l);
+    const T al = shfl_val<T>(a, l);
+    for (int off = lane; off < ll; off += 64) {
+      const int64_t p0 = sl + off, p1 = p0 + 32;
+      const bool ok1 = off + 32 < ll;
+      if (!HS_G(B.dbg, p0 >= 0 && p0 < B.nnz && (!ok1 || p1 < B.nnz), 4, p0)) continue;
+      const int c0 = __ldg(B.j + p0);
+      const int c1 = ok1 ? __ldg(B.j + p1) : 0;
+      if constexpr (SR::has_val) {
+        T b0{}, b1{};
+        if constexpr (SR::needs_b) {
+          b0 = load_val<T>(B.v, p0);
+          if (ok1) b1 = load_val<T>(B.v, p1);
+        }
+        visit(c0, SR::mul(al, b0), el + off);
+        if (ok1) visit(c1, SR::mul(al, b1), el + off + 32);
+      } else {
+        visit(c0, NoVal{}, el + off);
+        if (ok1) visit(c1, NoVal{}, el + off + 32);
+      }
+    }
+  }
+  // short segments: one product per lane
+  const int slen = len < 32 ? len : 0;
+  const int sincl = warp_incl_scan(slen);
+  const int stotal = __shfl_sync(FULL, sincl, 31);
+  for (int base = 0; base < stotal; base += 32) {
     const int p = base + lane;
     int src = 0;  // number of lanes whose inclusive end is <= p
 #pragma unroll
     for (int step = 16; step >= 1; step >>= 1) {
-      int v = __shfl_sync(FULL, incl, src + step - 1);
+      int v = __shfl_sync(FULL, sincl, src + step - 1);
       if (v <= p) src += step;
     }
     const int64_t ss = __shfl_sync(FULL, s, src);
-    const int ex = __shfl_sync(FULL, incl - len, src);
+    const int sex = __shfl_sync(FULL, sincl - slen, src);
+    const int fex = __shfl_sync(FULL, ex_full, src);
     const T aa = shfl_val<T>(a, src);
-    if (p < total && HS_G(B.dbg, ss + (p - ex) >= 0 && ss + (p - ex) < B.nnz, 4, ss + (p - ex))) {
-      const int64_t pos = ss + (p - ex);
-      const int col = __ldg(B.j + pos);
-      if constexpr (SR::has_val) {
-        T b{};
-        if constexpr (SR::needs_b) b = load_val<T>(B.v, pos);
-        visit(col, SR::mul(aa, b), p);
-      } else {
-        visit(col, NoVal{}, p);
+    if (p < stotal) {
+      const int64_t pos = ss + (p - sex);
+      if (HS_G(B.dbg, pos >= 0 && pos < B.nnz, 4, pos)) {
+        const int col = __ldg(B.j + pos);
+        if constexpr (SR::has_val) {
+          T b{};
+          if constexpr (SR::needs_b) b = load_val<T>(B.v, pos);
+          visit(col, SR::mul(aa, b), fex + (p - sex));
+        } else {
+          visit(col, NoVal{}, fex + (p - sex));
+        }
       }
     }
   }
@@ -378,7 +419,7 @@ __device__ __forceinline__ int64_t gallop_lower_bound(const int32_t *j, int64_t 
 // range one product per lane (warp_expand).  Per-row product counts must stay
 // below 2^31.  All threads of the CTA must call this together.
 template <class SR, int CH, class Visit>
-__device__ void cta_products(const DevCsr &A, const DevCsr &B, int64_t q0, int64_t q1, bool restrict_cols,
+__device__ __forceinline__ void cta_products(const DevCsr &A, const DevCsr &B, int64_t q0, int64_t q1, bool restrict_cols,
                              int lo, int hi, CtaExpandSmem<typename SR::val_t, CH> &sm, int *wtmp,
                              Visit &&visit) {
   using T = typename SR::val_t;
