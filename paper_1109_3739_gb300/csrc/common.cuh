@@ -392,6 +392,44 @@ __device__ __forceinline__ void cta_expand_staged(const DevCsr &B, const int64_t
   }
 }
 
+// First position in [s, e) whose column is >= x.  Long ranges start with one
+// interpolation probe (column ids of a row are close to uniform after a
+// random relabelling) and narrow the bracket around it; then, as for short
+// ranges, probe lo, lo+1, lo+3, lo+7, ... (galloping) and finish with a
+// binary search, so the cost stays logarithmic for any distribution.
+__device__ __forceinline__ int64_t gallop_lower_bound(const int32_t *j, int64_t s, int64_t e, int x);
+__device__ __forceinline__ int64_t interp_lower_bound(const int32_t *j, int64_t s, int64_t e, int x) {
+  if (e - s > 64) {
+    const int c0 = __ldg(j + s), c1 = __ldg(j + e - 1);
+    if (c0 >= x) return s;
+    if (c1 < x) return e;
+    // c0 < x <= c1: the answer is in (s, e-1]
+    int64_t g = s + 1 + (int64_t)(((double)(x - c0) / (double)(c1 - c0 + 1)) * (double)(e - 2 - s));
+    if (g > e - 1) g = e - 1;
+    if (g <= s) g = s + 1;
+    if (__ldg(j + g) >= x) {
+      // answer in (s, g]: gallop leftwards from g
+      int64_t hi = g, step = 1, lo = g - 1;
+      while (lo > s && __ldg(j + lo) >= x) {
+        hi = lo;
+        step <<= 1;
+        lo = g - step;
+        if (lo < s) lo = s;
+      }
+      // j[lo] < x (or lo == s), j[hi] >= x
+      int64_t a = lo + 1, b = hi;
+      while (a < b) {
+        const int64_t mid = a + ((b - a) >> 1);
+        if (__ldg(j + mid) < x) a = mid + 1;
+        else b = mid;
+      }
+      return a;
+    }
+    return gallop_lower_bound(j, g + 1, e, x);
+  }
+  return gallop_lower_bound(j, s, e, x);
+}
+
 // First position in [s, e) whose column is >= x: probe s, s+1, s+3, s+7, ...
 // (galloping) and finish with a binary search, so a short distance costs few
 // loads whatever the row's length.

@@ -239,7 +239,9 @@ template <typename T> struct HeavySmem {
   T aval[HV_CH];
   T vals[heavy_cap<T>()];
   int wtmp[33];
-  int row, part_end, part_cnt, total;
+  int row, part_end, part_cnt, total, nparts;
+  int pend[SEG_SMEM];  // the row's parts: end segment and output count
+  int pcnt[SEG_SMEM];
 };
 
 template <class SR>
@@ -274,10 +276,41 @@ __global__ void __launch_bounds__(HV_NT, 2) k_num_heavy(NumArgs a) {
     const int64_t q0 = A.p[r], q1 = r_ok ? A.p[r + 1] : q0;
     const int nrounds = (int)((q1 - q0 + HV_CH - 1) / HV_CH);
     for (int64_t q = q0 + tid; q < q1; q += HV_NT) gcur[q] = 0;
+    // the row's parts, chosen greedily from its segment counts: at most CAPH
+    // outputs and HV_WMAX columns each
+    const bool plan = h >= 0 && nseg <= SEG_SMEM;
+    if (plan) {
+      for (int g = tid; g < nseg; g += HV_NT) sm.pend[g] = (int)hist[g];  // stage the counts
+      __syncthreads();
+      if (tid == 0) {
+        int np = 0, e = 0;
+        while (e < nseg) {
+          const int b = e;
+          int sum = 0;
+          while (e < nseg && e - b < HV_WMAX / SEG_W && sum + sm.pend[e] <= CAPH) sum += sm.pend[e++];
+          if (e == b) {  // cannot happen: a segment holds at most SEG_W <= CAPH outputs
+            atomicExch(a.err, 5);
+            e = nseg;
+          }
+          sm.pcnt[np] = sum;
+          sm.pend[np] = e;  // np <= b: the counts still to read lie at or after e
+          ++np;
+        }
+        sm.nparts = np;
+      }
+      __syncthreads();
+    }
     int64_t done = 0;
     int seg = 0;
+    int part = 0;
     while (seg < nseg && h >= 0) {
-      if (tid == 0) {
+      if (plan) {
+        if (tid == 0) {
+          sm.part_end = sm.pend[part];
+          sm.part_cnt = sm.pcnt[part];
+        }
+        ++part;
+      } else if (tid == 0) {
         int e = seg, sum = 0;
         while (e < nseg && e - seg < HV_WMAX / SEG_W && sum + (int)hist[e] <= CAPH) sum += (int)hist[e++];
         if (e == seg) {  // cannot happen: a segment holds at most SEG_W <= CAPH outputs
@@ -309,7 +342,7 @@ __global__ void __launch_bounds__(HV_NT, 2) k_num_heavy(NumArgs a) {
               if (HS_G(dbg, k >= 0 && k < B.rows, 2, k)) {
                 const int64_t base = __ldg(B.p + k), end = __ldg(B.p + k + 1);
                 s = base + gcur[q];
-                const int64_t se = gallop_lower_bound(B.j, s, end, hi);
+                const int64_t se = interp_lower_bound(B.j, s, end, hi);
                 len = (int)(se - s);
                 gend[q] = (int32_t)(se - base);
                 if (nrounds == 1) {
