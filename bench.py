@@ -41,6 +41,12 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target length of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "batched", "serving"],
+                    help="rmat: the headline product; batched: 2000 independent ER products, "
+                         "one batched call against one call per problem")
+    ap.add_argument("--batch", type=int, default=2000)
+    ap.add_argument("--requests", type=int, default=400)
+    ap.add_argument("--rate", type=float, default=0.0, help="serving: arrivals per second (0: sweep)")
     return ap.parse_args()
 
 
@@ -167,11 +173,132 @@ def run_reference(args):
     }), flush=True)
 
 
+# ------------------------------------------------------------- batched form
+def run_batched(args):
+    """2000 independent ER products (n_i log-uniform in [256, 65536], 2..32
+    nonzeros per column, f64 (+,x)): one hs_spgemm_batched call against one
+    hs_spgemm call per problem, same GPU, same results."""
+    import torch
+
+    from paper_1109_3739_gb300 import hspgemm as h
+    from paper_1109_3739_gb300 import inputs as I
+    dev = torch.device("cuda", 0)
+    probs = I.batched_er(args.batch, seed=4, dtype="f64", workers=min(16, os.cpu_count() or 1))
+    flops = 0
+    for a, b in probs:
+        deg_b = np.diff(b.rowptr)
+        flops += int(deg_b[a.col].sum())
+    As = [h.DeviceCSR.from_host(a, device=dev) for a, _ in probs]
+    Bs = [h.DeviceCSR.from_host(b, device=dev) for _, b in probs]
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(fn, steps, warmup):
+        out = None
+        for _ in range(warmup):
+            out = None
+            out = fn()
+        torch.cuda.synchronize(dev)
+        ts = []
+        for _ in range(steps):
+            flush.fill_(1)
+            out = None
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return ts, out
+
+    l0 = h.launch_count()
+    h.profile_enable(True)
+    h.profile_reset()
+    tb, res = timed(lambda: h.spgemm_batched("plus_times", As, Bs, stream=stream), args.steps, args.warmup)
+    phases = {k: v[0] / (args.steps + args.warmup) for k, v in h.profile_read().items()}
+    h.profile_enable(False)
+    nb_launch = (h.launch_count() - l0) // (args.steps + args.warmup)
+    nnz_c = res[0].nnz
+    res = None
+    l0 = h.launch_count()
+    tl, res = timed(lambda: [h.spgemm("plus_times", a, b, stream=stream) for a, b in zip(As, Bs)],
+                    max(1, args.steps // 3), 1)
+    nl_launch = (h.launch_count() - l0) // (max(1, args.steps // 3) + 1)
+    res = None
+    med_b, med_l = statistics.median(tb), statistics.median(tl)
+    hbm, peak_kind = peaks()
+    nnz_a = sum(a.nnz for a, _ in probs) + sum(b.nnz for _, b in probs)
+    alg = nnz_a * 12 + sum(a.m + b.m + 2 for a, b in probs) * 8 + nnz_c * 12 + sum(a.m + 1 for a, _ in probs) * 8
+    print(json.dumps({
+        "metric": METRIC, "value": flops / (med_b / 1000.0), "unit": "mults/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": med_b, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"batched_er_{args.batch}_f64", "problems": args.batch, "flops_mults": flops,
+                   "nnz_C": nnz_c, "step_hbm_fraction": alg / (med_b / 1000.0) / 1e9 / hbm,
+                   "l2": "flushed between steps (512 MB write)"},
+        "one_call_per_problem": {"ms_per_step": med_l, "value": flops / (med_l / 1000.0),
+                                 "gpu_launches": nl_launch},
+        "speedup_vs_one_call_per_problem": med_l / med_b,
+        "gpu_launches": nb_launch,
+        "phases_ms_per_step": phases,
+    }), flush=True)
+
+
+# ------------------------------------------------------------------ serving
+def run_serving(args):
+    """Resident R-MAT scale 22 graph (edge factor 16, int32 weights 1..100) and a
+    Poisson stream of 70 % SpRef subgraph extractions (|I| log-uniform in
+    2^6..2^16), 10 % contractions S*A*S^T (n/64 random clusters, int64) and
+    20 % SpAsgn batch updates (2^10..2^16 random edges); p50/p99 latency per
+    type and requests/s, served with admission and continuous batching, against
+    the same stream served one request at a time."""
+    import torch
+
+    from paper_1109_3739_gb300 import inputs as I
+    from paper_1109_3739_gb300 import serving as S
+    A = I.rmat_matrix(22, 16, seed=5, dtype="i32")
+    n = A.n
+    labels = S.make_label_sets(n, 4, seed=6)
+    out = {"metric": "served_requests_per_s", "unit": "req/s", "n_gpus": 1, "higher_is_better": True,
+           "data": "synthetic", "dtype": "i32",
+           "config": {"workload": "serving_rmat22_ef16_i32", "nnz_A": A.nnz, "requests": args.requests,
+                      "mix": "spref 0.7 / contract 0.1 / spasgn 0.2"}, "runs": []}
+    rates = [args.rate] if args.rate > 0 else [20.0, 80.0]
+    for rate in rates:
+        reqs = S.make_requests(n, args.requests, rate=rate, seed=9)
+        res = {}
+        for mode in ("batched", "serial"):
+            store = S.GraphStore(A)
+            ex = S.Executor(store, labels, store.device, keep_results=False)
+            ex.prepare()
+            # warm-up: a few requests of each kind, not timed
+            warm = S.make_requests(n, 8, rate=1e6, seed=99, spref_range=(6, 10), asgn_range=(10, 11))
+            S.run_serial(store, ex, warm)
+            torch.cuda.synchronize()
+            rq = [S.Request(r.rid, r.kind, r.arrival, I=r.I, labels_id=r.labels_id, edges=r.edges) for r in reqs]
+            if mode == "batched":
+                done, mk = S.Server(store, ex, slots=4, max_batch=16, mem_budget=24 << 30).run(rq)
+            else:
+                done, mk = S.run_serial(store, ex, rq)
+            res[mode] = S.latency_summary(done, mk)
+            del store, ex
+            torch.cuda.empty_cache()
+        out["runs"].append({"rate": rate, **res})
+    last = out["runs"][-1]
+    out["value"] = last["batched"]["req_per_s"]
+    print(json.dumps(out), flush=True)
+
+
 # ----------------------------------------------------------------- GPU arm
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
     import torch
 
     from paper_1109_3739_gb300 import hspgemm as h

@@ -138,6 +138,21 @@ int hs_spasgn(const hs_mat *A, const int32_t *I, int64_t nI, const int32_t *J, i
               const hs_mat *B, int accumulate, int add_semiring, hs_mat *C,
               const hs_allocator *al, void *stream, uint32_t flags);
 
+/* Many independent products C_i = A_i * B_i, i < count, in one pass of the
+ * pipeline (the batched form; Section 1's SpGEMM applied to a batch): the
+ * problems are stacked into one block-diagonal product, so rows of every
+ * problem share the same bins and launches, and the batch costs one launch
+ * per phase and two host synchronisations.  A[i], B[i]: CSR descriptors of
+ * device arrays (A[i].n == B[i].m; one dtype for all A, one for all B).  On
+ * return C is the stacked result (sum of A[i].m rows, max B[i].n columns,
+ * local column ids) allocated through `al`, and row_offsets (host array of
+ * count+1) gives problem i's rows [row_offsets[i], row_offsets[i+1]) of C.
+ * Semirings and dtypes as for hs_spgemm.  Errors: HS_EINVAL (shapes, mixed
+ * dtypes, NULL pointers), HS_EUNSUPPORTED (more than 2^31-1 stacked rows of
+ * B), HS_ENOMEM, HS_ECUDA, and those of hs_spgemm. */
+int hs_spgemm_batched(int semiring, int64_t count, const hs_mat *A, const hs_mat *B, hs_mat *C,
+                      int64_t *row_offsets, const hs_allocator *al, void *stream, uint32_t flags);
+
 /* SpGEMM for callers that cannot allocate device memory while they run (the
  * paper has no counterpart): for example code that has given the GPU's memory
  * to its own pool and must keep its footprint fixed, or code running where a

@@ -464,18 +464,17 @@ __device__ __forceinline__ void cta_products(const DevCsr &A, const DevCsr &B, i
   const int tid = threadIdx.x;
   for (int64_t c0 = q0; c0 < q1; c0 += CH) {
     const int n = (int)min((int64_t)CH, q1 - c0);
-    for (int e = tid; e < CH; e += blockDim.x) {
+    for (int e = tid; e < n; e += blockDim.x) {
       int64_t s = 0, en = 0;
-      if (e < n) {
-        entry_segment(A, B, c0 + e, restrict_cols, lo, hi, s, en);
-        if constexpr (SR::needs_a) sm.aval[e] = load_val<T>(A.v, c0 + e);
-      }
+      entry_segment(A, B, c0 + e, restrict_cols, lo, hi, s, en);
+      if constexpr (SR::needs_a) sm.aval[e] = load_val<T>(A.v, c0 + e);
       sm.excl[e] = (int)(en - s);
       sm.sbeg[e] = s;
     }
     __syncthreads();
-    const int total = group_excl_scan<CtaGroup>(sm.excl, CH, wtmp);
-    if (tid == 0) sm.excl[CH] = total;
+    // only the staged entries are scanned (a short row costs what it holds)
+    const int total = group_excl_scan<CtaGroup>(sm.excl, n, wtmp);
+    if (tid == 0) sm.excl[n] = total;
     __syncthreads();
     cta_expand_staged<SR>(B, sm.sbeg, sm.excl, sm.aval, n, total, visit);
     __syncthreads();

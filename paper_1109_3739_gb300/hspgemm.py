@@ -76,6 +76,9 @@ def _lib():
             L.hs_spasgn.argtypes = [P(hs_mat), vp, i64, vp, i64, P(hs_mat), ci, ci, P(hs_mat),
                                     P(hs_allocator), vp, u32]
             L.hs_spasgn.restype = ci
+            L.hs_spgemm_batched.argtypes = [ci, i64, P(hs_mat), P(hs_mat), P(hs_mat), P(ctypes.c_int64),
+                                             P(hs_allocator), vp, u32]
+            L.hs_spgemm_batched.restype = ci
             L.hs_spgemm_noalloc.argtypes = [ci, P(hs_mat), P(hs_mat), P(hs_mat), i64, vp]
             L.hs_spgemm_noalloc.restype = ci
             L.hs_mat_free.argtypes = [P(hs_mat), P(hs_allocator), vp]
@@ -223,6 +226,37 @@ def spgemm(semiring: str, A: DeviceCSR, B: DeviceCSR, validate: bool = False, st
     if st != 0:
         raise HsError(st, "hs_spgemm")
     return _adopt_output(al, c)
+
+
+def spgemm_batched(semiring: str, As: list, Bs: list, validate: bool = False, stream=None):
+    """C_i = A_i * B_i for every pair, in one pass (hs_spgemm_batched).
+
+    Returns (C, row_offsets): C is the stacked result (local column ids) and
+    problem i owns rows row_offsets[i]..row_offsets[i+1] of it.
+    """
+    L = _lib()
+    count = len(As)
+    if count != len(Bs):
+        raise ValueError("As and Bs differ in length")
+    dev = _device_of(As[0]) if count else _torch().device("cuda")
+    al = _TorchAlloc(dev)
+    A_arr = (hs_mat * max(count, 1))(*[x.desc() for x in As])
+    B_arr = (hs_mat * max(count, 1))(*[x.desc() for x in Bs])
+    offs = (ctypes.c_int64 * (count + 1))()
+    c = hs_mat()
+    st = L.hs_spgemm_batched(SEMIRING[semiring], count, A_arr, B_arr, ctypes.byref(c), offs,
+                             ctypes.byref(al.struct), _stream_ptr(stream), FLAG_VALIDATE if validate else 0)
+    if st != 0:
+        raise HsError(st, "hs_spgemm_batched")
+    return _adopt_output(al, c), np.array(offs[:], dtype=np.int64)
+
+
+def csr_rows(C: DeviceCSR, r0: int, r1: int, n: int | None = None) -> DeviceCSR:
+    """Rows r0..r1-1 of C as a CSR of their own (rebased offsets; copies the offsets only)."""
+    rp = C.rowptr[r0:r1 + 1]
+    a, b = int(rp[0]), int(rp[-1])
+    return DeviceCSR(r1 - r0, C.n if n is None else n, rp - a, C.col[a:b],
+                     None if C.val is None else C.val[a:b], C.dtype)
 
 
 def spgemm_noalloc(semiring: str, A: DeviceCSR, B: DeviceCSR, capacity: int, stream=None) -> DeviceCSR:

@@ -370,3 +370,40 @@ def random_unique_sequence(n: int, k: int, seed: int, stream: int = 9) -> np.nda
 def random_sequence(n: int, k: int, seed: int, stream: int = 10) -> np.ndarray:
     """k indices of 0..n-1 drawn with replacement (duplicates allowed), random order."""
     return _below(draws(seed, stream, 0, k), n).astype(np.int32)
+
+
+# ----------------------------------------------------------------------------- batches
+def batched_er_sizes(count: int, seed: int, nmin: int = 256, nmax: int = 65536, dmin: int = 2, dmax: int = 32):
+    """(n_i, d_i) of a batch of Erdos-Renyi problems: n_i = floor(exp(U[ln nmin, ln nmax])),
+    d_i uniform integer in [dmin, dmax] (one d_i for A_i and B_i)."""
+    u = uniform_f64(draws(seed, 20, 0, count))
+    n = np.floor(np.exp(np.log(nmin) + u * (np.log(nmax) - np.log(nmin)))).astype(np.int64)
+    n = np.clip(n, nmin, nmax)
+    d = _below(draws(seed, 21, 0, count), dmax - dmin + 1) + dmin
+    d = np.minimum(d, n)
+    return n, d
+
+
+def batched_er_problem(i: int, n: int, d: int, seed: int, dtype: str = "f64"):
+    """Problem i of a batch: square n x n A_i and B_i with d distinct nonzeros per column."""
+    base = (seed * 1000003 + i) * 2
+    return (er_matrix(n, n, d, seed=base + 1, dtype=dtype),
+            er_matrix(n, n, d, seed=base + 2, dtype=dtype))
+
+
+def _batched_worker(args):
+    i, n, d, seed, dtype = args
+    return batched_er_problem(i, n, d, seed, dtype)
+
+
+def batched_er(count: int, seed: int, dtype: str = "f64", nmax: int = 65536, workers: int = 0):
+    """All problems of a batch (list of (A_i, B_i)); workers > 1 generates them in
+    a spawn-context process pool (results identical to the serial order)."""
+    n, d = batched_er_sizes(count, seed, nmax=nmax)
+    jobs = [(i, int(n[i]), int(d[i]), seed, dtype) for i in range(count)]
+    if workers > 1 and count > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            return list(ex.map(_batched_worker, jobs, chunksize=max(1, count // (4 * workers))))
+    return [_batched_worker(j) for j in jobs]

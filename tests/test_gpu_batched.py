@@ -1,0 +1,87 @@
+"""hs_spgemm_batched against the CPU oracle, problem by problem.
+
+Small batches are compared in full for several semirings; the full batch of
+2000 Erdos-Renyi problems (n_i log-uniform in [256, 65536], 2..32 nonzeros per
+column, f64 (+,x)) is compared on sampled problems (the largest and a random
+sample), in the configuration the benchmark times.
+"""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1109_3739_gb300 import inputs as I
+from tests.helpers import assert_bitexact, assert_within
+
+pytestmark = pytest.mark.gpu
+NT = os.cpu_count() or 1
+
+
+def H():
+    from paper_1109_3739_gb300 import hspgemm
+    return hspgemm
+
+
+def check_problem(sr, C, offs, i, A, B):
+    h = H()
+    Ci = h.csr_rows(C, int(offs[i]), int(offs[i + 1]), n=B.n).to_host()
+    if sr == "plus_times" and A.dtype in ("f32", "f64"):
+        R, bound = oracle.spgemm(sr, A, B, with_bound=True, nthreads=NT)
+        assert_within(Ci, R, bound, A.dtype, f"problem {i}")
+    else:
+        assert_bitexact(Ci, oracle.spgemm(sr, A, B, nthreads=NT), f"problem {i}")
+
+
+@pytest.mark.parametrize("sr,dt", [("plus_times", "f64"), ("plus_times", "f32"), ("or_and", "bool"),
+                                   ("plus_times", "i64"), ("min_plus", "i32")])
+def test_small_batch_every_problem(sr, dt):
+    h = H()
+    probs = I.batched_er(40, seed=7, dtype=dt, nmax=2048)
+    As = [h.DeviceCSR.from_host(a) for a, _ in probs]
+    Bs = [h.DeviceCSR.from_host(b) for _, b in probs]
+    C, offs = h.spgemm_batched(sr, As, Bs, validate=True)
+    assert len(offs) == 41 and offs[-1] == sum(a.m for a, _ in probs)
+    for i, (A, B) in enumerate(probs):
+        check_problem(sr, C, offs, i, A, B)
+
+
+def test_batch_with_empty_and_rectangular_problems():
+    h = H()
+    probs = [
+        (I.er_matrix(30, 20, 3, seed=1), I.er_matrix(20, 50, 4, seed=2)),
+        (I.CSR(5, 7, np.zeros(6, np.int64), np.zeros(0, np.int32), np.zeros(0), "f64"),
+         I.er_matrix(7, 9, 2, seed=3)),
+        (I.er_matrix(11, 13, 2, seed=4), I.CSR(13, 3, np.zeros(14, np.int64), np.zeros(0, np.int32),
+                                               np.zeros(0), "f64")),
+        (I.er_matrix(64, 64, 8, seed=5), I.er_matrix(64, 64, 8, seed=6)),
+    ]
+    As = [h.DeviceCSR.from_host(a) for a, _ in probs]
+    Bs = [h.DeviceCSR.from_host(b) for _, b in probs]
+    C, offs = h.spgemm_batched("plus_times", As, Bs, validate=True)
+    for i, (A, B) in enumerate(probs):
+        check_problem("plus_times", C, offs, i, A, B)
+    C0, offs0 = h.spgemm_batched("plus_times", [], [])
+    assert C0.m == 0 and list(offs0) == [0]
+
+
+def test_full_batch_sampled():
+    """2000 problems at full size; the largest and 12 random problems against the oracle."""
+    h = H()
+    probs = I.batched_er(2000, seed=4, dtype="f64", workers=min(16, NT))
+    As = [h.DeviceCSR.from_host(a) for a, _ in probs]
+    Bs = [h.DeviceCSR.from_host(b) for _, b in probs]
+    C, offs = h.spgemm_batched("plus_times", As, Bs)
+    sizes = np.array([a.m for a, _ in probs])
+    pick = set(I.random_subset_sorted(2000, 12, 19).tolist()) | {int(np.argmax(sizes))}
+    for i in sorted(pick):
+        A, B = probs[i]
+        check_problem("plus_times", C, offs, i, A, B)
+    # every problem's row count matches the oracle's symbolic pass on a sample of rows
+    rp = C.rowptr.cpu().numpy()
+    for i in sorted(pick):
+        A, B = probs[i]
+        _, rn = oracle.spgemm_count(A, B, nthreads=NT)
+        np.testing.assert_array_equal(np.diff(rp[offs[i]:offs[i + 1] + 1]), rn)
