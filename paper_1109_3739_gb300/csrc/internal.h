@@ -114,6 +114,9 @@ struct SymArgs {
   int nseg;
   int *dyn;                // dynamic row counter (heavy)
   int *err;
+  unsigned *gbm;           // heavy rows' column bitmaps (bm_words per row), or null
+  int32_t *bslot;          // per row slot: index of its saved bitmap (-1 none)
+  int64_t bm_words;        // words per saved bitmap: ceil(n / 32)
 };
 void launch_sym_tiny(const SymArgs &a, cudaStream_t st);
 void launch_sym_warp(const SymArgs &a, cudaStream_t st);
@@ -138,6 +141,9 @@ struct NumArgs {
   int *err;
   int32_t *gcur;  // heavy bin: per-A-entry cursor into its B row (nnz(A) entries)
   int32_t *gend;  // heavy bin: end of the current part's segment
+  const unsigned *gbm;    // saved column bitmaps of the symbolic heavy rows, or null
+  const int32_t *bslot;   // per row slot: its saved bitmap (-1 none)
+  int64_t bm_words;
 };
 // kind: 0 tiny, 1 warp, 2 mid, 3 large, 4 heavy.  dtype codes as in the ABI.
 bool launch_numeric_pt(int dtype, int kind, const NumArgs &a, cudaStream_t st);

@@ -200,7 +200,7 @@ static int spgemm_noalloc_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat 
     NA_CK(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)nhist * nseg, st));
   }
 
-  SymArgs sa{rs, rb, f, nullptr, 0, Cp, hslot, hist, nseg, &sb->dyn[0], &sb->err};
+  SymArgs sa{rs, rb, f, nullptr, 0, Cp, hslot, hist, nseg, &sb->dyn[0], &sb->err, nullptr, nullptr, 0};
   auto sym_bin = [&](int k0, int k1) {
     sa.list = list + key_off[k0];
     sa.count = key_off[k1] - key_off[k0];
@@ -238,7 +238,8 @@ static int spgemm_noalloc_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat 
     gend = ar.take<int32_t>((size_t)A->nnz);
     if (ar.over) return HS_ESCRATCH;
   }
-  NumArgs na{rs, rb, f, nullptr, 0, Cp, C->idx, C->val, hslot, hist, nseg, &sb->dyn[1], &sb->err, gcur, gend};
+  NumArgs na{rs,   rb,   f,    nullptr,     0,        Cp,   C->idx, C->val,  hslot,
+             hist, nseg, &sb->dyn[1], &sb->err, gcur, gend, nullptr, nullptr, 0};
   const int k0s[5] = {KEY_TINY, KEY_WARP, KEY_MID, KEY_LARGE, KEY_HEAVY};
   const int k1s[5] = {KEY_TINY + 1, KEY_WARP + 1, KEY_MID + 1, KEY_LARGE + 1, NKEYS};
   for (int kind = 0; kind < 5; ++kind) {

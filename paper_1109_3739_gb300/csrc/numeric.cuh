@@ -170,7 +170,7 @@ template <typename T, int SLOTS, int CAP> struct CtaNumLayout {
 };
 
 template <class SR, int SLOTS, int CAP>
-__global__ void __launch_bounds__(CAP > 2048 ? 1024 : 256) k_num_cta(NumArgs a) {
+__global__ void __launch_bounds__(CAP > 2048 ? 1024 : 256, 1) k_num_cta(NumArgs a) {
   using T = typename SR::val_t;
   using L = CtaNumLayout<T, SLOTS, CAP>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -275,6 +275,9 @@ __global__ void __launch_bounds__(HV_NT, 2) k_num_heavy(NumArgs a) {
     const uint32_t *hist = a.hist + (int64_t)(h < 0 ? 0 : h) * a.nseg;
     const int64_t q0 = A.p[r], q1 = r_ok ? A.p[r + 1] : q0;
     const int nrounds = (int)((q1 - q0 + HV_CH - 1) / HV_CH);
+    // the row's column bitmap saved by the symbolic pass, if any
+    const int bs = (r_ok && a.gbm) ? a.bslot[r] : -1;
+    const unsigned *bm = bs >= 0 ? a.gbm + (int64_t)bs * a.bm_words : nullptr;
     for (int64_t q = q0 + tid; q < q1; q += HV_NT) gcur[q] = 0;
     // the row's parts, chosen greedily from its segment counts: at most CAPH
     // outputs and HV_WMAX columns each
@@ -326,44 +329,50 @@ __global__ void __launch_bounds__(HV_NT, 2) k_num_heavy(NumArgs a) {
         const int lo = seg * SEG_W;
         const int hi = (int)min((int64_t)pe * SEG_W, n);
         const int words = (hi - lo + 31) >> 5;
-        for (int w = tid; w < words; w += HV_NT) sm.bitmap[w] = 0u;
-        // ---- pass 1: occupancy
+        // ---- occupancy: the saved bitmap of the symbolic pass, or pass 1
+        if (bm) {
+          const unsigned *src = bm + (lo >> 5);
+          for (int w = tid; w < words; w += HV_NT) sm.bitmap[w] = __ldg(src + w);
+        } else {
+          for (int w = tid; w < words; w += HV_NT) sm.bitmap[w] = 0u;
+        }
         int total = 0;
         for (int rd = 0; rd < nrounds; ++rd) {
           const int64_t rq0 = q0 + (int64_t)rd * HV_CH;
           const int cnt = (int)min((int64_t)HV_CH, q1 - rq0);
           __syncthreads();
-          for (int e = tid; e < HV_CH; e += HV_NT) {
+          for (int e = tid; e < cnt; e += HV_NT) {
             int64_t s = 0;
             int len = 0;
-            if (e < cnt) {
-              const int64_t q = rq0 + e;
-              const int k = __ldg(A.j + q);
-              if (HS_G(dbg, k >= 0 && k < B.rows, 2, k)) {
-                const int64_t base = __ldg(B.p + k), end = __ldg(B.p + k + 1);
-                s = base + gcur[q];
-                const int64_t se = interp_lower_bound(B.j, s, end, hi);
-                len = (int)(se - s);
-                gend[q] = (int32_t)(se - base);
-                if (nrounds == 1) {
-                  gcur[q] = (int32_t)(se - base);
-                  if constexpr (SR::needs_a) sm.aval[e] = load_val<T>(A.v, q);
-                }
+            const int64_t q = rq0 + e;
+            const int k = __ldg(A.j + q);
+            if (HS_G(dbg, k >= 0 && k < B.rows, 2, k)) {
+              const int64_t base = __ldg(B.p + k), end = __ldg(B.p + k + 1);
+              s = base + gcur[q];
+              const int64_t se = interp_lower_bound(B.j, s, end, hi);
+              len = (int)(se - s);
+              gend[q] = (int32_t)(se - base);
+              if (nrounds == 1) {
+                gcur[q] = (int32_t)(se - base);
+                if constexpr (SR::needs_a) sm.aval[e] = load_val<T>(A.v, q);
               }
             }
             sm.excl[e] = len;
             sm.sbeg[e] = s;
           }
+          if (bm && nrounds > 1) continue;  // only the part ends are needed (pass 2 restages)
           __syncthreads();
-          total = group_excl_scan<CtaGroup>(sm.excl, HV_CH, sm.wtmp);
-          if (tid == 0) sm.excl[HV_CH] = total;
+          total = group_excl_scan<CtaGroup>(sm.excl, cnt, sm.wtmp);
+          if (tid == 0) sm.excl[cnt] = total;
           __syncthreads();
-          auto set_bit = [&](int col, NoVal, int) {
-            const int x = col - lo;
-            if (HS_G(dbg, x >= 0 && x < hi - lo, 60, col)) atomicOr(sm.bitmap + (x >> 5), 1u << (x & 31));
-          };
-          cta_expand_staged<StructOf<SR>>(B, sm.sbeg, sm.excl, reinterpret_cast<const NoVal *>(sm.aval), cnt,
-                                          total, set_bit);
+          if (!bm) {
+            auto set_bit = [&](int col, NoVal, int) {
+              const int x = col - lo;
+              if (HS_G(dbg, x >= 0 && x < hi - lo, 60, col)) atomicOr(sm.bitmap + (x >> 5), 1u << (x & 31));
+            };
+            cta_expand_staged<StructOf<SR>>(B, sm.sbeg, sm.excl, reinterpret_cast<const NoVal *>(sm.aval), cnt,
+                                            total, set_bit);
+          }
         }
         __syncthreads();
         // ---- rank: prefix of set bits per word, in runs of 32 words per warp
@@ -402,26 +411,24 @@ __global__ void __launch_bounds__(HV_NT, 2) k_num_heavy(NumArgs a) {
               const int64_t rq0 = q0 + (int64_t)rd * HV_CH;
               const int cnt = (int)min((int64_t)HV_CH, q1 - rq0);
               __syncthreads();
-              for (int e = tid; e < HV_CH; e += HV_NT) {
+              for (int e = tid; e < cnt; e += HV_NT) {
                 int64_t s = 0;
                 int len = 0;
-                if (e < cnt) {
-                  const int64_t q = rq0 + e;
-                  const int k = __ldg(A.j + q);
-                  if (HS_G(dbg, k >= 0 && k < B.rows, 2, k)) {
-                    const int64_t base = __ldg(B.p + k);
-                    s = base + gcur[q];
-                    len = gend[q] - gcur[q];
-                    gcur[q] = gend[q];
-                    if constexpr (SR::needs_a) sm.aval[e] = load_val<T>(A.v, q);
-                  }
+                const int64_t q = rq0 + e;
+                const int k = __ldg(A.j + q);
+                if (HS_G(dbg, k >= 0 && k < B.rows, 2, k)) {
+                  const int64_t base = __ldg(B.p + k);
+                  s = base + gcur[q];
+                  len = gend[q] - gcur[q];
+                  gcur[q] = gend[q];
+                  if constexpr (SR::needs_a) sm.aval[e] = load_val<T>(A.v, q);
                 }
                 sm.excl[e] = len;
                 sm.sbeg[e] = s;
               }
               __syncthreads();
-              total = group_excl_scan<CtaGroup>(sm.excl, HV_CH, sm.wtmp);
-              if (tid == 0) sm.excl[HV_CH] = total;
+              total = group_excl_scan<CtaGroup>(sm.excl, cnt, sm.wtmp);
+              if (tid == 0) sm.excl[cnt] = total;
               __syncthreads();
               auto add_val = [&](int col, T v, int) {
                 const int x = col - lo;

@@ -349,8 +349,32 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
     CK(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)nhist * nseg, st));
   }
 
+  // heavy rows keep their symbolic column bitmaps for the numeric pass when
+  // they fit a quarter of the free device memory (at most 32 GiB)
+  unsigned *gbm = nullptr;
+  int32_t *bslot = nullptr;
+  const int64_t bm_words = (n + 31) / 32;
+  {
+    const int64_t nsh = key_off[NKEYS] - key_off[KEY_HEAVY];
+    size_t free_b = 0, total_b = 0;
+    if (nsh > 0 && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+      const size_t bytes = (size_t)nsh * (size_t)bm_words * 4;
+      const size_t budget = free_b / 4 < ((size_t)32 << 30) ? free_b / 4 : ((size_t)32 << 30);
+      if (bytes <= budget) {
+        gbm = (unsigned *)mem.raw(bytes);
+        bslot = gbm ? (int32_t *)mem.raw(sizeof(int32_t) * (size_t)nslots) : nullptr;
+        if (gbm) mem.scratch.push_back({gbm, bytes});
+        if (bslot) mem.scratch.push_back({bslot, sizeof(int32_t) * (size_t)nslots});
+        mem.failed = false;  // an optional buffer: without it the numeric pass rebuilds the bitmaps
+        if (!bslot) gbm = nullptr;
+        else CK(cudaMemsetAsync(bslot, 0xff, sizeof(int32_t) * (size_t)nslots, st));
+      }
+    }
+    cudaGetLastError();
+  }
+
   // ---- symbolic
-  SymArgs sa{rs, rb, f, nullptr, 0, Cp, hslot, hist, nseg, &sb->dyn[0], &sb->err};
+  SymArgs sa{rs, rb, f, nullptr, 0, Cp, hslot, hist, nseg, &sb->dyn[0], &sb->err, gbm, bslot, bm_words};
   auto sym_bin = [&](int k0, int k1) {
     sa.list = list + key_off[k0];
     sa.count = key_off[k1] - key_off[k0];
@@ -416,7 +440,8 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
     gend = mem.tmp<int32_t>((size_t)A->nnz);
     if (!gcur || !gend) return HS_ENOMEM;
   }
-  NumArgs na{rs, rb, f, nullptr, 0, Cp, C->idx, C->val, hslot, hist, nseg, &sb->dyn[1], &sb->err, gcur, gend};
+  NumArgs na{rs, rb,   f,    nullptr, 0,    Cp,    C->idx, C->val, hslot,
+             hist, nseg, &sb->dyn[1], &sb->err, gcur, gend, gbm, bslot, bm_words};
   const char *names[5] = {"numeric_tiny", "numeric_warp", "numeric_mid", "numeric_large", "numeric_heavy"};
   const int k0s[5] = {KEY_TINY, KEY_WARP, KEY_MID, KEY_LARGE, KEY_HEAVY};
   const int k1s[5] = {KEY_TINY + 1, KEY_WARP + 1, KEY_MID + 1, KEY_LARGE + 1, NKEYS};

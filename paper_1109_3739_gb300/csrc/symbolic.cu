@@ -155,7 +155,7 @@ struct SymHeavySmem {
   unsigned bitmap[BITMAP_COLS / 32];
 };
 
-__global__ void __launch_bounds__(1024) k_sym_heavy(SymArgs a) {
+__global__ void __launch_bounds__(1024, 1) k_sym_heavy(SymArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto &sm = *reinterpret_cast<SymHeavySmem *>(smem_raw);
   const DevCsr A = dev_a(a.A), B = dev_b(a.B);
@@ -192,10 +192,14 @@ __global__ void __launch_bounds__(1024) k_sym_heavy(SymArgs a) {
                                    if (HS_G(a.A.dbg, x >= 0 && x < hi - lo, 33, col))
                                      atomicOr(sm.bitmap + (x >> 5), 1u << (x & 31));
                                  });
-      // count: each warp takes 32 consecutive words (1024 columns, inside one segment)
+      // count: each warp takes 32 consecutive words (1024 columns, inside one segment);
+      // the words are also saved for the numeric pass when a bitmap store is given
+      unsigned *save = (a.gbm && r_ok) ? a.gbm + (int64_t)idx * a.bm_words + (lo >> 5) : nullptr;
       for (int wb = warp * 32; wb < words; wb += nw * 32) {
         const int wd = wb + lane;
-        int c = wd < words ? __popc(sm.bitmap[wd]) : 0;
+        const unsigned bits = wd < words ? sm.bitmap[wd] : 0u;
+        if (save && wd < words) save[wd] = bits;
+        int c = __popc(bits);
         c = warp_sum(c);
         if (lane == 0 && c) {
           cnt += c;
@@ -212,7 +216,10 @@ __global__ void __launch_bounds__(1024) k_sym_heavy(SymArgs a) {
     __syncthreads();
     if (hist && seg_smem)
       for (int g = threadIdx.x; g < a.nseg; g += blockDim.x) hist[g] = sm.segcnt[g];
-    if (threadIdx.x == 0 && r_ok) put_count(a, out_row(a.A, r), sm.total);
+    if (threadIdx.x == 0 && r_ok) {
+      put_count(a, out_row(a.A, r), sm.total);
+      if (a.gbm) a.bslot[r] = idx;
+    }
     __syncthreads();
   }
 }
