@@ -39,16 +39,17 @@ static int grid_for(int64_t items, int per_block, int max_per_sm) {
 }
 
 // ------------------------------------------------------------------ flops
-// stats[0] += total flops, stats[1] = max row flops, stats[2] = max row nnz of A
-__global__ void k_flops(RowSet A, RightOp B, int64_t *f, int *key_cnt, unsigned long long *stats) {
+// stats[0] += total flops, stats[1] = max row flops, stats[2] = max row nnz
+// of A, stats[3] += min(f, n) over rows of the symbolic heavy bin
+__global__ void k_flops(RowSet A, RightOp B, int64_t *f, int *key_cnt, unsigned long long *stats, int cap_large) {
   __shared__ int hist[NKEYS];
-  __shared__ unsigned long long blk_tot, blk_max, blk_amax;
+  __shared__ unsigned long long blk_tot, blk_max, blk_amax, blk_heavy;
   for (int i = threadIdx.x; i < NKEYS; i += blockDim.x) hist[i] = 0;
-  if (threadIdx.x == 0) blk_tot = blk_max = blk_amax = 0;
+  if (threadIdx.x == 0) blk_tot = blk_max = blk_amax = blk_heavy = 0;
   __syncthreads();
   const int lane = lane_id();
   const int64_t wpb = blockDim.x >> 5;
-  unsigned long long my_tot = 0, my_max = 0, my_amax = 0;
+  unsigned long long my_tot = 0, my_max = 0, my_amax = 0, my_heavy = 0;
   for (int64_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < A.nslots; r += (int64_t)gridDim.x * wpb) {
     const int64_t q0 = A.p[r], q1 = A.p[r + 1];
     long long s = 0;
@@ -60,8 +61,9 @@ __global__ void k_flops(RowSet A, RightOp B, int64_t *f, int *key_cnt, unsigned 
     s = warp_sum(s);
     if (lane == 0) {
       f[r] = s;
-      const int key = sym_key(s);
+      const int key = sym_key(s, cap_large);
       if (key) atomicAdd(hist + key, 1);
+      if (key >= KEY_HEAVY) my_heavy += (unsigned long long)min((int64_t)s, B.n);
       my_tot += (unsigned long long)s;
       my_max = max(my_max, (unsigned long long)s);
       my_amax = max(my_amax, (unsigned long long)(q1 - q0));
@@ -71,6 +73,7 @@ __global__ void k_flops(RowSet A, RightOp B, int64_t *f, int *key_cnt, unsigned 
     atomicAdd(&blk_tot, my_tot);
     atomicMax(&blk_max, my_max);
     atomicMax(&blk_amax, my_amax);
+    atomicAdd(&blk_heavy, my_heavy);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < NKEYS; i += blockDim.x)
@@ -79,14 +82,57 @@ __global__ void k_flops(RowSet A, RightOp B, int64_t *f, int *key_cnt, unsigned 
     atomicAdd(stats + 0, blk_tot);
     atomicMax(stats + 1, blk_max);
     atomicMax(stats + 2, blk_amax);
+    atomicAdd(stats + 3, blk_heavy);
   }
 }
 
 void launch_flops(const RowSet &A, const RightOp &B, int64_t *f, int *key_cnt, unsigned long long *stats,
-                  cudaStream_t st) {
+                  int cap_large, cudaStream_t st) {
   if (A.nslots == 0) return;
   count_launch();
-  k_flops<<<grid_for(A.nslots, 8, 16), 256, 0, st>>>(A, B, f, key_cnt, stats);
+  k_flops<<<grid_for(A.nslots, 8, 16), 256, 0, st>>>(A, B, f, key_cnt, stats, cap_large);
+}
+
+// ---------------------------------------------------- B segment index
+// One warp per B row.  Rows longer than min_len take the next table row and
+// record, for every segment g = 0..nseg, the offset of their first entry with
+// column >= g*SEG_W (nseg gives the row length).  Entry p fills the segments
+// after its predecessor's up to its own; the last entry fills the rest.
+__global__ void k_build_bci(RightOp B, int nseg, int min_len, int64_t max_rows, int32_t *bci_id, int32_t *bci,
+                            int *counter) {
+  const int lane = lane_id();
+  const int64_t wpb = blockDim.x >> 5;
+  const int64_t stride = (int64_t)nseg + 1;
+  for (int64_t k = blockIdx.x * wpb + (threadIdx.x >> 5); k < B.m; k += (int64_t)gridDim.x * wpb) {
+    const int64_t b0 = B.p[k], b1 = B.p[k + 1];
+    const int64_t len = b1 - b0;
+    int t = -1;
+    if (len > min_len && lane == 0) {
+      t = atomicAdd(counter, 1);
+      if (t >= max_rows) t = -1;
+    }
+    t = __shfl_sync(FULL, t, 0);
+    if (lane == 0) bci_id[k] = t;
+    if (t < 0) continue;
+    int32_t *row = bci + (int64_t)t * stride;
+    for (int64_t q = lane; q < len; q += 32) {
+      if (!HS_G(B.dbg, b0 + q < B.nnz, 53, b0 + q)) break;
+      const int c = B.j[b0 + q];
+      if (!HS_G(B.dbg, c >= 0 && c < B.n, 54, c)) break;
+      const int g = c / SEG_W;
+      const int gp = q ? B.j[b0 + q - 1] / SEG_W : -1;
+      for (int x = gp + 1; x <= g && x <= nseg; ++x) row[x] = (int32_t)q;
+      if (q == len - 1)
+        for (int x = g + 1; x <= nseg; ++x) row[x] = (int32_t)len;
+    }
+  }
+}
+
+void launch_build_bci(const RightOp &B, int nseg, int min_len, int64_t max_rows, int32_t *bci_id, int32_t *bci,
+                      int *counter, cudaStream_t st) {
+  if (B.m <= 0) return;
+  count_launch();
+  k_build_bci<<<grid_for(B.m, 8, 16), 256, 0, st>>>(B, nseg, min_len, max_rows, bci_id, bci, counter);
 }
 
 // one warp: exclusive scan of the NKEYS counters into offsets and cursors
@@ -125,7 +171,7 @@ __global__ void k_scatter_sym(RowSet A, const int64_t *f, int *key_cur, int *lis
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < A.nslots;
        r += (int64_t)gridDim.x * blockDim.x) {
     const int64_t fr = f[r];
-    const int key = sym_key(fr);
+    const int key = sym_key(fr, hist_threshold);
     if (key) append_row(key, (int)r, key_cur, list, A.nslots, A.dbg);
     // rows that may need column parts in the numeric pass get a histogram slot
     const bool h = fr > hist_threshold;

@@ -13,6 +13,7 @@
 //     memory and coalesced stores of the finished row.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace hs {
@@ -219,6 +220,14 @@ template <typename T> __device__ __forceinline__ T load_val(const void *v, int64
 }
 template <> __device__ __forceinline__ NoVal load_val<NoVal>(const void *, int64_t) { return NoVal{}; }
 
+// A visitor may split its work in two: prep(col) does the reads (and any
+// atomic whose result it needs) and returns a state; commit(state, value)
+// does the final write.  The long-segment loop then preps all of a step's
+// products before committing any, so their shared-memory round trips overlap
+// instead of queueing behind each other's atomics.
+template <class V, class = void> struct two_stage : std::false_type {};
+template <class V> struct two_stage<V, std::void_t<decltype(V::kTwoStage)>> : std::bool_constant<V::kTwoStage> {};
+
 template <typename T> __device__ __forceinline__ T shfl_val(T x, int src) { return __shfl_sync(FULL, x, src); }
 template <> __device__ __forceinline__ NoVal shfl_val<NoVal>(NoVal x, int) { return x; }
 
@@ -232,7 +241,7 @@ template <> __device__ __forceinline__ NoVal shfl_val<NoVal>(NoVal x, int) { ret
 // lane that holds a product, p being the product's index in the order of the
 // segments (as if they were walked lane by lane).  Returns the number of
 // products.  All 32 lanes must call this together.
-template <class SR, class Visit>
+template <class SR, int U = 2, class Visit>
 __device__ __forceinline__ int warp_expand(const DevCsr &B, int64_t s, int len, typename SR::val_t a,
                                             Visit &visit) {
   using T = typename SR::val_t;
@@ -240,7 +249,8 @@ __device__ __forceinline__ int warp_expand(const DevCsr &B, int64_t s, int len, 
   const int incl = warp_incl_scan(len);
   const int total = __shfl_sync(FULL, incl, 31);
   const int ex_full = incl - len;
-  // long segments: the whole warp on one segment
+  // long segments: the whole warp on one segment, U entries per lane per
+  // step (all loads of a step issued before the first visit)
   unsigned longm = __ballot_sync(FULL, len >= 32);
   while (longm) {
     const int l = __ffs(longm) - 1;
@@ -249,23 +259,38 @@ __device__ __forceinline__ int warp_expand(const DevCsr &B, int64_t s, int len, 
     const int ll = __shfl_sync(FULL, len, l);
     const int el = __shfl_sync(FULL, ex_full, l);
     const T al = shfl_val<T>(a, l);
-    for (int off = lane; off < ll; off += 64) {
-      const int64_t p0 = sl + off, p1 = p0 + 32;
-      const bool ok1 = off + 32 < ll;
-      if (!HS_G(B.dbg, p0 >= 0 && p0 < B.nnz && (!ok1 || p1 < B.nnz), 4, p0)) continue;
-      const int c0 = __ldg(B.j + p0);
-      const int c1 = ok1 ? __ldg(B.j + p1) : 0;
-      if constexpr (SR::has_val) {
-        T b0{}, b1{};
-        if constexpr (SR::needs_b) {
-          b0 = load_val<T>(B.v, p0);
-          if (ok1) b1 = load_val<T>(B.v, p1);
+    if (!HS_G(B.dbg, sl >= 0 && sl + ll <= B.nnz, 4, sl)) continue;
+    const int32_t *bj = B.j + sl;
+    const T *bv = reinterpret_cast<const T *>(B.v) + sl;
+    for (int off = lane; off < ll; off += 32 * U) {
+      int c[U];
+      T b[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const bool ok = off + 32 * u < ll;
+        c[u] = ok ? __ldg(bj + off + 32 * u) : 0;
+        b[u] = T{};
+        if constexpr (SR::needs_b)
+          if (ok) b[u] = __ldg(bv + off + 32 * u);
+      }
+      if constexpr (two_stage<std::decay_t<Visit>>::value) {
+        typename std::decay_t<Visit>::State st[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (off + 32 * u < ll) st[u] = visit.prep(c[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (off + 32 * u >= ll) break;
+          if constexpr (SR::has_val) visit.commit(st[u], SR::mul(al, b[u]));
+          else visit.commit(st[u], NoVal{});
         }
-        visit(c0, SR::mul(al, b0), el + off);
-        if (ok1) visit(c1, SR::mul(al, b1), el + off + 32);
       } else {
-        visit(c0, NoVal{}, el + off);
-        if (ok1) visit(c1, NoVal{}, el + off + 32);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (off + 32 * u >= ll) break;
+          if constexpr (SR::has_val) visit(c[u], SR::mul(al, b[u]), el + off + 32 * u);
+          else visit(c[u], NoVal{}, el + off + 32 * u);
+        }
       }
     }
   }
@@ -339,6 +364,22 @@ __device__ __forceinline__ void warp_products(const DevCsr &A, const DevCsr &B, 
   }
 }
 
+// Ask for [p, p + bytes) to be brought into L2 ahead of its reads (bulk
+// prefetch, no completion to wait for).  The range is narrowed to 16-byte
+// boundaries, so it never leaves the buffer, and issued in pieces of at most
+// 64 KB.
+__device__ __forceinline__ void prefetch_l2(const void *p, int64_t bytes) {
+  if (bytes <= 0) return;
+  uint64_t a = (uint64_t)__cvta_generic_to_global(p);
+  const uint64_t e = (a + (uint64_t)bytes) & ~(uint64_t)15;
+  a = (a + 15) & ~(uint64_t)15;
+  while (a < e) {
+    const uint64_t len = e - a < 65536 ? e - a : 65536;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((unsigned)len) : "memory");
+    a += len;
+  }
+}
+
 __host__ __device__ __forceinline__ int next_pow2(int x) {
   int p = 1;
   while (p < x) p <<= 1;
@@ -357,7 +398,7 @@ template <typename T, int CH> struct CtaExpandSmem {
 // the warps of the CTA: each warp takes one contiguous range of the products
 // and deals it one product per lane (warp_expand).  Reads the staged arrays
 // only; all threads of the CTA must call it together.
-template <class SR, class Visit>
+template <class SR, int U = 2, class Visit>
 __device__ __forceinline__ void cta_expand_staged(const DevCsr &B, const int64_t *sbeg, const int *excl,
                                                   const typename SR::val_t *aval, int n, int total,
                                                   Visit &visit) {
@@ -387,7 +428,7 @@ __device__ __forceinline__ void cta_expand_staged(const DevCsr &B, const int64_t
         if constexpr (SR::needs_a) a = aval[e];
       }
     }
-    warp_expand<SR>(B, s, len, a, visit);
+    warp_expand<SR, U>(B, s, len, a, visit);
     if (eb + 32 >= n || excl[eb + 32] >= pe) break;
   }
 }
@@ -456,7 +497,7 @@ __device__ __forceinline__ int64_t gallop_lower_bound(const int32_t *j, int64_t 
 // round are cut into one contiguous range per warp, and each warp deals its
 // range one product per lane (warp_expand).  Per-row product counts must stay
 // below 2^31.  All threads of the CTA must call this together.
-template <class SR, int CH, class Visit>
+template <class SR, int CH, int U = 2, class Visit>
 __device__ __forceinline__ void cta_products(const DevCsr &A, const DevCsr &B, int64_t q0, int64_t q1, bool restrict_cols,
                              int lo, int hi, CtaExpandSmem<typename SR::val_t, CH> &sm, int *wtmp,
                              Visit &&visit) {
@@ -476,7 +517,7 @@ __device__ __forceinline__ void cta_products(const DevCsr &A, const DevCsr &B, i
     const int total = group_excl_scan<CtaGroup>(sm.excl, n, wtmp);
     if (tid == 0) sm.excl[n] = total;
     __syncthreads();
-    cta_expand_staged<SR>(B, sm.sbeg, sm.excl, sm.aval, n, total, visit);
+    cta_expand_staged<SR, U>(B, sm.sbeg, sm.excl, sm.aval, n, total, visit);
     __syncthreads();
   }
 }

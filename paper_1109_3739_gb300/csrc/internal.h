@@ -15,7 +15,7 @@ constexpr int NKEYS = 64;
 constexpr int KEY_TINY = 1;   // f <= 32: warp, one product per lane
 constexpr int KEY_WARP = 2;   // f <= 512: warp, private shared hash table
 constexpr int KEY_MID = 3;    // symbolic: f <= 4096;  numeric: c <= CAP_MID
-constexpr int KEY_LARGE = 4;  // symbolic: f <= 16384; numeric: c <= cap_large
+constexpr int KEY_LARGE = 4;  // symbolic: f <= min(16384, cap_large); numeric: c <= cap_large
 constexpr int KEY_HEAVY = 5;  // 5 + (62 - floor(log2 f)): symbolic bitmap / numeric column parts
 constexpr int F_TINY = 32, F_WARP = 512, F_MID = 4096, F_LARGE = 16384;
 constexpr int CAP_MID = 2048;
@@ -33,12 +33,15 @@ __host__ __device__ inline int floor_log2_u64(uint64_t x) {
 #endif
 }
 __host__ __device__ inline int heavy_key(int64_t f) { return KEY_HEAVY + (62 - floor_log2_u64((uint64_t)f)); }
-__host__ __device__ inline int sym_key(int64_t f) {
+// Symbolic bins.  Every row that may end in the numeric heavy bin (c >
+// cap_large needs f > cap_large) takes the bitmap kernel, which also writes
+// the row's sorted column list for the numeric pass.
+__host__ __device__ inline int sym_key(int64_t f, int cap_large) {
   if (f <= 0) return 0;
   if (f <= F_TINY) return KEY_TINY;
   if (f <= F_WARP) return KEY_WARP;
   if (f <= F_MID) return KEY_MID;
-  if (f <= F_LARGE) return KEY_LARGE;
+  if (f <= F_LARGE && f <= cap_large) return KEY_LARGE;
   return heavy_key(f);
 }
 __host__ __device__ inline int num_key(int64_t f, int64_t c, int cap_large) {
@@ -85,10 +88,13 @@ template <class K> inline void set_smem_attr(K kernel, size_t bytes) {
 
 // --------------------------------------------------------------- launchers
 // analysis.cu
+// stats[0] total flops, [1] max row flops, [2] max row nnz of A, [3] sum of
+// min(f, n) over the rows of the symbolic heavy bin (their list pool bound)
 void launch_flops(const RowSet &A, const RightOp &B, int64_t *f, int *key_cnt, unsigned long long *stats,
-                  cudaStream_t st);
+                  int cap_large, cudaStream_t st);
 void launch_key_offsets(const int *key_cnt, int *key_off, int *key_cur, cudaStream_t st);
-// rows with more than hist_threshold products get a column-segment histogram slot
+// rows with more than hist_threshold (= cap_large) products get a column-segment
+// histogram slot; the same bound ends the symbolic large bin (sym_key)
 void launch_scatter_sym(const RowSet &A, const int64_t *f, int *key_cur, int *list, int32_t *hslot,
                         int *nhist, int hist_threshold, cudaStream_t st);
 void launch_num_count(const RowSet &A, const int64_t *f, const int64_t *Cp, int cap_large, int *key_cnt,
@@ -97,6 +103,12 @@ void launch_scatter_num(const RowSet &A, const int64_t *f, const int64_t *Cp, in
                         int *list, cudaStream_t st);
 void launch_scan_i64(int64_t *a, int64_t n, int64_t *tmp, cudaStream_t st);  // exclusive, in place
 int64_t scan_tmp_elems(int64_t n);
+// B segment index: for every B row longer than `min_len`, the offset (within
+// the row) of its first entry in each SEG_W-column segment, nseg+1 values
+// (the last is the row length).  Rows get consecutive table rows through
+// *counter; at most max_rows of them are indexed.
+void launch_build_bci(const RightOp &B, int nseg, int min_len, int64_t max_rows, int32_t *bci_id, int32_t *bci,
+                      int *counter, cudaStream_t st);
 void launch_validate(const int64_t *p, const int32_t *j, int64_t rows, int64_t ncols, int *flag, cudaStream_t st);
 void launch_sm_count_init();
 int sm_count();
@@ -114,9 +126,10 @@ struct SymArgs {
   int nseg;
   int *dyn;                // dynamic row counter (heavy)
   int *err;
-  unsigned *gbm;           // heavy rows' column bitmaps (bm_words per row), or null
-  int32_t *bslot;          // per row slot: index of its saved bitmap (-1 none)
-  int64_t bm_words;        // words per saved bitmap: ceil(n / 32)
+  int32_t *glist;          // heavy rows' sorted column lists (pool of lcap entries), or null
+  int64_t *loff;           // per row slot: start of its list in the pool (-1 none)
+  unsigned long long *lpool;  // pool cursor (entries handed out)
+  int64_t lcap;
 };
 void launch_sym_tiny(const SymArgs &a, cudaStream_t st);
 void launch_sym_warp(const SymArgs &a, cudaStream_t st);
@@ -141,9 +154,10 @@ struct NumArgs {
   int *err;
   int32_t *gcur;  // heavy bin: per-A-entry cursor into its B row (nnz(A) entries)
   int32_t *gend;  // heavy bin: end of the current part's segment
-  const unsigned *gbm;    // saved column bitmaps of the symbolic heavy rows, or null
-  const int32_t *bslot;   // per row slot: its saved bitmap (-1 none)
-  int64_t bm_words;
+  const int32_t *glist;   // sorted column lists written by the symbolic heavy pass, or null
+  const int64_t *loff;    // per row slot: its list (-1 none)
+  const int32_t *bci_id;  // per B row: its row of the segment index (-1 none), or null
+  const int32_t *bci;     // segment index: nseg+1 offsets per indexed B row
 };
 // kind: 0 tiny, 1 warp, 2 mid, 3 large, 4 heavy.  dtype codes as in the ABI.
 bool launch_numeric_pt(int dtype, int kind, const NumArgs &a, cudaStream_t st);

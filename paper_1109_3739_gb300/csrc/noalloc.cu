@@ -182,7 +182,7 @@ static int spgemm_noalloc_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat 
   RowSet rs{A->ptr, A->idx, A->val, A->fmt == HS_DCSR ? A->ids : nullptr, nslots, A->nnz, m, sb->dbg};
   RightOp rb{B->ptr, B->idx, B->val, n, B->m, B->nnz, sb->dbg};
   NA_CK(cudaMemsetAsync(sb, 0, sizeof(NaBlock), st));
-  launch_flops(rs, rb, f, sb->key_cnt, sb->stats, st);
+  launch_flops(rs, rb, f, sb->key_cnt, sb->stats, vb == 8 ? 4096 : 8192, st);
   launch_key_offsets(sb->key_cnt, sb->key_off, sb->key_cur, st);
   launch_scatter_sym(rs, f, sb->key_cur, list, hslot, &sb->nhist, vb == 8 ? 4096 : 8192, st);
   if (int e = check_last()) return e;
@@ -200,7 +200,7 @@ static int spgemm_noalloc_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat 
     NA_CK(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)nhist * nseg, st));
   }
 
-  SymArgs sa{rs, rb, f, nullptr, 0, Cp, hslot, hist, nseg, &sb->dyn[0], &sb->err, nullptr, nullptr, 0};
+  SymArgs sa{rs, rb, f, nullptr, 0, Cp, hslot, hist, nseg, &sb->dyn[0], &sb->err, nullptr, nullptr, nullptr, 0};
   auto sym_bin = [&](int k0, int k1) {
     sa.list = list + key_off[k0];
     sa.count = key_off[k1] - key_off[k0];
@@ -239,7 +239,7 @@ static int spgemm_noalloc_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat 
     if (ar.over) return HS_ESCRATCH;
   }
   NumArgs na{rs,   rb,   f,    nullptr,     0,        Cp,   C->idx, C->val,  hslot,
-             hist, nseg, &sb->dyn[1], &sb->err, gcur, gend, nullptr, nullptr, 0};
+             hist, nseg, &sb->dyn[1], &sb->err, gcur, gend, nullptr, nullptr, nullptr, nullptr};
   const int k0s[5] = {KEY_TINY, KEY_WARP, KEY_MID, KEY_LARGE, KEY_HEAVY};
   const int k1s[5] = {KEY_TINY + 1, KEY_WARP + 1, KEY_MID + 1, KEY_LARGE + 1, NKEYS};
   for (int kind = 0; kind < 5; ++kind) {

@@ -42,7 +42,7 @@ template <class SR> using StructOf = Semiring<OR_AND, NoVal>;
 // --------------------------------------------------------------- tiny
 constexpr int NTINY_WPB = 8;
 template <class SR>
-__global__ void __launch_bounds__(NTINY_WPB * 32) k_num_tiny(NumArgs a) {
+__global__ void __launch_bounds__(NTINY_WPB * 32, 4) k_num_tiny(NumArgs a) {
   using T = typename SR::val_t;
   __shared__ int scol[NTINY_WPB][32];
   __shared__ T sval[NTINY_WPB][32];
@@ -113,7 +113,7 @@ template <typename T> struct WarpNumSmem {
 };
 
 template <class SR>
-__global__ void __launch_bounds__(NWARP_WPB * 32) k_num_warp(NumArgs a) {
+__global__ void __launch_bounds__(NWARP_WPB * 32, 4) k_num_warp(NumArgs a) {
   using T = typename SR::val_t;
   using L = WarpNumSmem<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -205,22 +205,25 @@ __global__ void __launch_bounds__(CAP > 2048 ? 1024 : 256, 1) k_num_cta(NumArgs 
 
 // ------------------------------------------------------------------ heavy
 // Rows whose output exceeds one shared table.  The row's columns are cut into
-// parts (consecutive 4096-column segments, using the symbolic pass's segment
-// counts) holding at most HEAVY_CAP outputs and spanning at most HV_WMAX
-// columns.  Each part is accumulated with the sparse accumulator of Figure 1
-// split in two: its occupancy as a bitmap over the part's columns, its values
-// as a compact array indexed by the column's rank among the part's set bits:
-//   pass 1  every product in the part ORs its column's bit;
-//   rank    a per-word prefix of set bits (warp scans) gives each word the
-//           number of output columns before it;
-//   pass 2  every product adds its value at rank(col) = prefix(word) +
-//           popcount(bits of the word below col);
-//   emit    the bitmap is walked in order (ascending columns, coalesced
-//           stores) and the value array is copied out as is.
-// No hashing and no sorting.  The B-row segment of each A entry for a part
-// continues where the previous part's ended: per-entry cursors (gcur, and
-// gend for the part's end) live in global scratch indexed like A's entries,
-// and each part's end is found by a galloping search from the cursor.
+// parts (consecutive 4096-column segments, planned from the symbolic pass's
+// segment counts) holding at most HEAVY_CAP outputs and spanning at most
+// HV_WMAX columns.  Each part is accumulated with the sparse accumulator of
+// Figure 1 split in two: its occupancy as a bitmap over the part's columns,
+// its values as a compact array indexed by the column's rank among the
+// part's set bits, rank(col) = wpre[word] + popcount(bits of the word below
+// col).  When the symbolic pass left the row's sorted column list, the part's
+// slice of it gives the bits and the word ranks directly (work in proportion
+// to the part's outputs), the products are visited once (values added at
+// their rank) and the slice is copied out as the part's columns.  Without a
+// list the kernel builds the bitmap from the products (pass 1), ranks the
+// words by prefix sums, adds the values (pass 2) and walks the bitmap to
+// write the columns.  No hashing and no sorting either way.
+//
+// The B-row segment of each A entry for a part continues where the previous
+// part's ended (a cursor per entry; in shared memory for rows of at most
+// HV_CH entries, else in global scratch indexed like A's entries).  The end
+// comes from the B segment index when the B row has one (its offset at the
+// part's last segment), else from a search from the cursor.
 constexpr int HV_NT = 512;          // threads per CTA; two CTAs share an SM
 constexpr int HV_WMAX = 1 << 18;    // columns per part: a 32 KB bitmap
 constexpr int HV_WORDS = HV_WMAX / 32;
@@ -231,17 +234,53 @@ template <typename T> constexpr int heavy_cap() {
 }
 
 template <typename T> struct HeavySmem {
-  unsigned bitmap[HV_WORDS];
+  unsigned bitmap[HV_WORDS];        // all zero at every part's start
   uint16_t wpre[HV_WORDS];          // set bits before word w within the part
   int wtot[HV_NT / 32 + 1];         // per-warp totals, then their exclusive scan
   int excl[HV_CH + 1];
   int64_t sbeg[HV_CH];
+  int64_t ebase[HV_CH];             // rows of at most HV_CH entries: per entry its B row's start,
+  int elen[HV_CH];                  //   length,
+  int et[HV_CH];                    //   segment-index row (-1 none),
+  int ecur[HV_CH];                  //   and cursor (offset of the next part's first entry)
   T aval[HV_CH];
   T vals[heavy_cap<T>()];
   int wtmp[33];
-  int row, part_end, part_cnt, total, nparts;
-  int pend[SEG_SMEM];  // the row's parts: end segment and output count
-  int pcnt[SEG_SMEM];
+  int row, part_end, part_cnt, total;
+  int pre[SEG_SMEM + 1];            // exclusive prefix of the row's segment counts
+};
+
+// Pass 2's visitor: prep finds the product's rank in the part (bitmap word
+// and word rank), commit adds the value there.  A product whose column is not
+// in the part's structure raises error 10 instead.
+template <class SR> struct HeavyAdd {
+  using T = typename SR::val_t;
+  static constexpr bool kTwoStage = true;
+  struct State {
+    int rank;  // -1: outside the structure; -2: failed guard (already recorded)
+  };
+  const unsigned *bitmap;
+  const uint16_t *wpre;
+  T *vals;
+  int lo;
+  unsigned span;
+  int pc;
+  int *err;
+  long long *dbg;
+  __device__ __forceinline__ State prep(int col) const {
+    const unsigned x = (unsigned)(col - lo);
+    if (!HS_G(dbg, x < span, 60, col)) return State{-2};
+    const int w = (int)(x >> 5);
+    const unsigned bits = bitmap[w];
+    const unsigned bit = 1u << (x & 31);
+    const int rank = wpre[w] + __popc(bits & (bit - 1u));
+    return State{(!(bits & bit) || rank >= pc) ? -1 : rank};
+  }
+  __device__ __forceinline__ void commit(const State &s, T v) const {
+    if (s.rank >= 0) SR::add_atomic(vals + s.rank, v);
+    else if (s.rank == -1) atomicExch(err, 10);
+  }
+  __device__ __forceinline__ void operator()(int col, T v, int) const { commit(prep(col), v); }
 };
 
 template <class SR>
@@ -256,7 +295,9 @@ __global__ void __launch_bounds__(HV_NT, 2) k_num_heavy(NumArgs a) {
   const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5, nw = HV_NT / 32;
   const int64_t n = a.B.n;
   const int nseg = (int)((n + SEG_W - 1) / SEG_W);
+  const int64_t bstride = (int64_t)nseg + 1;
   long long *dbg = a.A.dbg;
+  for (int w = tid; w < HV_WORDS; w += HV_NT) sm.bitmap[w] = 0u;
 
   while (true) {
     if (tid == 0) sm.row = atomicAdd(a.dyn, 1);
@@ -275,67 +316,100 @@ __global__ void __launch_bounds__(HV_NT, 2) k_num_heavy(NumArgs a) {
     const uint32_t *hist = a.hist + (int64_t)(h < 0 ? 0 : h) * a.nseg;
     const int64_t q0 = A.p[r], q1 = r_ok ? A.p[r + 1] : q0;
     const int nrounds = (int)((q1 - q0 + HV_CH - 1) / HV_CH);
-    // the row's column bitmap saved by the symbolic pass, if any
-    const int bs = (r_ok && a.gbm) ? a.bslot[r] : -1;
-    const unsigned *bm = bs >= 0 ? a.gbm + (int64_t)bs * a.bm_words : nullptr;
-    for (int64_t q = q0 + tid; q < q1; q += HV_NT) gcur[q] = 0;
+    const bool cached = nrounds == 1;
+    // the row's sorted column list left by the symbolic pass, if any
+    const int64_t lofs = (r_ok && a.loff && a.glist) ? a.loff[r] : -1;
+    const int32_t *L = lofs >= 0 ? a.glist + lofs : nullptr;
+    if (L && tid == 0) prefetch_l2(L, c * 4);  // the row's parts read it in order
+    if (cached) {
+      const int cnt = (int)(q1 - q0);
+      for (int e = tid; e < cnt; e += HV_NT) {
+        const int64_t q = q0 + e;
+        const int k = __ldg(A.j + q);
+        int64_t base = 0;
+        int len = 0, t = -1;
+        if (HS_G(dbg, k >= 0 && k < B.rows, 2, k)) {
+          base = __ldg(B.p + k);
+          len = (int)(__ldg(B.p + k + 1) - base);
+          if (a.bci_id) t = __ldg(a.bci_id + k);
+        }
+        sm.ebase[e] = base;
+        sm.elen[e] = len;
+        sm.et[e] = t;
+        sm.ecur[e] = 0;
+        if constexpr (SR::needs_a) sm.aval[e] = load_val<T>(A.v, q);
+      }
+    } else {
+      for (int64_t q = q0 + tid; q < q1; q += HV_NT) gcur[q] = 0;
+    }
     // the row's parts, chosen greedily from its segment counts: at most CAPH
     // outputs and HV_WMAX columns each
     const bool plan = h >= 0 && nseg <= SEG_SMEM;
     if (plan) {
-      for (int g = tid; g < nseg; g += HV_NT) sm.pend[g] = (int)hist[g];  // stage the counts
+      for (int g = tid; g < nseg; g += HV_NT) sm.pre[g] = (int)hist[g];
       __syncthreads();
-      if (tid == 0) {
-        int np = 0, e = 0;
-        while (e < nseg) {
-          const int b = e;
-          int sum = 0;
-          while (e < nseg && e - b < HV_WMAX / SEG_W && sum + sm.pend[e] <= CAPH) sum += sm.pend[e++];
-          if (e == b) {  // cannot happen: a segment holds at most SEG_W <= CAPH outputs
-            atomicExch(a.err, 5);
-            e = nseg;
-          }
-          sm.pcnt[np] = sum;
-          sm.pend[np] = e;  // np <= b: the counts still to read lie at or after e
-          ++np;
-        }
-        sm.nparts = np;
-      }
-      __syncthreads();
+      const int tot = group_excl_scan<CtaGroup>(sm.pre, nseg, sm.wtmp);
+      if (tid == 0) sm.pre[nseg] = tot;
     }
     int64_t done = 0;
     int seg = 0;
-    int part = 0;
     while (seg < nseg && h >= 0) {
-      if (plan) {
-        if (tid == 0) {
-          sm.part_end = sm.pend[part];
-          sm.part_cnt = sm.pcnt[part];
-        }
-        ++part;
-      } else if (tid == 0) {
+      if (tid == 0) {
+        const int emax = min(nseg, seg + HV_WMAX / SEG_W);
         int e = seg, sum = 0;
-        while (e < nseg && e - seg < HV_WMAX / SEG_W && sum + (int)hist[e] <= CAPH) sum += (int)hist[e++];
-        if (e == seg) {  // cannot happen: a segment holds at most SEG_W <= CAPH outputs
+        if (plan) {
+          // the last end in (seg, emax] whose part holds at most CAPH outputs
+          const int base = sm.pre[seg];
+          int lo_e = seg + 1, hi_e = emax;
+          while (lo_e < hi_e) {
+            const int mid = (lo_e + hi_e + 1) >> 1;
+            if (sm.pre[mid] - base <= CAPH) lo_e = mid;
+            else hi_e = mid - 1;
+          }
+          e = lo_e;
+          sum = sm.pre[e] - base;
+          if (sum > CAPH) e = seg;  // cannot happen: a segment holds at most SEG_W <= CAPH outputs
+        } else {
+          while (e < emax && sum + (int)hist[e] <= CAPH) sum += (int)hist[e++];
+        }
+        if (e == seg) {
           atomicExch(a.err, 5);
           e = nseg;
+          sum = 0;
         }
         sm.part_end = e;
         sm.part_cnt = sum;
       }
-      __syncthreads();  // also orders the cursor reset before the first part's reads
+      __syncthreads();  // also orders the row set-up before the first part's reads
       const int pe = sm.part_end, pc = sm.part_cnt;
       if (pc > 0) {
         const int lo = seg * SEG_W;
         const int hi = (int)min((int64_t)pe * SEG_W, n);
         const int words = (hi - lo + 31) >> 5;
-        // ---- occupancy: the saved bitmap of the symbolic pass, or pass 1
-        if (bm) {
-          const unsigned *src = bm + (lo >> 5);
-          for (int w = tid; w < words; w += HV_NT) sm.bitmap[w] = __ldg(src + w);
-        } else {
-          for (int w = tid; w < words; w += HV_NT) sm.bitmap[w] = 0u;
+        const int32_t *Lp = (L && HS_G(dbg, done + pc <= c, 64, done + pc)) ? L + done : nullptr;
+        // ---- occupancy and word ranks from the list: one bit per column and
+        // one rank store per nonempty word
+        if (Lp) {
+          constexpr int U = 4;  // loads in flight per thread
+          for (int i0 = tid; i0 < pc; i0 += U * HV_NT) {
+            int x[U], xp[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              const int i = i0 + u * HV_NT;
+              x[u] = i < pc ? __ldg(Lp + i) - lo : -1;
+              xp[u] = (i < pc && i > 0) ? __ldg(Lp + i - 1) - lo : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              const int i = i0 + u * HV_NT;
+              if (i >= pc || !HS_G(dbg, x[u] >= 0 && x[u] < hi - lo, 63, x[u])) continue;
+              const int w = x[u] >> 5;
+              atomicOr(sm.bitmap + w, 1u << (x[u] & 31));
+              if (i == 0 || (xp[u] >> 5) != w) sm.wpre[w] = (uint16_t)i;
+            }
+          }
         }
+        // ---- B segments of the part (and, without a list, pass 1)
         int total = 0;
         for (int rd = 0; rd < nrounds; ++rd) {
           const int64_t rq0 = q0 + (int64_t)rd * HV_CH;
@@ -344,28 +418,38 @@ __global__ void __launch_bounds__(HV_NT, 2) k_num_heavy(NumArgs a) {
           for (int e = tid; e < cnt; e += HV_NT) {
             int64_t s = 0;
             int len = 0;
-            const int64_t q = rq0 + e;
-            const int k = __ldg(A.j + q);
-            if (HS_G(dbg, k >= 0 && k < B.rows, 2, k)) {
-              const int64_t base = __ldg(B.p + k), end = __ldg(B.p + k + 1);
-              s = base + gcur[q];
-              const int64_t se = interp_lower_bound(B.j, s, end, hi);
-              len = (int)(se - s);
-              gend[q] = (int32_t)(se - base);
-              if (nrounds == 1) {
-                gcur[q] = (int32_t)(se - base);
-                if constexpr (SR::needs_a) sm.aval[e] = load_val<T>(A.v, q);
+            if (cached) {
+              const int64_t base = sm.ebase[e];
+              const int cur = sm.ecur[e], t = sm.et[e], rl = sm.elen[e];
+              int eo = t >= 0 ? __ldg(a.bci + (int64_t)t * bstride + pe)
+                              : (int)(interp_lower_bound(B.j, base + cur, base + rl, hi) - base);
+              if (!HS_G(dbg, eo >= cur && eo <= rl, 65, eo)) eo = cur;
+              s = base + cur;
+              len = eo - cur;
+              sm.ecur[e] = eo;
+            } else {
+              const int64_t q = rq0 + e;
+              const int k = __ldg(A.j + q);
+              if (HS_G(dbg, k >= 0 && k < B.rows, 2, k)) {
+                const int64_t base = __ldg(B.p + k), end = __ldg(B.p + k + 1);
+                const int t = a.bci_id ? __ldg(a.bci_id + k) : -1;
+                s = base + gcur[q];
+                int64_t se = t >= 0 ? base + __ldg(a.bci + (int64_t)t * bstride + pe)
+                                    : interp_lower_bound(B.j, s, end, hi);
+                if (!HS_G(dbg, se >= s && se <= end, 65, se)) se = s;
+                len = (int)(se - s);
+                gend[q] = (int32_t)(se - base);
               }
             }
             sm.excl[e] = len;
             sm.sbeg[e] = s;
           }
-          if (bm && nrounds > 1) continue;  // only the part ends are needed (pass 2 restages)
+          if (!cached && Lp) continue;  // only the part ends are needed (pass 2 restages)
           __syncthreads();
           total = group_excl_scan<CtaGroup>(sm.excl, cnt, sm.wtmp);
           if (tid == 0) sm.excl[cnt] = total;
           __syncthreads();
-          if (!bm) {
+          if (!Lp) {
             auto set_bit = [&](int col, NoVal, int) {
               const int x = col - lo;
               if (HS_G(dbg, x >= 0 && x < hi - lo, 60, col)) atomicOr(sm.bitmap + (x >> 5), 1u << (x & 31));
@@ -375,8 +459,8 @@ __global__ void __launch_bounds__(HV_NT, 2) k_num_heavy(NumArgs a) {
           }
         }
         __syncthreads();
-        // ---- rank: prefix of set bits per word, in runs of 32 words per warp
-        {
+        if (!Lp) {
+          // ---- rank: prefix of set bits per word, in runs of 32 words per warp
           const int wpw = ((words + nw - 1) / nw + 31) & ~31;
           const int w0 = warp * wpw, w1 = min(words, w0 + wpw);
           int carry = 0;
@@ -398,16 +482,19 @@ __global__ void __launch_bounds__(HV_NT, 2) k_num_heavy(NumArgs a) {
           __syncthreads();
           const int add = sm.wtot[warp];
           for (int w = w0 + lane; w < w1; w += 32) sm.wpre[w] = (uint16_t)(sm.wpre[w] + add);
-          if constexpr (SR::has_val)
-            for (int i = tid; i < pc; i += HV_NT) sm.vals[i] = SR::identity();
+        } else if (tid == 0) {
+          sm.total = pc;
         }
+        if constexpr (SR::has_val)
+          for (int i = tid; i < pc; i += HV_NT) sm.vals[i] = SR::identity();
         __syncthreads();
         const bool consistent = sm.total == pc;
         if (!consistent && tid == 0) atomicExch(a.err, 9);
         // ---- pass 2: values at their rank
         if constexpr (SR::has_val) {
-          for (int rd = 0; rd < nrounds; ++rd) {
-            if (nrounds > 1) {
+          HeavyAdd<SR> add_val{sm.bitmap, sm.wpre, sm.vals, lo, (unsigned)(hi - lo), pc, a.err, dbg};
+          if (!cached) {
+            for (int rd = 0; rd < nrounds; ++rd) {
               const int64_t rq0 = q0 + (int64_t)rd * HV_CH;
               const int cnt = (int)min((int64_t)HV_CH, q1 - rq0);
               __syncthreads();
@@ -430,47 +517,51 @@ __global__ void __launch_bounds__(HV_NT, 2) k_num_heavy(NumArgs a) {
               total = group_excl_scan<CtaGroup>(sm.excl, cnt, sm.wtmp);
               if (tid == 0) sm.excl[cnt] = total;
               __syncthreads();
-              auto add_val = [&](int col, T v, int) {
-                const int x = col - lo;
-                if (!HS_G(dbg, x >= 0 && x < hi - lo, 60, col)) return;
-                const int w = x >> 5;
-                const int rank = sm.wpre[w] + __popc(sm.bitmap[w] & ((1u << (x & 31)) - 1u));
-                if (HS_G(dbg, rank < pc, 61, rank)) SR::add_atomic(sm.vals + rank, v);
-              };
-              cta_expand_staged<SR>(B, sm.sbeg, sm.excl, sm.aval, cnt, total, add_val);
-            } else {
-              auto add_val = [&](int col, T v, int) {
-                const int x = col - lo;
-                if (!HS_G(dbg, x >= 0 && x < hi - lo, 60, col)) return;
-                const int w = x >> 5;
-                const int rank = sm.wpre[w] + __popc(sm.bitmap[w] & ((1u << (x & 31)) - 1u));
-                if (HS_G(dbg, rank < pc, 61, rank)) SR::add_atomic(sm.vals + rank, v);
-              };
-              const int cnt = (int)(q1 - q0);
-              cta_expand_staged<SR>(B, sm.sbeg, sm.excl, sm.aval, cnt, total, add_val);
+              cta_expand_staged<SR, 4>(B, sm.sbeg, sm.excl, sm.aval, cnt, total, add_val);
             }
+          } else {
+            cta_expand_staged<SR, 4>(B, sm.sbeg, sm.excl, sm.aval, (int)(q1 - q0), total, add_val);
           }
           __syncthreads();
-        } else if (nrounds > 1) {
+        } else if (!cached) {
           // structure only: still advance the cursors past this part
           for (int64_t q = q0 + tid; q < q1; q += HV_NT) gcur[q] = gend[q];
         }
-        // ---- emit: columns in bitmap order, values in rank order
+        // ---- emit (columns ascending, values in rank order), then clear the bitmap
         const int64_t out = cb + done;
-        if (consistent && HS_G(dbg, done + pc <= c, 62, done + pc)) {
+        const bool fits = consistent && HS_G(dbg, done + pc <= c, 62, done + pc);
+        if (Lp) {
+          constexpr int U = 4;
+          for (int i0 = tid; i0 < pc; i0 += U * HV_NT) {
+            int col[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) col[u] = i0 + u * HV_NT < pc ? __ldg(Lp + i0 + u * HV_NT) : lo - 1;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              const int i = i0 + u * HV_NT;
+              if (i >= pc) continue;
+              if (fits) __stcs(a.Cj + out + i, col[u]);
+              const int x = col[u] - lo;
+              if (x >= 0 && x < hi - lo) sm.bitmap[x >> 5] = 0u;
+            }
+          }
+        } else {
           for (int w = tid; w < words; w += HV_NT) {
             unsigned bits = sm.bitmap[w];
             int pos = sm.wpre[w];
-            while (bits) {
-              const int b = __ffs(bits) - 1;
-              a.Cj[out + pos] = lo + (w << 5) + b;
-              ++pos;
-              bits &= bits - 1;
-            }
+            if (fits)
+              while (bits) {
+                const int b = __ffs(bits) - 1;
+                a.Cj[out + pos] = lo + (w << 5) + b;
+                ++pos;
+                bits &= bits - 1;
+              }
+            sm.bitmap[w] = 0u;
           }
-          if constexpr (SR::has_val)
-            for (int i = tid; i < pc; i += HV_NT) Cv[out + i] = sm.vals[i];
         }
+        if constexpr (SR::has_val)
+          if (fits)
+            for (int i = tid; i < pc; i += HV_NT) __stcs(Cv + out + i, sm.vals[i]);
         done += pc;
       }
       seg = pe;

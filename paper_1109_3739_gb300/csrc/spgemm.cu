@@ -205,6 +205,9 @@ struct SmallBlock {  // device counters, read back in one copy
   int valflag;
   int pad;
   unsigned long long stats[4];
+  unsigned long long lpool;  // heavy rows' column lists: pool entries handed out
+  int bci_cnt;               // B segment index rows handed out
+  int pad2;
   long long nnz;
   long long dbg[2];  // guarded builds: first failed check (code, index)
 };
@@ -326,7 +329,7 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
       launch_validate(A->ptr, A->idx, nslots, A->n, &sb->valflag, st);
       launch_validate(B->ptr, B->idx, B->m, B->n, &sb->valflag, st);
     }
-    launch_flops(rs, rb, f, sb->key_cnt, sb->stats, st);
+    launch_flops(rs, rb, f, sb->key_cnt, sb->stats, cap_large_of(out_dt), st);
     launch_key_offsets(sb->key_cnt, sb->key_off, sb->key_cur, st);
     launch_scatter_sym(rs, f, sb->key_cur, list, hslot, &sb->nhist, cap_large_of(out_dt), st);
   }
@@ -349,32 +352,38 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
     CK(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)nhist * nseg, st));
   }
 
-  // heavy rows keep their symbolic column bitmaps for the numeric pass when
-  // they fit a quarter of the free device memory (at most 32 GiB)
-  unsigned *gbm = nullptr;
-  int32_t *bslot = nullptr;
-  const int64_t bm_words = (n + 31) / 32;
+  // the symbolic heavy rows write their sorted column lists for the numeric
+  // pass into a pool of sum(min(f, n)) entries, as much of it as fits a
+  // quarter of the free device memory (at most 32 GiB); rows that find no
+  // room are left to the numeric pass's own bitmap build
+  int32_t *glist = nullptr;
+  int64_t *loff = nullptr;
+  int64_t lcap = 0;
   {
     const int64_t nsh = key_off[NKEYS] - key_off[KEY_HEAVY];
     size_t free_b = 0, total_b = 0;
-    if (nsh > 0 && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
-      const size_t bytes = (size_t)nsh * (size_t)bm_words * 4;
+    if (nsh > 0 && hb->stats[3] > 0 && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
       const size_t budget = free_b / 4 < ((size_t)32 << 30) ? free_b / 4 : ((size_t)32 << 30);
-      if (bytes <= budget) {
-        gbm = (unsigned *)mem.raw(bytes);
-        bslot = gbm ? (int32_t *)mem.raw(sizeof(int32_t) * (size_t)nslots) : nullptr;
-        if (gbm) mem.scratch.push_back({gbm, bytes});
-        if (bslot) mem.scratch.push_back({bslot, sizeof(int32_t) * (size_t)nslots});
-        mem.failed = false;  // an optional buffer: without it the numeric pass rebuilds the bitmaps
-        if (!bslot) gbm = nullptr;
-        else CK(cudaMemsetAsync(bslot, 0xff, sizeof(int32_t) * (size_t)nslots, st));
+      const size_t want = (size_t)hb->stats[3] * 4;
+      const size_t bytes = want < budget ? want : budget;
+      if (bytes >= 4) {
+        glist = (int32_t *)mem.raw(bytes);
+        loff = glist ? (int64_t *)mem.raw(sizeof(int64_t) * (size_t)nslots) : nullptr;
+        if (glist) mem.scratch.push_back({glist, bytes});
+        if (loff) mem.scratch.push_back({loff, sizeof(int64_t) * (size_t)nslots});
+        mem.failed = false;  // optional buffers
+        if (!loff) glist = nullptr;
+        else {
+          lcap = (int64_t)(bytes / 4);
+          CK(cudaMemsetAsync(loff, 0xff, sizeof(int64_t) * (size_t)nslots, st));
+        }
       }
     }
     cudaGetLastError();
   }
 
   // ---- symbolic
-  SymArgs sa{rs, rb, f, nullptr, 0, Cp, hslot, hist, nseg, &sb->dyn[0], &sb->err, gbm, bslot, bm_words};
+  SymArgs sa{rs, rb, f, nullptr, 0, Cp, hslot, hist, nseg, &sb->dyn[0], &sb->err, glist, loff, &sb->lpool, lcap};
   auto sym_bin = [&](int k0, int k1) {
     sa.list = list + key_off[k0];
     sa.count = key_off[k1] - key_off[k0];
@@ -440,8 +449,38 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
     gend = mem.tmp<int32_t>((size_t)A->nnz);
     if (!gcur || !gend) return HS_ENOMEM;
   }
+  // heavy bin: the B segment index (rows longer than min_len; the table kept
+  // within an eighth of the free memory, at most 4 GiB)
+  int32_t *bci_id = nullptr, *bci = nullptr;
+  if (key_off[NKEYS] > key_off[KEY_HEAVY] && B->nnz > 0) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+      const size_t budget = free_b / 8 < ((size_t)4 << 30) ? free_b / 8 : ((size_t)4 << 30);
+      const int64_t stride = (int64_t)nseg + 1;
+      const int64_t row_bytes = stride * 4;
+      int64_t min_len = 32;
+      const int64_t need = (B->nnz * row_bytes + (int64_t)budget - 1) / (int64_t)(budget ? budget : 1);
+      if (need > min_len) min_len = need;
+      int64_t max_rows = B->nnz / (min_len + 1);
+      if (max_rows > (int64_t)(budget / row_bytes)) max_rows = (int64_t)(budget / row_bytes);
+      if (max_rows > 0 && min_len < 0x7fffffff) {
+        bci_id = (int32_t *)mem.raw(sizeof(int32_t) * (size_t)B->m);
+        bci = bci_id ? (int32_t *)mem.raw((size_t)max_rows * (size_t)row_bytes) : nullptr;
+        if (bci_id) mem.scratch.push_back({bci_id, sizeof(int32_t) * (size_t)B->m});
+        if (bci) mem.scratch.push_back({bci, (size_t)max_rows * (size_t)row_bytes});
+        mem.failed = false;  // optional: without it the part ends are searched
+        if (!bci) bci_id = nullptr;
+        else {
+          PhaseTimer t("bci", st);
+          launch_build_bci(rb, nseg, (int)min_len, max_rows, bci_id, bci, &sb->bci_cnt, st);
+          if (int e = phase_check("bci", st, sb->dbg)) return e;
+        }
+      }
+    }
+    cudaGetLastError();
+  }
   NumArgs na{rs, rb,   f,    nullptr, 0,    Cp,    C->idx, C->val, hslot,
-             hist, nseg, &sb->dyn[1], &sb->err, gcur, gend, gbm, bslot, bm_words};
+             hist, nseg, &sb->dyn[1], &sb->err, gcur, gend, glist, loff, bci_id, bci};
   const char *names[5] = {"numeric_tiny", "numeric_warp", "numeric_mid", "numeric_large", "numeric_heavy"};
   const int k0s[5] = {KEY_TINY, KEY_WARP, KEY_MID, KEY_LARGE, KEY_HEAVY};
   const int k1s[5] = {KEY_TINY + 1, KEY_WARP + 1, KEY_MID + 1, KEY_LARGE + 1, NKEYS};

@@ -7,10 +7,15 @@
 //                      with __match_any_sync;
 //   warp  (f <= 512)   one warp, private shared-memory hash set;
 //   mid   (f <= 4096)  one CTA, shared hash set of 2f..8192 slots;
-//   large (f <= 16384) one CTA, shared hash set of up to 32768 slots, and
-//                      per-column-segment counts for the numeric pass;
-//   heavy (f > 16384)  one CTA, a bitmap over 2^20 columns (occupancy SPA in
-//                      shared memory), rows handed out largest first.
+//   large (f <= min(16384, cap_large))
+//                      one CTA, shared hash set of up to 32768 slots;
+//   heavy (larger f)   one CTA, a bitmap over 2^20 columns (occupancy SPA in
+//                      shared memory), rows handed out largest first.  The
+//                      bitmap is read out in column order, so the kernel also
+//                      writes the row's sorted column list for the numeric
+//                      pass, which then only has to place values.
+// Rows with more than cap_large products also get per-column-segment counts
+// (4096-column segments) from which the numeric pass plans its column parts.
 // Counts go to cnt[row + 1] so an inclusive scan turns them into row offsets.
 #include "common.cuh"
 #include "internal.h"
@@ -29,7 +34,7 @@ __device__ __forceinline__ int64_t out_row(const RowSet &A, int r) { return A.id
 
 // --------------------------------------------------------------- tiny
 constexpr int TINY_WPB = 8;
-__global__ void __launch_bounds__(TINY_WPB * 32) k_sym_tiny(SymArgs a) {
+__global__ void __launch_bounds__(TINY_WPB * 32, 4) k_sym_tiny(SymArgs a) {
   __shared__ int scol[TINY_WPB][32];
   const int w = threadIdx.x >> 5, lane = lane_id();
   const DevCsr A = dev_a(a.A), B = dev_b(a.B);
@@ -67,7 +72,7 @@ __global__ void __launch_bounds__(TINY_WPB * 32) k_sym_tiny(SymArgs a) {
 
 // --------------------------------------------------------------- warp
 constexpr int WARP_WPB = 8, WARP_SLOTS = 1024;
-__global__ void __launch_bounds__(WARP_WPB * 32) k_sym_warp(SymArgs a) {
+__global__ void __launch_bounds__(WARP_WPB * 32, 4) k_sym_warp(SymArgs a) {
   __shared__ int tables[WARP_WPB][WARP_SLOTS];
   const int w = threadIdx.x >> 5, lane = lane_id();
   int *keys = tables[w];
@@ -146,12 +151,49 @@ __global__ void __launch_bounds__(HIST ? 512 : 256) k_sym_cta(SymArgs a) {
 }
 
 // --------------------------------------------------------------- heavy
+// Per row and per chunk of 2^20 columns: the products set their bits, and a
+// bit that was clear counts one new column of its 4096-column segment.  The
+// segment counts give the chunk's histogram and, scanned, each segment's
+// place in the row's sorted column list.  Each warp then walks whole
+// segments, every lane four consecutive words: the lanes' bit counts are
+// scanned across the warp, the columns go to a per-warp staging buffer in
+// ascending order and leave it in coalesced stores.
+constexpr int SH_SEGS = BITMAP_COLS / SEG_W;  // segments per chunk (256)
+constexpr int SH_BUF = 256;                   // per-warp list staging entries
+static_assert(SEG_W == 4096, "a segment is 128 words: four per lane");
+
+// Product visitor: prep sets the column's bit (the old word comes back),
+// commit counts the column for its segment if the bit was clear.
+struct SymHeavyBit {
+  static constexpr bool kTwoStage = true;
+  struct State {
+    unsigned old, bit;
+    int seg;
+  };
+  unsigned *bitmap;
+  int *scnt;
+  int lo;
+  unsigned span;
+  long long *dbg;
+  __device__ __forceinline__ State prep(int col) const {
+    const unsigned x = (unsigned)(col - lo);
+    if (!HS_G(dbg, x < span, 33, col)) return State{1u, 1u, 0};
+    const unsigned bit = 1u << (x & 31);
+    return State{atomicOr(bitmap + (x >> 5), bit), bit, (int)(x / SEG_W)};
+  }
+  __device__ __forceinline__ void commit(const State &s, NoVal) const {
+    if (!(s.old & s.bit)) atomicAdd(scnt + s.seg, 1);
+  }
+  __device__ __forceinline__ void operator()(int col, NoVal v, int) const { commit(prep(col), v); }
+};
+
 struct SymHeavySmem {
   CtaExpandSmem<NoVal, CH> ex;
   int wtmp[33];
-  int total;
   int row;
-  unsigned segcnt[SEG_SMEM];  // per-segment counts of the current row (nseg <= SEG_SMEM)
+  long long loff;        // the row's list in the pool, or -1
+  int scnt[SH_SEGS + 1];  // new columns per segment of the chunk, then their exclusive scan
+  int wbuf[32][SH_BUF];
   unsigned bitmap[BITMAP_COLS / 32];
 };
 
@@ -162,10 +204,20 @@ __global__ void __launch_bounds__(1024, 1) k_sym_heavy(SymArgs a) {
   const int64_t n = a.B.n;
   const int nchunk = (int)((n + BITMAP_COLS - 1) / BITMAP_COLS);
   const int lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int *buf = sm.wbuf[warp];
   while (true) {
     if (threadIdx.x == 0) {
       sm.row = atomicAdd(a.dyn, 1);
-      sm.total = 0;
+      sm.loff = -1;
+      if (sm.row < a.count && a.glist) {
+        // room for the row's list: min(f, n) entries bound its output
+        const int r = a.list[sm.row];
+        if (r >= 0 && r < a.A.nslots) {
+          const long long need = (long long)min(a.f[r], n);
+          const unsigned long long at = atomicAdd(a.lpool, (unsigned long long)need);
+          if ((long long)at + need <= a.lcap) sm.loff = (long long)at;
+        }
+      }
     }
     __syncthreads();
     const int idx = sm.row;
@@ -176,49 +228,70 @@ __global__ void __launch_bounds__(1024, 1) k_sym_heavy(SymArgs a) {
     const int r = r_ok ? r0 : 0;
     const int h = r_ok ? a.hslot[r] : -1;
     uint32_t *hist = h >= 0 ? a.hist + (int64_t)h * a.nseg : nullptr;
-    const bool seg_smem = a.nseg <= SEG_SMEM;
-    if (hist && seg_smem)
-      for (int g = threadIdx.x; g < a.nseg; g += blockDim.x) sm.segcnt[g] = 0u;
-    int cnt = 0;
+    int32_t *lst = (r_ok && sm.loff >= 0) ? a.glist + sm.loff : nullptr;
+    const int64_t lmax = r_ok ? min(a.f[r], n) : 0;  // the list's room
+    int64_t written = 0;  // columns of the earlier chunks
     for (int ch = 0; ch < (r_ok ? nchunk : 0); ++ch) {
       const int lo = ch * BITMAP_COLS;
       const int hi = (int)min((int64_t)lo + BITMAP_COLS, n);
       const int words = (hi - lo + 31) >> 5;
+      const int nsc = (hi - lo + SEG_W - 1) / SEG_W;
       for (int wd = threadIdx.x; wd < words; wd += blockDim.x) sm.bitmap[wd] = 0u;
+      for (int g = threadIdx.x; g <= SH_SEGS; g += blockDim.x) sm.scnt[g] = 0;
       __syncthreads();
-      cta_products<StructSR, CH>(A, B, A.p[r], A.p[r + 1], nchunk > 1, lo, hi, sm.ex, sm.wtmp,
-                                 [&](int col, NoVal, int) {
-                                   const int x = col - lo;
-                                   if (HS_G(a.A.dbg, x >= 0 && x < hi - lo, 33, col))
-                                     atomicOr(sm.bitmap + (x >> 5), 1u << (x & 31));
-                                 });
-      // count: each warp takes 32 consecutive words (1024 columns, inside one segment);
-      // the words are also saved for the numeric pass when a bitmap store is given
-      unsigned *save = (a.gbm && r_ok) ? a.gbm + (int64_t)idx * a.bm_words + (lo >> 5) : nullptr;
-      for (int wb = warp * 32; wb < words; wb += nw * 32) {
-        const int wd = wb + lane;
-        const unsigned bits = wd < words ? sm.bitmap[wd] : 0u;
-        if (save && wd < words) save[wd] = bits;
-        int c = __popc(bits);
-        c = warp_sum(c);
-        if (lane == 0 && c) {
-          cnt += c;
-          const int g = (lo + wb * 32) / SEG_W;
-          if (hist && HS_G(a.A.dbg, g < a.nseg, 32, wb)) {
-            if (seg_smem) atomicAdd(sm.segcnt + g, (unsigned)c);
-            else atomicAdd(hist + g, (uint32_t)c);
+      cta_products<StructSR, CH, 4>(A, B, A.p[r], A.p[r + 1], nchunk > 1, lo, hi, sm.ex, sm.wtmp,
+                                    SymHeavyBit{sm.bitmap, sm.scnt, lo, (unsigned)(hi - lo), a.A.dbg});
+      __syncthreads();
+      if (hist)
+        for (int g = threadIdx.x; g < nsc; g += blockDim.x)
+          if (HS_G(a.A.dbg, lo / SEG_W + g < a.nseg, 32, g)) hist[lo / SEG_W + g] = (uint32_t)sm.scnt[g];
+      const int ctotal = group_excl_scan<CtaGroup>(sm.scnt, nsc, sm.wtmp);
+      // list: warp w takes segments w, w + 32, ...
+      if (lst) {
+        for (int g = warp; g < nsc; g += nw) {
+          const int wb = g * (SEG_W / 32) + 4 * lane;
+          unsigned b[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) b[u] = wb + u < words ? sm.bitmap[wb + u] : 0u;
+          const int pcl = __popc(b[0]) + __popc(b[1]) + __popc(b[2]) + __popc(b[3]);
+          const int incl = warp_incl_scan(pcl);
+          const int tot = __shfl_sync(FULL, incl, 31);
+          const int64_t at0 = written + sm.scnt[g];
+          if (!HS_G(a.A.dbg, at0 + tot <= lmax, 34, at0 + tot)) continue;
+          if (tot <= SH_BUF) {
+            int p = incl - pcl;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              unsigned bits = b[u];
+              const int cbase = lo + ((wb + u) << 5);
+              while (bits) {
+                buf[p++] = cbase + __ffs(bits) - 1;
+                bits &= bits - 1;
+              }
+            }
+            __syncwarp();
+            for (int i = lane; i < tot; i += 32) lst[at0 + i] = buf[i];
+            __syncwarp();
+          } else {  // a dense segment: each lane's columns are one long run
+            int64_t at = at0 + incl - pcl;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              unsigned bits = b[u];
+              const int cbase = lo + ((wb + u) << 5);
+              while (bits) {
+                lst[at++] = cbase + __ffs(bits) - 1;
+                bits &= bits - 1;
+              }
+            }
           }
         }
       }
+      written += ctotal;
       __syncthreads();
     }
-    if (lane == 0 && cnt) atomicAdd(&sm.total, cnt);
-    __syncthreads();
-    if (hist && seg_smem)
-      for (int g = threadIdx.x; g < a.nseg; g += blockDim.x) hist[g] = sm.segcnt[g];
     if (threadIdx.x == 0 && r_ok) {
-      put_count(a, out_row(a.A, r), sm.total);
-      if (a.gbm) a.bslot[r] = idx;
+      put_count(a, out_row(a.A, r), written);
+      if (a.loff) a.loff[r] = lst ? sm.loff : -1;
     }
     __syncthreads();
   }
