@@ -373,16 +373,21 @@ def main():
     # offsets once
     cnt = np.diff(c_rowptr)
     deg = np.diff(A.rowptr)
-    cap_large = 8192
+    cap_large = 8192  # f32 values
+    big = (f > 512) & (cnt > 0)
     in_bin = {
-        "numeric_heavy": (f > 512) & (cnt > cap_large),
-        "numeric_large": (f > 512) & (cnt > 2048) & (cnt <= cap_large),
-        "numeric_mid": (f > 512) & (cnt > 0) & (cnt <= 2048),
-        "numeric_warp": (f > 32) & (f <= 512),
+        "numeric_heavy": big & (cnt > cap_large),
+        "numeric_large": big & (cnt > cap_large // 2) & (cnt <= cap_large),
+        "numeric_large_s": big & (cnt > 2048) & (cnt <= cap_large // 2),
+        "numeric_mid": big & (cnt > 1024) & (cnt <= 2048),
+        "numeric_mid_s": big & (cnt <= 1024),
+        "numeric_warp": (f > 128) & (f <= 512),
+        "numeric_warp_s": (f > 32) & (f <= 128),
         "numeric_tiny": (f > 0) & (f <= 32),
-        "symbolic_heavy": f > 16384,
-        "symbolic_large": (f > 4096) & (f <= 16384),
-        "symbolic_mid": (f > 512) & (f <= 4096),
+        "symbolic_heavy": f > cap_large,
+        "symbolic_large": (f > 4096) & (f <= cap_large),
+        "symbolic_mid": (f > 1024) & (f <= 4096),
+        "symbolic_mid_s": (f > 512) & (f <= 1024),
         "symbolic_warp": (f > 32) & (f <= 512),
         "symbolic_tiny": (f > 0) & (f <= 32),
     }[dom]

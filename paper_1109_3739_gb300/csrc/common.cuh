@@ -600,7 +600,8 @@ template <class G, typename T, bool HAS_VAL>
 __device__ void group_sort_emit(const int *keys, const T *vals, int slots, int c, int *ck, T *cv,
                                 void *work, int *wtmp, EmitScratch *es, int32_t *out_j, T *out_v,
                                 int *err, int cap, long long *dbg) {
-  const int gs = G::size(), r = G::rank();
+  constexpr int EU = 4;  // entries per thread per step: their shared-memory chains overlap
+  const int gs = G::size(), r = G::rank(), lane = lane_id();
   if (!HS_G(dbg, c >= 0 && c <= cap, 20, c)) {
     if (r == 0) atomicExch(err, 8);
     return;
@@ -611,31 +612,40 @@ __device__ void group_sort_emit(const int *keys, const T *vals, int slots, int c
     es->count = 0;
   }
   G::sync();
-  // (1) compaction
-  int lmin = 0x7fffffff, lmax = -1;
-  for (int base = 0; base < slots; base += gs) {
-    const int s = base + r;
-    const int k = s < slots ? keys[s] : EMPTY;
-    const bool occ = k != EMPTY;
-    const unsigned m = __ballot_sync(FULL, occ);
-    int wbase = 0;
-    if (lane_id() == 0 && m) wbase = atomicAdd(&es->count, __popc(m));
-    wbase = __shfl_sync(FULL, wbase, 0);
-    if (occ) {
-      const int at = wbase + __popc(m & ((1u << lane_id()) - 1));
-      if (at < c) {
-        ck[at] = k;
-        if constexpr (HAS_VAL) cv[at] = vals[s];
+  // (1) compaction: each warp counts its run of slots, reserves room once,
+  // then copies the run's entries in order
+  {
+    const int nw = G::nwarps(), w = G::warp();
+    const int per = ((slots + nw - 1) / nw + 31) & ~31;
+    const int s0 = min(slots, w * per), s1 = min(slots, s0 + per);
+    int n = 0;
+    for (int sb = s0; sb < s1; sb += 32) n += __popc(__ballot_sync(FULL, sb + lane < s1 && keys[sb + lane] != EMPTY));
+    int base = 0;
+    if (lane == 0 && n) base = atomicAdd(&es->count, n);
+    base = __shfl_sync(FULL, base, 0);
+    int lmin = 0x7fffffff, lmax = -1;
+    for (int sb = s0; sb < s1; sb += 32) {
+      const int sl = sb + lane;
+      const int k = sl < s1 ? keys[sl] : EMPTY;
+      const bool occ = k != EMPTY;
+      const unsigned m = __ballot_sync(FULL, occ);
+      if (occ) {
+        const int at = base + __popc(m & ((1u << lane) - 1));
+        if (at < c) {
+          ck[at] = k;
+          if constexpr (HAS_VAL) cv[at] = vals[sl];
+        }
+        lmin = min(lmin, k);
+        lmax = max(lmax, k);
       }
-      lmin = min(lmin, k);
-      lmax = max(lmax, k);
+      base += __popc(m);
     }
-  }
-  lmin = warp_min(lmin);
-  lmax = warp_max(lmax);
-  if (lane_id() == 0) {
-    atomicMin(&es->kmin, lmin);
-    atomicMax(&es->kmax, lmax);
+    lmin = warp_min(lmin);
+    lmax = warp_max(lmax);
+    if (lane == 0) {
+      atomicMin(&es->kmin, lmin);
+      atomicMax(&es->kmax, lmax);
+    }
   }
   G::sync();
   if (es->count != c) {  // structure disagrees with the symbolic count
@@ -656,30 +666,58 @@ __device__ void group_sort_emit(const int *keys, const T *vals, int slots, int c
   auto bucket = [&](int key) { return (int)(((uint64_t)(unsigned)(key - kmin) * scale) >> 32); };
   for (int b = r; b < nb; b += gs) bcnt[b] = 0;
   G::sync();
-  for (int e = r; e < c; e += gs)
-    if (HS_G(dbg, bucket(ck[e]) >= 0 && bucket(ck[e]) < nb, 21, ck[e])) atomicAdd(bcnt + bucket(ck[e]), 1);
+  for (int e = r; e < c; e += gs) {
+    const int b = bucket(ck[e]);
+    if (HS_G(dbg, b >= 0 && b < nb, 21, b)) atomicAdd(bcnt + b, 1);
+  }
   G::sync();
   group_excl_scan<G>(bcnt, nb, wtmp);
   // scatter entry ids into their buckets (arbitrary order inside a bucket);
   // bcnt[b] advances to the bucket's end, so the start is bcnt[b] - size
-  for (int e = r; e < c; e += gs) {
-    const int b = bucket(ck[e]);
-    if (!HS_G(dbg, b >= 0 && b < nb, 22, b)) continue;
-    const int at = atomicAdd(bcnt + b, 1);
-    if (HS_G(dbg, at >= 0 && at < c, 23, at)) order[at] = e;
+  for (int e0 = r; e0 < c; e0 += EU * gs) {
+    int b[EU], at[EU];
+#pragma unroll
+    for (int u = 0; u < EU; ++u) {
+      const int e = e0 + u * gs;
+      b[u] = e < c ? bucket(ck[e]) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < EU; ++u) {
+      at[u] = -1;
+      if (b[u] >= 0 && HS_G(dbg, b[u] < nb, 22, b[u])) at[u] = atomicAdd(bcnt + b[u], 1);
+    }
+#pragma unroll
+    for (int u = 0; u < EU; ++u)
+      if (at[u] >= 0 && HS_G(dbg, at[u] < c, 23, at[u])) order[at[u]] = e0 + u * gs;
   }
   G::sync();
   // (3) rank inside the bucket: bucket b spans [end(b-1), end(b))
-  for (int e = r; e < c; e += gs) {
-    const int key = ck[e];
-    const int b = bucket(key);
-    const int bs = b ? bcnt[b - 1] : 0, be = bcnt[b];
-    int rank = bs;
-    for (int t = bs; t < be; ++t)
-      if (HS_G(dbg, t >= 0 && t < c && order[t] >= 0 && order[t] < c, 24, t)) rank += ck[order[t]] < key;
-    if (!HS_G(dbg, rank >= 0 && rank < c, 25, rank)) continue;
-    sk[rank] = key;
-    if constexpr (HAS_VAL) sv[rank] = cv[e];
+  for (int e0 = r; e0 < c; e0 += EU * gs) {
+    int key[EU], bs[EU], be[EU], rank[EU];
+    T v[EU];
+#pragma unroll
+    for (int u = 0; u < EU; ++u) {
+      const int e = e0 + u * gs;
+      key[u] = e < c ? ck[e] : 0;
+      if constexpr (HAS_VAL) v[u] = e < c ? cv[e] : T{};
+    }
+#pragma unroll
+    for (int u = 0; u < EU; ++u) {
+      const int b = e0 + u * gs < c ? bucket(key[u]) : 0;
+      bs[u] = b ? bcnt[b - 1] : 0;
+      be[u] = e0 + u * gs < c ? bcnt[b] : 0;
+      rank[u] = bs[u];
+    }
+#pragma unroll
+    for (int u = 0; u < EU; ++u)
+      for (int t = bs[u]; t < be[u]; ++t)
+        if (HS_G(dbg, t >= 0 && t < c && order[t] >= 0 && order[t] < c, 24, t)) rank[u] += ck[order[t]] < key[u];
+#pragma unroll
+    for (int u = 0; u < EU; ++u) {
+      if (e0 + u * gs >= c || !HS_G(dbg, rank[u] >= 0 && rank[u] < c, 25, rank[u])) continue;
+      sk[rank[u]] = key[u];
+      if constexpr (HAS_VAL) sv[rank[u]] = v[u];
+    }
   }
   G::sync();
   // (4) coalesced stores

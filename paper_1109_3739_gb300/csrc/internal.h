@@ -12,13 +12,16 @@ namespace hs {
 // concatenated row lists; heavy rows get one key per power of two of f,
 // largest first, so dynamic scheduling hands out the longest rows first.
 constexpr int NKEYS = 64;
-constexpr int KEY_TINY = 1;   // f <= 32: warp, one product per lane
-constexpr int KEY_WARP = 2;   // f <= 512: warp, private shared hash table
-constexpr int KEY_MID = 3;    // symbolic: f <= 4096;  numeric: c <= CAP_MID
-constexpr int KEY_LARGE = 4;  // symbolic: f <= min(16384, cap_large); numeric: c <= cap_large
-constexpr int KEY_HEAVY = 5;  // 5 + (62 - floor(log2 f)): symbolic bitmap / numeric column parts
-constexpr int F_TINY = 32, F_WARP = 512, F_MID = 4096, F_LARGE = 16384;
-constexpr int CAP_MID = 2048;
+constexpr int KEY_TINY = 1;     // f <= 32: warp, one product per lane
+constexpr int KEY_WARP_S = 2;   // numeric: f <= 128: warp, 256-slot table
+constexpr int KEY_WARP = 3;     // f <= 512: warp, private shared hash table
+constexpr int KEY_MID_S = 4;    // symbolic: f <= 1024;  numeric: c <= 1024
+constexpr int KEY_MID = 5;      // symbolic: f <= 4096;  numeric: c <= CAP_MID
+constexpr int KEY_LARGE_S = 6;  // numeric: c <= cap_large / 2
+constexpr int KEY_LARGE = 7;    // symbolic: f <= min(16384, cap_large); numeric: c <= cap_large
+constexpr int KEY_HEAVY = 8;    // 8 + (62 - floor(log2 f)): symbolic bitmap / numeric column parts
+constexpr int F_TINY = 32, F_WARP_S = 128, F_WARP = 512, F_MID_S = 1024, F_MID = 4096, F_LARGE = 16384;
+constexpr int CAP_MID_S = 1024, CAP_MID = 2048;
 // Column segments recorded for rows that may need column parts: width SEG_W
 // (a multiple of 1024, at most every numeric table's capacity).
 constexpr int SEG_W = 4096;
@@ -40,15 +43,21 @@ __host__ __device__ inline int sym_key(int64_t f, int cap_large) {
   if (f <= 0) return 0;
   if (f <= F_TINY) return KEY_TINY;
   if (f <= F_WARP) return KEY_WARP;
+  if (f <= F_MID_S) return KEY_MID_S;
   if (f <= F_MID) return KEY_MID;
   if (f <= F_LARGE && f <= cap_large) return KEY_LARGE;
   return heavy_key(f);
 }
+// Numeric bins: the smaller tiers take smaller tables, so more of their rows
+// are in flight on an SM at once.
 __host__ __device__ inline int num_key(int64_t f, int64_t c, int cap_large) {
   if (c <= 0) return 0;
   if (f <= F_TINY) return KEY_TINY;
+  if (f <= F_WARP_S) return KEY_WARP_S;
   if (f <= F_WARP) return KEY_WARP;
+  if (c <= CAP_MID_S) return KEY_MID_S;
   if (c <= CAP_MID) return KEY_MID;
+  if (c <= cap_large / 2) return KEY_LARGE_S;
   if (c <= cap_large) return KEY_LARGE;
   return heavy_key(f);
 }
@@ -133,6 +142,7 @@ struct SymArgs {
 };
 void launch_sym_tiny(const SymArgs &a, cudaStream_t st);
 void launch_sym_warp(const SymArgs &a, cudaStream_t st);
+void launch_sym_mid_s(const SymArgs &a, cudaStream_t st);
 void launch_sym_mid(const SymArgs &a, cudaStream_t st);
 void launch_sym_large(const SymArgs &a, cudaStream_t st);
 void launch_sym_heavy(const SymArgs &a, cudaStream_t st);
@@ -159,7 +169,10 @@ struct NumArgs {
   const int32_t *bci_id;  // per B row: its row of the segment index (-1 none), or null
   const int32_t *bci;     // segment index: nseg+1 offsets per indexed B row
 };
-// kind: 0 tiny, 1 warp, 2 mid, 3 large, 4 heavy.  dtype codes as in the ABI.
+// kind: 0 tiny, 1 warp_s, 2 warp, 3 mid_s, 4 mid, 5 large_s, 6 large, 7 heavy
+// (bin key KEY_TINY + kind; heavy takes every key from KEY_HEAVY on).
+// dtype codes as in the ABI.
+constexpr int NUM_KINDS = 8;
 bool launch_numeric_pt(int dtype, int kind, const NumArgs &a, cudaStream_t st);
 bool launch_numeric_mp(int dtype, int kind, const NumArgs &a, cudaStream_t st);
 bool launch_numeric_oa(int kind, const NumArgs &a, cudaStream_t st);

@@ -209,6 +209,8 @@ static int spgemm_noalloc_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat 
   launch_sym_tiny(sa, st);
   sym_bin(KEY_WARP, KEY_WARP + 1);
   launch_sym_warp(sa, st);
+  sym_bin(KEY_MID_S, KEY_MID_S + 1);
+  launch_sym_mid_s(sa, st);
   sym_bin(KEY_MID, KEY_MID + 1);
   launch_sym_mid(sa, st);
   sym_bin(KEY_LARGE, KEY_LARGE + 1);
@@ -240,11 +242,10 @@ static int spgemm_noalloc_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat 
   }
   NumArgs na{rs,   rb,   f,    nullptr,     0,        Cp,   C->idx, C->val,  hslot,
              hist, nseg, &sb->dyn[1], &sb->err, gcur, gend, nullptr, nullptr, nullptr, nullptr};
-  const int k0s[5] = {KEY_TINY, KEY_WARP, KEY_MID, KEY_LARGE, KEY_HEAVY};
-  const int k1s[5] = {KEY_TINY + 1, KEY_WARP + 1, KEY_MID + 1, KEY_LARGE + 1, NKEYS};
-  for (int kind = 0; kind < 5; ++kind) {
-    na.list = list + key_off[k0s[kind]];
-    na.count = key_off[k1s[kind]] - key_off[k0s[kind]];
+  for (int kind = 0; kind < NUM_KINDS; ++kind) {
+    const int k0 = KEY_TINY + kind, k1 = kind == NUM_KINDS - 1 ? NKEYS : k0 + 1;
+    na.list = list + key_off[k0];
+    na.count = key_off[k1] - key_off[k0];
     if (na.count > 0 && !na_launch_num(sr, out_dt, kind, na, st)) return HS_EINVAL;
   }
   if (int e = check_last()) return e;

@@ -101,21 +101,22 @@ __global__ void __launch_bounds__(NTINY_WPB * 32, 4) k_num_tiny(NumArgs a) {
 }
 
 // --------------------------------------------------------------- warp
-constexpr int NWARP_WPB = 4, NWARP_SLOTS = 1024, NWARP_CAP = 512;
+constexpr int NWARP_WPB = 4;
 
-template <typename T> struct WarpNumSmem {
-  static constexpr size_t table_bytes = (size_t)NWARP_SLOTS * (4 + vbytes<T>());
-  static constexpr size_t work_bytes = ((((size_t)(NWARP_CAP / 1 + 2 * NWARP_CAP) * 4 + 7) & ~(size_t)7)) +
-                                       (size_t)NWARP_CAP * vbytes<T>();
+// a warp's table (SLOTS), its compacted entries (at most CAP) and sort scratch
+template <typename T, int SLOTS, int CAP> struct WarpNumSmem {
+  static constexpr size_t table_bytes = (size_t)SLOTS * (4 + vbytes<T>());
+  static constexpr size_t work_bytes = ((((size_t)(CAP / 1 + 2 * CAP) * 4 + 7) & ~(size_t)7)) +
+                                       (size_t)CAP * vbytes<T>();
   static constexpr size_t region0 = ((table_bytes > work_bytes ? table_bytes : work_bytes) + 15) & ~(size_t)15;
-  static constexpr size_t compact = (((size_t)NWARP_CAP * (4 + vbytes<T>())) + 15) & ~(size_t)15;
+  static constexpr size_t compact = (((size_t)CAP * (4 + vbytes<T>())) + 15) & ~(size_t)15;
   static constexpr size_t per_warp = region0 + compact + 16;
 };
 
-template <class SR>
+template <class SR, int NWARP_SLOTS, int NWARP_CAP>
 __global__ void __launch_bounds__(NWARP_WPB * 32, 4) k_num_warp(NumArgs a) {
   using T = typename SR::val_t;
-  using L = WarpNumSmem<T>;
+  using L = WarpNumSmem<T, NWARP_SLOTS, NWARP_CAP>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int w = threadIdx.x >> 5, lane = lane_id();
   unsigned char *base = smem_raw + (size_t)w * L::per_warp;
@@ -149,7 +150,9 @@ __global__ void __launch_bounds__(NWARP_WPB * 32, 4) k_num_warp(NumArgs a) {
 }
 
 // ---------------------------------------------------- mid / large / heavy
-constexpr int NCH = 1024;  // A entries per expansion round
+// A entries per expansion round: the mid kernel stages fewer so that more of
+// its CTAs fit an SM (rows in flight hide each other's latency)
+template <int CAP> constexpr int nch() { return CAP >= 8192 ? 1024 : 256; }
 
 template <typename T, int SLOTS, int CAP> struct CtaNumLayout {
   static constexpr size_t table_bytes = (size_t)SLOTS * (4 + vbytes<T>());
@@ -158,7 +161,7 @@ template <typename T, int SLOTS, int CAP> struct CtaNumLayout {
   static constexpr size_t region0 = ((table_bytes > work_bytes ? table_bytes : work_bytes) + 15) & ~(size_t)15;
   static constexpr size_t compact = (((size_t)CAP * (4 + vbytes<T>())) + 15) & ~(size_t)15;
   static constexpr size_t ex_off = region0 + compact;
-  static constexpr size_t tail_off = ex_off + ((sizeof(CtaExpandSmem<T, NCH>) + 15) & ~(size_t)15);
+  static constexpr size_t tail_off = ex_off + ((sizeof(CtaExpandSmem<T, nch<CAP>()>) + 15) & ~(size_t)15);
   struct Tail {
     EmitScratch es;
     int wtmp[33];
@@ -169,8 +172,8 @@ template <typename T, int SLOTS, int CAP> struct CtaNumLayout {
   static constexpr size_t bytes = tail_off + sizeof(Tail);
 };
 
-template <class SR, int SLOTS, int CAP>
-__global__ void __launch_bounds__(CAP > 2048 ? 1024 : 256, 1) k_num_cta(NumArgs a) {
+template <class SR, int SLOTS, int CAP, int NT>
+__global__ void __launch_bounds__(NT, 1) k_num_cta(NumArgs a) {
   using T = typename SR::val_t;
   using L = CtaNumLayout<T, SLOTS, CAP>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -178,7 +181,7 @@ __global__ void __launch_bounds__(CAP > 2048 ? 1024 : 256, 1) k_num_cta(NumArgs 
   T *vals = reinterpret_cast<T *>(smem_raw + (size_t)SLOTS * 4);
   int *ck = reinterpret_cast<int *>(smem_raw + L::region0);
   T *cv = reinterpret_cast<T *>(smem_raw + L::region0 + (size_t)CAP * 4);
-  auto &ex = *reinterpret_cast<CtaExpandSmem<T, NCH> *>(smem_raw + L::ex_off);
+  auto &ex = *reinterpret_cast<CtaExpandSmem<T, nch<CAP>()> *>(smem_raw + L::ex_off);
   auto &tl = *reinterpret_cast<typename L::Tail *>(smem_raw + L::tail_off);
   const DevCsr A = ndev_a(a.A), B = ndev_b(a.B);
   T *Cv = reinterpret_cast<T *>(a.Cv);
@@ -195,7 +198,7 @@ __global__ void __launch_bounds__(CAP > 2048 ? 1024 : 256, 1) k_num_cta(NumArgs 
       if constexpr (SR::has_val) vals[s] = SR::identity();
     }
     __syncthreads();
-    cta_products<SR, NCH>(A, B, A.p[r], A.p[r + 1], false, 0, 0, ex, tl.wtmp,
+    cta_products<SR, nch<CAP>()>(A, B, A.p[r], A.p[r + 1], false, 0, 0, ex, tl.wtmp,
                           [&](int col, T v, int) { hash_insert_val<SR>(keys, vals, mask, col, v, a.err); });
     group_sort_emit<CtaGroup, T, SR::has_val>(keys, vals, slots, c, ck, cv, smem_raw, tl.wtmp, &tl.es,
                                               a.Cj + cb, SR::has_val ? Cv + cb : nullptr, a.err, CAP, a.A.dbg);
@@ -578,6 +581,33 @@ inline int ngrid_cap(int items, int per_block, int per_sm) {
   int cap = sm_count() * per_sm;
   return g < cap ? (g < 1 ? 1 : g) : cap;
 }
+// CTAs that fit one SM for this kernel, block size and dynamic shared memory
+template <class K> int fit_per_sm(K kernel, int threads, size_t smem) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    n = 1;
+  }
+  return n < 1 ? 1 : n;
+}
+
+template <class SR, int SLOTS, int CAP> void launch_num_warp(const NumArgs &a, cudaStream_t st) {
+  using T = typename SR::val_t;
+  const size_t bytes = WarpNumSmem<T, SLOTS, CAP>::per_warp * NWARP_WPB;
+  auto k = k_num_warp<SR, SLOTS, CAP>;
+  set_smem_attr(k, bytes);
+  count_launch();
+  k<<<ngrid_cap(a.count, NWARP_WPB, fit_per_sm(k, NWARP_WPB * 32, bytes)), NWARP_WPB * 32, bytes, st>>>(a);
+}
+
+template <class SR, int SLOTS, int CAP, int NT> void launch_num_cta(const NumArgs &a, cudaStream_t st) {
+  using T = typename SR::val_t;
+  using L = CtaNumLayout<T, SLOTS, CAP>;
+  auto k = k_num_cta<SR, SLOTS, CAP, NT>;
+  set_smem_attr(k, L::bytes);
+  count_launch();
+  k<<<ngrid_cap(a.count, 1, fit_per_sm(k, NT, L::bytes)), NT, L::bytes, st>>>(a);
+}
 
 template <class SR> void launch_numeric_sr(int kind, const NumArgs &a, cudaStream_t st) {
   using T = typename SR::val_t;
@@ -588,28 +618,15 @@ template <class SR> void launch_numeric_sr(int kind, const NumArgs &a, cudaStrea
       count_launch();
       k_num_tiny<SR><<<ngrid_cap(a.count, NTINY_WPB, 8), NTINY_WPB * 32, 0, st>>>(a);
       break;
-    case 1: {
-      const size_t bytes = WarpNumSmem<T>::per_warp * NWARP_WPB;
-      set_smem_attr(k_num_warp<SR>, bytes);
-      count_launch();
-      k_num_warp<SR><<<ngrid_cap(a.count, NWARP_WPB, 3), NWARP_WPB * 32, bytes, st>>>(a);
+    case 1: launch_num_warp<SR, 2 * F_WARP_S, F_WARP_S>(a, st); break;
+    case 2: launch_num_warp<SR, 2 * F_WARP, F_WARP>(a, st); break;
+    case 3: launch_num_cta<SR, 2 * CAP_MID_S, CAP_MID_S, 256>(a, st); break;
+    case 4: launch_num_cta<SR, 2 * CAP_MID, CAP_MID, 256>(a, st); break;
+    case 5:
+      if constexpr (CAPL / 2 > CAP_MID) launch_num_cta<SR, CAPL, CAPL / 2, 512>(a, st);
       break;
-    }
-    case 2: {
-      using L = CtaNumLayout<T, 2 * CAP_MID, CAP_MID>;
-      set_smem_attr(k_num_cta<SR, 2 * CAP_MID, CAP_MID>, L::bytes);
-      count_launch();
-      k_num_cta<SR, 2 * CAP_MID, CAP_MID><<<ngrid_cap(a.count, 1, 3), 256, L::bytes, st>>>(a);
-      break;
-    }
-    case 3: {
-      using L = CtaNumLayout<T, 2 * CAPL, CAPL>;
-      set_smem_attr(k_num_cta<SR, 2 * CAPL, CAPL>, L::bytes);
-      count_launch();
-      k_num_cta<SR, 2 * CAPL, CAPL><<<ngrid_cap(a.count, 1, 1), 1024, L::bytes, st>>>(a);
-      break;
-    }
-    case 4: {
+    case 6: launch_num_cta<SR, 2 * CAPL, CAPL, 1024>(a, st); break;
+    case 7: {
       const size_t bytes = sizeof(HeavySmem<T>);
       set_smem_attr(k_num_heavy<SR>, bytes);
       count_launch();

@@ -396,6 +396,9 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
     sym_bin(KEY_WARP, KEY_WARP + 1);
     { PhaseTimer t2("symbolic_warp", st, sa.count > 0); launch_sym_warp(sa, st); }
     if (int e = phase_check("symbolic_warp", st, sb->dbg)) return e;
+    sym_bin(KEY_MID_S, KEY_MID_S + 1);
+    { PhaseTimer t2("symbolic_mid_s", st, sa.count > 0); launch_sym_mid_s(sa, st); }
+    if (int e = phase_check("symbolic_mid_s", st, sb->dbg)) return e;
     sym_bin(KEY_MID, KEY_MID + 1);
     { PhaseTimer t2("symbolic_mid", st, sa.count > 0); launch_sym_mid(sa, st); }
     if (int e = phase_check("symbolic_mid", st, sb->dbg)) return e;
@@ -481,14 +484,15 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
   }
   NumArgs na{rs, rb,   f,    nullptr, 0,    Cp,    C->idx, C->val, hslot,
              hist, nseg, &sb->dyn[1], &sb->err, gcur, gend, glist, loff, bci_id, bci};
-  const char *names[5] = {"numeric_tiny", "numeric_warp", "numeric_mid", "numeric_large", "numeric_heavy"};
-  const int k0s[5] = {KEY_TINY, KEY_WARP, KEY_MID, KEY_LARGE, KEY_HEAVY};
-  const int k1s[5] = {KEY_TINY + 1, KEY_WARP + 1, KEY_MID + 1, KEY_LARGE + 1, NKEYS};
+  const char *names[NUM_KINDS] = {"numeric_tiny", "numeric_warp_s", "numeric_warp",  "numeric_mid_s",
+                                  "numeric_mid",  "numeric_large_s", "numeric_large", "numeric_heavy"};
+  static_assert(KEY_TINY + NUM_KINDS - 1 == KEY_HEAVY, "one key per numeric kind before the heavy keys");
   {
     PhaseTimer t("numeric", st);
-    for (int kind = 0; kind < 5; ++kind) {
-      na.list = list + key_off[k0s[kind]];
-      na.count = key_off[k1s[kind]] - key_off[k0s[kind]];
+    for (int kind = 0; kind < NUM_KINDS; ++kind) {
+      const int k0 = KEY_TINY + kind, k1 = kind == NUM_KINDS - 1 ? NKEYS : k0 + 1;
+      na.list = list + key_off[k0];
+      na.count = key_off[k1] - key_off[k0];
       {
         PhaseTimer t2(names[kind], st, na.count > 0);
         if (na.count > 0 && !launch_num(sr, out_dt, kind, na, st)) return HS_EINVAL;

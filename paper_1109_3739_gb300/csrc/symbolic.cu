@@ -6,9 +6,11 @@
 //   tiny  (f <= 32)    one warp, one product per lane, equal columns found
 //                      with __match_any_sync;
 //   warp  (f <= 512)   one warp, private shared-memory hash set;
-//   mid   (f <= 4096)  one CTA, shared hash set of 2f..8192 slots;
-//   large (f <= min(16384, cap_large))
-//                      one CTA, shared hash set of up to 32768 slots;
+//   mid   (f <= 1024, and f <= 4096)
+//                      one CTA, shared hash set of 2f slots (at most 2048,
+//                      and 8192: the smaller tier keeps more CTAs per SM);
+//   large (f <= min(16384, cap_large), so f <= 8192)
+//                      one CTA, shared hash set of up to 16384 slots;
 //   heavy (larger f)   one CTA, a bitmap over 2^20 columns (occupancy SPA in
 //                      shared memory), rows handed out largest first.  The
 //                      bitmap is read out in column order, so the kernel also
@@ -94,20 +96,20 @@ __global__ void __launch_bounds__(WARP_WPB * 32, 4) k_sym_warp(SymArgs a) {
 }
 
 // ----------------------------------------------------------- mid / large
-constexpr int CH = 1024;  // A entries per expansion round
+constexpr int CH = 1024;   // A entries per expansion round (heavy)
+constexpr int CHM = 256;   // the same for the hash kernels: smaller staging, more CTAs per SM
 
-template <int SLOTS, bool HIST> struct SymCtaSmem {
+template <int SLOTS> struct SymCtaSmem {
   int keys[SLOTS];
-  CtaExpandSmem<NoVal, CH> ex;
+  CtaExpandSmem<NoVal, CHM> ex;
   int wtmp[33];
   int total;
-  unsigned segcnt[HIST ? SEG_SMEM : 1];  // per-segment counts of the current row
 };
 
-template <int SLOTS, bool HIST>
-__global__ void __launch_bounds__(HIST ? 512 : 256) k_sym_cta(SymArgs a) {
+template <int SLOTS, int NT>
+__global__ void __launch_bounds__(NT) k_sym_cta(SymArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  auto &sm = *reinterpret_cast<SymCtaSmem<SLOTS, HIST> *>(smem_raw);
+  auto &sm = *reinterpret_cast<SymCtaSmem<SLOTS> *>(smem_raw);
   const DevCsr A = dev_a(a.A), B = dev_b(a.B);
   for (int idx = blockIdx.x; idx < a.count; idx += gridDim.x) {
     const int r = a.list[idx];
@@ -118,32 +120,10 @@ __global__ void __launch_bounds__(HIST ? 512 : 256) k_sym_cta(SymArgs a) {
     if (threadIdx.x == 0) sm.total = 0;
     __syncthreads();
     int cnt = 0;
-    cta_products<StructSR, CH>(A, B, A.p[r], A.p[r + 1], false, 0, 0, sm.ex, sm.wtmp,
-                               [&](int col, NoVal, int) { cnt += hash_insert_key(sm.keys, mask, col); });
+    cta_products<StructSR, CHM>(A, B, A.p[r], A.p[r + 1], false, 0, 0, sm.ex, sm.wtmp,
+                                [&](int col, NoVal, int) { cnt += hash_insert_key(sm.keys, mask, col); });
     cnt = warp_sum(cnt);
     if (lane_id() == 0 && cnt) atomicAdd(&sm.total, cnt);
-    if constexpr (HIST) {
-      const int h = a.hslot[r];
-      if (h >= 0) {
-        uint32_t *hist = a.hist + (int64_t)h * a.nseg;
-        if (a.nseg <= SEG_SMEM) {
-          // count in shared memory, then write the row's histogram once
-          for (int g = threadIdx.x; g < a.nseg; g += blockDim.x) sm.segcnt[g] = 0u;
-          __syncthreads();
-          for (int s = threadIdx.x; s < slots; s += blockDim.x) {
-            const int k = sm.keys[s];
-            if (k != EMPTY && HS_G(a.A.dbg, k / SEG_W < a.nseg, 31, k)) atomicAdd(sm.segcnt + k / SEG_W, 1u);
-          }
-          __syncthreads();
-          for (int g = threadIdx.x; g < a.nseg; g += blockDim.x) hist[g] = sm.segcnt[g];
-        } else {
-          for (int s = threadIdx.x; s < slots; s += blockDim.x) {
-            const int k = sm.keys[s];
-            if (k != EMPTY && HS_G(a.A.dbg, k / SEG_W < a.nseg, 31, k)) atomicAdd(hist + k / SEG_W, 1u);
-          }
-        }
-      }
-    }
     __syncthreads();
     if (threadIdx.x == 0) put_count(a, out_row(a.A, r), sm.total);
     __syncthreads();
@@ -309,21 +289,33 @@ void launch_sym_tiny(const SymArgs &a, cudaStream_t st) {
   count_launch();
   k_sym_tiny<<<grid_cap(a.count, TINY_WPB, 8), TINY_WPB * 32, 0, st>>>(a);
 }
+// CTAs that fit one SM for this kernel, block size and dynamic shared memory
+template <class K> static int fit_per_sm(K kernel, int threads, size_t smem) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    n = 1;
+  }
+  return n < 1 ? 1 : n;
+}
+
 void launch_sym_warp(const SymArgs &a, cudaStream_t st) {
   if (a.count <= 0) return;
   count_launch();
-  k_sym_warp<<<grid_cap(a.count, WARP_WPB, 6), WARP_WPB * 32, 0, st>>>(a);
+  k_sym_warp<<<grid_cap(a.count, WARP_WPB, fit_per_sm(k_sym_warp, WARP_WPB * 32, 0)), WARP_WPB * 32, 0, st>>>(a);
 }
 
-template <int SLOTS, bool HIST> static void launch_sym_cta(const SymArgs &a, int nt, int per_sm, cudaStream_t st) {
+template <int SLOTS, int NT> static void launch_sym_cta(const SymArgs &a, cudaStream_t st) {
   if (a.count <= 0) return;
-  const size_t bytes = sizeof(SymCtaSmem<SLOTS, HIST>);
-  set_smem_attr(k_sym_cta<SLOTS, HIST>, bytes);
+  const size_t bytes = sizeof(SymCtaSmem<SLOTS>);
+  set_smem_attr(k_sym_cta<SLOTS, NT>, bytes);
   count_launch();
-  k_sym_cta<SLOTS, HIST><<<grid_cap(a.count, 1, per_sm), nt, bytes, st>>>(a);
+  k_sym_cta<SLOTS, NT><<<grid_cap(a.count, 1, fit_per_sm(k_sym_cta<SLOTS, NT>, NT, bytes)), NT, bytes, st>>>(a);
 }
-void launch_sym_mid(const SymArgs &a, cudaStream_t st) { launch_sym_cta<8192, false>(a, 256, 4, st); }
-void launch_sym_large(const SymArgs &a, cudaStream_t st) { launch_sym_cta<32768, true>(a, 512, 1, st); }
+// table capacity 2f: mid rows have f <= 4096, large rows f <= min(16384, cap_large) = 8192 at most
+void launch_sym_mid_s(const SymArgs &a, cudaStream_t st) { launch_sym_cta<2 * F_MID_S, 256>(a, st); }
+void launch_sym_mid(const SymArgs &a, cudaStream_t st) { launch_sym_cta<2 * F_MID, 256>(a, st); }
+void launch_sym_large(const SymArgs &a, cudaStream_t st) { launch_sym_cta<16384, 512>(a, st); }
 
 void launch_sym_heavy(const SymArgs &a, cudaStream_t st) {
   if (a.count <= 0) return;
