@@ -243,6 +243,24 @@ def run_batched(args):
     nb_launch = (h.launch_count() - l0) // (args.steps + args.warmup)
     nnz_c = res[0].nnz
     res = None
+    # the batch's numeric pass replayed from a captured CUDA graph: structure
+    # from one plan (symbolic once), values recomputed by every replay
+    SA, SB, _ = h.batch_stack(As, Bs, stream=stream)
+    plan = h.Plan("plus_times", SA, SB, stream=stream)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        plan.execute()
+    stream.wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    l0 = h.launch_count()
+    with torch.cuda.graph(graph):
+        plan.execute()
+    replay_launches = h.launch_count() - l0
+    tg, _ = timed(lambda: graph.replay(), args.steps, args.warmup)
+    plan.status()
+    plan.close()
+    plan = graph = SA = SB = None
     l0 = h.launch_count()
     tl, res = timed(lambda: [h.spgemm("plus_times", a, b, stream=stream) for a, b in zip(As, Bs)],
                     max(1, args.steps // 3), 1)
@@ -262,6 +280,11 @@ def run_batched(args):
         "one_call_per_problem": {"ms_per_step": med_l, "value": flops / (med_l / 1000.0),
                                  "gpu_launches": nl_launch},
         "speedup_vs_one_call_per_problem": med_l / med_b,
+        "numeric_graph_replay": {"ms_per_step": statistics.median(tg),
+                                 "value": flops / (statistics.median(tg) / 1000.0),
+                                 "gpu_launches": replay_launches,
+                                 "what": "values of every product recomputed on the plan's structure "
+                                         "(hs_plan_execute captured once in a CUDA graph)"},
         "gpu_launches": nb_launch,
         "phases_ms_per_step": phases,
     }), flush=True)

@@ -153,6 +153,46 @@ int hs_spasgn(const hs_mat *A, const int32_t *I, int64_t nI, const int32_t *J, i
 int hs_spgemm_batched(int semiring, int64_t count, const hs_mat *A, const hs_mat *B, hs_mat *C,
                       int64_t *row_offsets, const hs_allocator *al, void *stream, uint32_t flags);
 
+/* Symbolic once, numeric many times.  In a multigrid setup the Galerkin
+ * product R*A*R^T of Section 4.3.2 is recomputed whenever A's values change
+ * while every structure stays the same; a batch of products can be rerun the
+ * same way.  hs_plan_create computes C = A*B exactly as hs_spgemm does (same
+ * arguments, results, errors and allocations of C) and keeps, in a plan,
+ * everything its numeric pass needs: the row bins, the heavy rows' column
+ * lists, the B segment index and the scratch, allocated through `al` (which
+ * must stay valid until hs_plan_destroy).
+ *
+ * hs_plan_execute recomputes C's values from new value arrays of A and B
+ * (device pointers, same dtypes and entry order as at creation) into C_val
+ * (c->nnz values of C's dtype; may be C->val).  It rewrites C->idx with the
+ * same column ids, so C->ptr and C->idx, and A's and B's ptr/idx/ids arrays,
+ * must stay allocated and unchanged while the plan is used.  A_val (B_val) may
+ * be NULL where the semiring ignores that operand's values.  The call only
+ * enqueues kernels (and one 4-byte memset) on `stream`: it allocates nothing
+ * and never waits for the GPU, so it can be captured in a CUDA graph and
+ * replayed.  Executions of one plan must not overlap (they share its scratch).
+ * Device-side checks raised during executes are reported by hs_plan_status,
+ * which synchronises with `stream`: HS_OK or HS_EINTERNAL.
+ *
+ * hs_plan_destroy releases the plan's scratch on `stream` (C is the caller's
+ * and is released with hs_mat_free). */
+typedef struct hs_plan hs_plan;
+int hs_plan_create(int semiring, const hs_mat *A, const hs_mat *B, hs_mat *C, hs_plan **plan,
+                   const hs_allocator *al, void *stream, uint32_t flags);
+int hs_plan_execute(const hs_plan *plan, const void *A_val, const void *B_val, void *C_val, void *stream);
+int hs_plan_status(const hs_plan *plan, void *stream);
+void hs_plan_destroy(hs_plan *plan, void *stream);
+
+/* The stacked operands of a batch: SA holds A_0..A_{count-1} one after the
+ * other (rows concatenated, column ids shifted to the stacked rows of SB), SB
+ * holds B_0..B_{count-1} likewise (local column ids), so SA*SB is the block
+ * diagonal product whose rows row_offsets[i]..row_offsets[i+1] are A_i*B_i.
+ * Same requirements on the inputs as hs_spgemm_batched; SA and SB are
+ * allocated through `al`, owned by the caller and released with hs_mat_free.
+ * hs_spgemm_batched is this call, one hs_spgemm and the release of SA, SB. */
+int hs_batch_stack(int64_t count, const hs_mat *A, const hs_mat *B, hs_mat *SA, hs_mat *SB,
+                   int64_t *row_offsets, const hs_allocator *al, void *stream);
+
 /* SpGEMM for callers that cannot allocate device memory while they run (the
  * paper has no counterpart): for example code that has given the GPU's memory
  * to its own pool and must keep its footprint fixed, or code running where a

@@ -94,11 +94,12 @@ static int vb_of(int dt) {
 
 using namespace hs;
 
-extern "C" int hs_spgemm_batched(int semiring, int64_t count, const hs_mat *A, const hs_mat *B, hs_mat *C,
-                                 int64_t *row_offsets, const hs_allocator *al, void *stream, uint32_t flags) {
-  if (!C || count < 0 || (count > 0 && (!A || !B || !row_offsets))) return HS_EINVAL;
+extern "C" int hs_batch_stack(int64_t count, const hs_mat *A, const hs_mat *B, hs_mat *SA, hs_mat *SB,
+                              int64_t *row_offsets, const hs_allocator *al, void *stream) {
+  if (!SA || !SB || count < 0 || (count > 0 && (!A || !B || !row_offsets))) return HS_EINVAL;
   if (count > 0x7fffffffLL) return HS_EUNSUPPORTED;
-  memset(C, 0, sizeof(*C));
+  memset(SA, 0, sizeof(*SA));
+  memset(SB, 0, sizeof(*SB));
   cudaStream_t st = (cudaStream_t)stream;
   // host-side layout of the stacked operands
   std::vector<BatchDesc> d((size_t)count);
@@ -126,7 +127,7 @@ extern "C" int hs_spgemm_batched(int semiring, int64_t count, const hs_mat *A, c
   }
   for (int64_t i = 0; i <= count; ++i) row_offsets[i] = a_row[i];
 
-  // temporaries through the caller's allocator (or cudaMallocAsync)
+  // outputs and temporaries through the caller's allocator (or cudaMallocAsync)
   auto alloc = [&](size_t bytes) -> void * {
     if (bytes == 0) bytes = 16;
     void *p = nullptr;
@@ -146,23 +147,23 @@ extern "C" int hs_spgemm_batched(int semiring, int64_t count, const hs_mat *A, c
     void *p;
     size_t n;
   };
-  std::vector<Blk> blocks;
-  auto take = [&](size_t bytes) -> void * {
+  std::vector<Blk> temps, outs;
+  auto take = [&](std::vector<Blk> &v, size_t bytes) -> void * {
     void *p = alloc(bytes);
-    if (p) blocks.push_back({p, bytes});
+    if (p) v.push_back({p, bytes ? bytes : 16});
     return p;
   };
+  const int64_t am = a_row[count], annz = a_nnz[count], bm = b_row[count], bnnz = b_nnz[count];
   int status = HS_OK;
   do {
-    const int64_t am = a_row[count], annz = a_nnz[count], bm = b_row[count], bnnz = b_nnz[count];
-    BatchDesc *dd = (BatchDesc *)take(sizeof(BatchDesc) * (size_t)(count ? count : 1));
-    int64_t *offs = (int64_t *)take(sizeof(int64_t) * 4 * (size_t)(count + 1));
-    int64_t *Ap = (int64_t *)take(sizeof(int64_t) * (size_t)(am + 1));
-    int32_t *Aj = (int32_t *)take(sizeof(int32_t) * (size_t)annz);
-    void *Av = avb ? take((size_t)avb * (size_t)annz) : nullptr;
-    int64_t *Bp = (int64_t *)take(sizeof(int64_t) * (size_t)(bm + 1));
-    int32_t *Bj = (int32_t *)take(sizeof(int32_t) * (size_t)bnnz);
-    void *Bv = bvb ? take((size_t)bvb * (size_t)bnnz) : nullptr;
+    BatchDesc *dd = (BatchDesc *)take(temps, sizeof(BatchDesc) * (size_t)(count ? count : 1));
+    int64_t *offs = (int64_t *)take(temps, sizeof(int64_t) * 4 * (size_t)(count + 1));
+    int64_t *Ap = (int64_t *)take(outs, sizeof(int64_t) * (size_t)(am + 1));
+    int32_t *Aj = (int32_t *)take(outs, sizeof(int32_t) * (size_t)annz);
+    void *Av = avb ? take(outs, (size_t)avb * (size_t)annz) : nullptr;
+    int64_t *Bp = (int64_t *)take(outs, sizeof(int64_t) * (size_t)(bm + 1));
+    int32_t *Bj = (int32_t *)take(outs, sizeof(int32_t) * (size_t)bnnz);
+    void *Bv = bvb ? take(outs, (size_t)bvb * (size_t)bnnz) : nullptr;
     if (!dd || !offs || !Ap || !Aj || !Bp || !Bj || (avb && !Av) || (bvb && !Bv)) {
       status = HS_ENOMEM;
       break;
@@ -194,14 +195,35 @@ extern "C" int hs_spgemm_batched(int semiring, int64_t count, const hs_mat *A, c
       }
       // (copies from pageable host memory return once the source is staged,
       // so the host vectors may go out of scope)
+      if (cudaGetLastError() != cudaSuccess) {
+        status = HS_ECUDA;
+        break;
+      }
     } else {
       cudaMemsetAsync(Ap, 0, 8, st);
       cudaMemsetAsync(Bp, 0, 8, st);
     }
-    hs_mat SA{HS_CSR, adt, am, bm, annz, 0, Ap, Aj, nullptr, Av};
-    hs_mat SB{HS_CSR, bdt, bm, nmax, bnnz, 0, Bp, Bj, nullptr, Bv};
-    status = hs_spgemm(semiring, &SA, &SB, C, al, stream, flags);
+    *SA = hs_mat{HS_CSR, adt, am, bm, annz, 0, Ap, Aj, nullptr, Av};
+    *SB = hs_mat{HS_CSR, bdt, bm, nmax, bnnz, 0, Bp, Bj, nullptr, Bv};
   } while (0);
-  for (auto &b : blocks) release(b.p, b.n);
+  for (auto &b : temps) release(b.p, b.n);
+  if (status != HS_OK) {
+    for (auto &b : outs) release(b.p, b.n);
+    memset(SA, 0, sizeof(*SA));
+    memset(SB, 0, sizeof(*SB));
+  }
+  return status;
+}
+
+extern "C" int hs_spgemm_batched(int semiring, int64_t count, const hs_mat *A, const hs_mat *B, hs_mat *C,
+                                 int64_t *row_offsets, const hs_allocator *al, void *stream, uint32_t flags) {
+  if (!C) return HS_EINVAL;
+  memset(C, 0, sizeof(*C));
+  hs_mat SA, SB;
+  int status = hs_batch_stack(count, A, B, &SA, &SB, row_offsets, al, stream);
+  if (status != HS_OK) return status;
+  status = hs_spgemm(semiring, &SA, &SB, C, al, stream, flags);
+  hs_mat_free(&SA, al, stream);
+  hs_mat_free(&SB, al, stream);
   return status;
 }

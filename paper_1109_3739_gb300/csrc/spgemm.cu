@@ -14,6 +14,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -272,8 +273,27 @@ static bool launch_num(int sr, int out_dt, int kind, const NumArgs &a, cudaStrea
   return false;
 }
 
+}  // namespace hs
+
+// A product's numeric pass, kept for re-execution (hs_plan_*): the numeric
+// arguments with every scratch buffer, the row bins, and the buffers' owner.
+struct hs_plan {
+  int sr = 0, out_dt = 0;
+  int64_t a_nnz = 0, b_nnz = 0, c_nnz = 0;
+  hs::NumArgs na{};
+  const int *list = nullptr;
+  int off[hs::NUM_KINDS] = {0}, count[hs::NUM_KINDS] = {0};
+  int *dyn = nullptr, *err = nullptr;
+  long long *dbg = nullptr;
+  hs_allocator al{};
+  bool has_al = false;
+  std::vector<hs::Mem::Blk> blocks;
+};
+
+namespace hs {
+
 static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem &mem, Mem &outmem,
-                       uint32_t flags) {
+                       uint32_t flags, hs_plan *plan = nullptr) {
   cudaStream_t st = mem.st;
   if (!A || !B || !C) return HS_EINVAL;
   if (A->fmt != HS_CSR && A->fmt != HS_DCSR) return HS_EINVAL;
@@ -302,6 +322,12 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
   if (!Cp) return HS_ENOMEM;
   C->ptr = Cp;
   CK(cudaMemsetAsync(Cp, 0, sizeof(int64_t) * (size_t)(m + 1), st));
+  if (plan) {
+    plan->sr = sr;
+    plan->out_dt = out_dt;
+    plan->a_nnz = A->nnz;
+    plan->b_nnz = B->nnz;
+  }
   if (nslots == 0 || A->nnz == 0 || B->nnz == 0 || n == 0) {
     C->idx = (int32_t *)outmem.raw(4);
     if (!C->idx) return HS_ENOMEM;
@@ -493,6 +519,10 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
       const int k0 = KEY_TINY + kind, k1 = kind == NUM_KINDS - 1 ? NKEYS : k0 + 1;
       na.list = list + key_off[k0];
       na.count = key_off[k1] - key_off[k0];
+      if (plan) {
+        plan->off[kind] = key_off[k0];
+        plan->count[kind] = na.count;
+      }
       {
         PhaseTimer t2(names[kind], st, na.count > 0);
         if (na.count > 0 && !launch_num(sr, out_dt, kind, na, st)) return HS_EINVAL;
@@ -511,6 +541,16 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
       snprintf(t_detail, sizeof(t_detail), "device consistency check %d", hb->err);
       return HS_EINTERNAL;
     }
+  }
+  if (plan) {  // the plan takes over every scratch buffer
+    plan->c_nnz = nnz;
+    plan->na = na;
+    plan->list = list;
+    plan->dyn = &sb->dyn[1];
+    plan->err = &sb->err;
+    plan->dbg = sb->dbg;
+    plan->blocks = std::move(mem.scratch);
+    mem.scratch.clear();
   }
   return HS_OK;
 }
@@ -676,6 +716,82 @@ int hs_spgemm(int semiring, const hs_mat *A, const hs_mat *B, hs_mat *C, const h
   Mem mem{al, (cudaStream_t)stream};
   Mem out{al, (cudaStream_t)stream};
   return with_output(C, out, [&] { return spgemm_impl(semiring, A, B, C, mem, out, flags); });
+}
+
+int hs_plan_create(int semiring, const hs_mat *A, const hs_mat *B, hs_mat *C, hs_plan **plan,
+                   const hs_allocator *al, void *stream, uint32_t flags) {
+  if (!C || !plan) return HS_EINVAL;
+  memset(C, 0, sizeof(*C));
+  *plan = nullptr;
+  t_detail[0] = 0;
+  hs_plan *P = new (std::nothrow) hs_plan();
+  if (!P) return HS_ENOMEM;
+  Mem mem{al, (cudaStream_t)stream};
+  Mem out{al, (cudaStream_t)stream};
+  const int e = with_output(C, out, [&] { return spgemm_impl(semiring, A, B, C, mem, out, flags, P); });
+  if (e != HS_OK) {
+    for (auto &b : P->blocks) mem.release(b.p, b.n);
+    delete P;
+    return e;
+  }
+  if (al) {
+    P->al = *al;
+    P->has_al = true;
+  }
+  *plan = P;
+  return HS_OK;
+}
+
+int hs_plan_execute(const hs_plan *P, const void *A_val, const void *B_val, void *C_val, void *stream) {
+  if (!P) return HS_EINVAL;
+  const int vb = vbytes_of(P->out_dt);
+  const bool need_a = P->sr == HS_PLUS_TIMES || P->sr == HS_MIN_PLUS || (P->sr == HS_SELECT1ST && vb);
+  const bool need_b = P->sr == HS_PLUS_TIMES || P->sr == HS_MIN_PLUS || (P->sr == HS_SELECT2ND && vb);
+  if ((need_a && P->a_nnz && !A_val) || (need_b && P->b_nnz && !B_val) || (vb && P->c_nnz && !C_val))
+    return HS_EINVAL;
+  if (P->c_nnz == 0) return HS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  NumArgs na = P->na;
+  na.A.v = A_val;
+  na.B.v = B_val;
+  na.Cv = C_val;
+  CK(cudaMemsetAsync(P->dyn, 0, sizeof(int), st));
+  for (int kind = 0; kind < NUM_KINDS; ++kind) {
+    if (P->count[kind] <= 0) continue;
+    na.list = P->list + P->off[kind];
+    na.count = P->count[kind];
+    if (!launch_num(P->sr, P->out_dt, kind, na, st)) return HS_EINVAL;
+  }
+  return check_launch();
+}
+
+int hs_plan_status(const hs_plan *P, void *stream) {
+  if (!P) return HS_EINVAL;
+  if (!P->err) return HS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  int *h = (int *)pinned(3 * sizeof(long long));
+  if (!h) return HS_ECUDA;
+  long long *hd = reinterpret_cast<long long *>(h) + 1;
+  CK(cudaMemcpyAsync(h, P->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hd, P->dbg, 2 * sizeof(long long), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (hd[0]) {
+    snprintf(t_detail, sizeof(t_detail), "index check %lld failed at %lld", hd[0], hd[1]);
+    return HS_EINTERNAL;
+  }
+  if (h[0]) {
+    snprintf(t_detail, sizeof(t_detail), "device consistency check %d", h[0]);
+    return HS_EINTERNAL;
+  }
+  return HS_OK;
+}
+
+void hs_plan_destroy(hs_plan *P, void *stream) {
+  if (!P) return;
+  Mem mem{P->has_al ? &P->al : nullptr, (cudaStream_t)stream};
+  for (auto &b : P->blocks) mem.release(b.p, b.n);
+  P->blocks.clear();
+  delete P;
 }
 
 int hs_spref(const hs_mat *A, const int32_t *I, int64_t nI, const int32_t *J, int64_t nJ, hs_mat *B,

@@ -81,6 +81,17 @@ def _lib():
             L.hs_spgemm_batched.restype = ci
             L.hs_spgemm_noalloc.argtypes = [ci, P(hs_mat), P(hs_mat), P(hs_mat), i64, vp]
             L.hs_spgemm_noalloc.restype = ci
+            L.hs_plan_create.argtypes = [ci, P(hs_mat), P(hs_mat), P(hs_mat), P(vp), P(hs_allocator), vp, u32]
+            L.hs_plan_create.restype = ci
+            L.hs_plan_execute.argtypes = [vp, vp, vp, vp, vp]
+            L.hs_plan_execute.restype = ci
+            L.hs_plan_status.argtypes = [vp, vp]
+            L.hs_plan_status.restype = ci
+            L.hs_plan_destroy.argtypes = [vp, vp]
+            L.hs_plan_destroy.restype = None
+            L.hs_batch_stack.argtypes = [i64, P(hs_mat), P(hs_mat), P(hs_mat), P(hs_mat), P(ctypes.c_int64),
+                                         P(hs_allocator), vp]
+            L.hs_batch_stack.restype = ci
             L.hs_mat_free.argtypes = [P(hs_mat), P(hs_allocator), vp]
             L.hs_mat_free.restype = None
             L.hs_strerror.argtypes = [ci]
@@ -249,6 +260,76 @@ def spgemm_batched(semiring: str, As: list, Bs: list, validate: bool = False, st
     if st != 0:
         raise HsError(st, "hs_spgemm_batched")
     return _adopt_output(al, c), np.array(offs[:], dtype=np.int64)
+
+
+def batch_stack(As: list, Bs: list, stream=None):
+    """The stacked operands (SA, SB, row_offsets) of a batch (hs_batch_stack):
+    SA*SB is the block-diagonal product whose rows row_offsets[i]..[i+1] are A_i*B_i."""
+    L = _lib()
+    count = len(As)
+    if count != len(Bs):
+        raise ValueError("As and Bs differ in length")
+    dev = _device_of(As[0]) if count else _torch().device("cuda")
+    al = _TorchAlloc(dev)
+    A_arr = (hs_mat * max(count, 1))(*[x.desc() for x in As])
+    B_arr = (hs_mat * max(count, 1))(*[x.desc() for x in Bs])
+    offs = (ctypes.c_int64 * (count + 1))()
+    sa, sb = hs_mat(), hs_mat()
+    st = L.hs_batch_stack(count, A_arr, B_arr, ctypes.byref(sa), ctypes.byref(sb), offs, ctypes.byref(al.struct),
+                          _stream_ptr(stream))
+    if st != 0:
+        raise HsError(st, "hs_batch_stack")
+    return _adopt_output(al, sa), _adopt_output(al, sb), np.array(offs[:], dtype=np.int64)
+
+
+class Plan:
+    """C = A*B computed once (hs_plan_create), then its values recomputed from
+    new values of A and B on the same structures (hs_plan_execute: no
+    allocation, no host synchronisation, so it can be captured in a CUDA
+    graph).  Keeps A, B and C alive while it is open."""
+
+    def __init__(self, semiring: str, A: DeviceCSR, B: DeviceCSR, validate: bool = False, stream=None):
+        L = _lib()
+        self._al = _TorchAlloc(_device_of(A))
+        self.A, self.B = A, B
+        a, b, c = A.desc(), B.desc(), hs_mat()
+        h = ctypes.c_void_p()
+        st = L.hs_plan_create(SEMIRING[semiring], ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(h),
+                              ctypes.byref(self._al.struct), _stream_ptr(stream), FLAG_VALIDATE if validate else 0)
+        if st != 0:
+            raise HsError(st, "hs_plan_create")
+        self._h = h
+        self.C = _adopt_output(self._al, c)
+
+    def execute(self, A_val=None, B_val=None, C_val=None, stream=None):
+        """Recompute C's values (into C_val, default C.val) from A_val, B_val (default: A's and B's arrays)."""
+        if self._h is None:
+            raise RuntimeError("plan is closed")
+        av = self.A.val if A_val is None else A_val
+        bv = self.B.val if B_val is None else B_val
+        cv = self.C.val if C_val is None else C_val
+        st = _lib().hs_plan_execute(self._h, None if av is None else av.data_ptr(),
+                                    None if bv is None else bv.data_ptr(), None if cv is None else cv.data_ptr(),
+                                    _stream_ptr(stream))
+        if st != 0:
+            raise HsError(st, "hs_plan_execute")
+
+    def status(self, stream=None):
+        """Raise if a device-side check failed during the executes so far (synchronises)."""
+        st = _lib().hs_plan_status(self._h, _stream_ptr(stream))
+        if st != 0:
+            raise HsError(st, "hs_plan_status")
+
+    def close(self, stream=None):
+        if self._h is not None:
+            _lib().hs_plan_destroy(self._h, _stream_ptr(stream))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def csr_rows(C: DeviceCSR, r0: int, r1: int, n: int | None = None) -> DeviceCSR:
