@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target length of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default row-bin thresholds")
     ap.add_argument("--workload", default="rmat", choices=["rmat", "batched", "serving"],
                     help="rmat: the headline product; batched: 2000 independent ER products, "
                          "one batched call against one call per problem")
@@ -234,6 +235,14 @@ def run_batched(args):
             ts.append(e0.elapsed_time(e1))
         return ts, out
 
+    tuning = None
+    if not args.no_tune:  # row-bin thresholds picked on the first 200 problems, used for the whole batch
+        from paper_1109_3739_gb300 import tune
+        sub = min(200, len(As))
+        best, log = tune.tune(lambda: h.spgemm_batched("plus_times", As[:sub], Bs[:sub], stream=stream),
+                              trials=2, stream=stream)
+        tuning = {"chosen": best, "sample_problems": sub, "default_ms": log[0][1],
+                  "tuned_ms": min(ms for _, ms in log), "settings_timed": len(log)}
     l0 = h.launch_count()
     h.profile_enable(True)
     h.profile_reset()
@@ -286,6 +295,7 @@ def run_batched(args):
                                  "what": "values of every product recomputed on the plan's structure "
                                          "(hs_plan_execute captured once in a CUDA graph)"},
         "gpu_launches": nb_launch,
+        "tuning": tuning,
         "phases_ms_per_step": phases,
     }), flush=True)
 
@@ -368,6 +378,13 @@ def main():
     def step():
         return h.spgemm("plus_times", dA, dA, stream=stream)
 
+    tuning = None
+    if not args.no_tune:  # row-bin thresholds picked by measurement on this workload
+        from paper_1109_3739_gb300 import tune
+        best, log = tune.tune(lambda: step(), trials=2, stream=stream)
+        tuning = {"chosen": best, "default_ms": log[0][1], "tuned_ms": min(ms for _, ms in log),
+                  "settings_timed": len(log)}
+
     C = None
     for _ in range(args.warmup):
         C = None
@@ -419,20 +436,26 @@ def main():
     cnt = np.diff(c_rowptr)
     deg = np.diff(A.rowptr)
     cap_large = 8192  # f32 values
+    t = h.get_tuning()  # the thresholds in force (clamped as the library clamps them)
+    ws = min(max(t["warp_s_max"], 32), 128)
+    ms_ = min(max(t["mid_s_max"], 0), 1024)
+    ls = min(max(t["large_s_max"], 2048), cap_large // 2)
+    sms = min(max(t["sym_mid_s_max"], 512), 1024)
+    shf = cap_large if t["sym_heavy_from"] <= 0 else min(max(t["sym_heavy_from"], 4096), cap_large)
     big = (f > 512) & (cnt > 0)
     in_bin = {
         "numeric_heavy": big & (cnt > cap_large),
-        "numeric_large": big & (cnt > cap_large // 2) & (cnt <= cap_large),
-        "numeric_large_s": big & (cnt > 2048) & (cnt <= cap_large // 2),
-        "numeric_mid": big & (cnt > 1024) & (cnt <= 2048),
-        "numeric_mid_s": big & (cnt <= 1024),
-        "numeric_warp": (f > 128) & (f <= 512),
-        "numeric_warp_s": (f > 32) & (f <= 128),
+        "numeric_large": big & (cnt > ls) & (cnt <= cap_large),
+        "numeric_large_s": big & (cnt > 2048) & (cnt <= ls),
+        "numeric_mid": big & (cnt > ms_) & (cnt <= 2048),
+        "numeric_mid_s": big & (cnt <= ms_),
+        "numeric_warp": (f > ws) & (f <= 512),
+        "numeric_warp_s": (f > 32) & (f <= ws),
         "numeric_tiny": (f > 0) & (f <= 32),
-        "symbolic_heavy": f > cap_large,
-        "symbolic_large": (f > 4096) & (f <= cap_large),
-        "symbolic_mid": (f > 1024) & (f <= 4096),
-        "symbolic_mid_s": (f > 512) & (f <= 1024),
+        "symbolic_heavy": f > shf,
+        "symbolic_large": (f > 4096) & (f <= shf),
+        "symbolic_mid": (f > sms) & (f <= 4096),
+        "symbolic_mid_s": (f > 512) & (f <= sms),
         "symbolic_warp": (f > 32) & (f <= 512),
         "symbolic_tiny": (f > 0) & (f <= 32),
     }[dom]
@@ -501,6 +524,7 @@ def main():
                        "step_alg_bytes": step_bytes},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
             "gpu_launches": launches,
+            "tuning": tuning,
             "phases_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         }), flush=True)
     if dist:

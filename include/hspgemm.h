@@ -153,6 +153,34 @@ int hs_spasgn(const hs_mat *A, const int32_t *I, int64_t nI, const int32_t *J, i
 int hs_spgemm_batched(int semiring, int64_t count, const hs_mat *A, const hs_mat *B, hs_mat *C,
                       int64_t *row_offsets, const hs_allocator *al, void *stream, uint32_t flags);
 
+/* Row-bin thresholds (process-wide; every later call on any thread uses
+ * them).  Rows are binned by their product count f and output count c, and
+ * each bin runs the accumulator sized for it (Sections 2.1-2.2: work follows
+ * the row, not the dimension).  The tables' capacities are fixed; these
+ * thresholds decide which rows take the smaller tiers, whose smaller tables
+ * leave room for more rows in flight per SM.  Values are clamped to what the
+ * tiers hold:
+ *   warp_s_max      numeric rows with 32 < f <= warp_s_max take 256-slot warp
+ *                   tables, the others up to f = 512 take 1024 (32..128; 128)
+ *   mid_s_max       numeric rows with f > 512 and c <= mid_s_max take the
+ *                   1024-output CTA tier, the others up to 2048 the next (0..1024; 1024)
+ *   large_s_max     numeric rows with 2048 < c <= large_s_max take the tier
+ *                   of half the large capacity (2048..4096 for 4-byte values
+ *                   and bool; that tier is empty for 8-byte values; 4096)
+ *   sym_mid_s_max   symbolic rows with 512 < f <= sym_mid_s_max take
+ *                   2048-slot tables, the others up to f = 4096 take 8192 (512..1024; 1024)
+ *   sym_heavy_from  symbolic rows with f > sym_heavy_from take the bitmap
+ *                   kernel that also writes their sorted column lists
+ *                   (4096..large capacity; 0 = the large capacity)
+ * Results do not depend on the thresholds.  hs_set_tuning(NULL) restores the
+ * defaults (given last above).  Both calls return HS_OK (hs_get_tuning:
+ * HS_EINVAL for NULL). */
+typedef struct hs_tuning {
+  int32_t warp_s_max, mid_s_max, large_s_max, sym_mid_s_max, sym_heavy_from;
+} hs_tuning;
+int hs_set_tuning(const hs_tuning *t);
+int hs_get_tuning(hs_tuning *t);
+
 /* Symbolic once, numeric many times.  In a multigrid setup the Galerkin
  * product R*A*R^T of Section 4.3.2 is recomputed whenever A's values change
  * while every structure stays the same; a batch of products can be rerun the

@@ -41,7 +41,7 @@ static int grid_for(int64_t items, int per_block, int max_per_sm) {
 // ------------------------------------------------------------------ flops
 // stats[0] += total flops, stats[1] = max row flops, stats[2] = max row nnz
 // of A, stats[3] += min(f, n) over rows of the symbolic heavy bin
-__global__ void k_flops(RowSet A, RightOp B, int64_t *f, int *key_cnt, unsigned long long *stats, int cap_large) {
+__global__ void k_flops(RowSet A, RightOp B, int64_t *f, int *key_cnt, unsigned long long *stats, BinCfg bins) {
   __shared__ int hist[NKEYS];
   __shared__ unsigned long long blk_tot, blk_max, blk_amax, blk_heavy;
   for (int i = threadIdx.x; i < NKEYS; i += blockDim.x) hist[i] = 0;
@@ -61,7 +61,7 @@ __global__ void k_flops(RowSet A, RightOp B, int64_t *f, int *key_cnt, unsigned 
     s = warp_sum(s);
     if (lane == 0) {
       f[r] = s;
-      const int key = sym_key(s, cap_large);
+      const int key = sym_key(s, bins);
       if (key) atomicAdd(hist + key, 1);
       if (key >= KEY_HEAVY) my_heavy += (unsigned long long)min((int64_t)s, B.n);
       my_tot += (unsigned long long)s;
@@ -87,10 +87,10 @@ __global__ void k_flops(RowSet A, RightOp B, int64_t *f, int *key_cnt, unsigned 
 }
 
 void launch_flops(const RowSet &A, const RightOp &B, int64_t *f, int *key_cnt, unsigned long long *stats,
-                  int cap_large, cudaStream_t st) {
+                  const BinCfg &bins, cudaStream_t st) {
   if (A.nslots == 0) return;
   count_launch();
-  k_flops<<<grid_for(A.nslots, 8, 16), 256, 0, st>>>(A, B, f, key_cnt, stats, cap_large);
+  k_flops<<<grid_for(A.nslots, 8, 16), 256, 0, st>>>(A, B, f, key_cnt, stats, bins);
 }
 
 // ---------------------------------------------------- B segment index
@@ -167,14 +167,14 @@ __device__ __forceinline__ void append_row(int key, int r, int *key_cur, int *li
 }
 
 __global__ void k_scatter_sym(RowSet A, const int64_t *f, int *key_cur, int *list, int32_t *hslot, int *nhist,
-                              int hist_threshold) {
+                              BinCfg bins) {
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < A.nslots;
        r += (int64_t)gridDim.x * blockDim.x) {
     const int64_t fr = f[r];
-    const int key = sym_key(fr, hist_threshold);
+    const int key = sym_key(fr, bins);
     if (key) append_row(key, (int)r, key_cur, list, A.nslots, A.dbg);
     // rows that may need column parts in the numeric pass get a histogram slot
-    const bool h = fr > hist_threshold;
+    const bool h = fr > bins.cap_large;
     const unsigned act = __activemask();
     const unsigned hm = __ballot_sync(act, h);
     int base = 0;
@@ -186,10 +186,10 @@ __global__ void k_scatter_sym(RowSet A, const int64_t *f, int *key_cur, int *lis
 }
 
 void launch_scatter_sym(const RowSet &A, const int64_t *f, int *key_cur, int *list, int32_t *hslot, int *nhist,
-                        int hist_threshold, cudaStream_t st) {
+                        const BinCfg &bins, cudaStream_t st) {
   if (A.nslots == 0) return;
   count_launch();
-  k_scatter_sym<<<grid_for(A.nslots, 256, 8), 256, 0, st>>>(A, f, key_cur, list, hslot, nhist, hist_threshold);
+  k_scatter_sym<<<grid_for(A.nslots, 256, 8), 256, 0, st>>>(A, f, key_cur, list, hslot, nhist, bins);
 }
 
 __device__ __forceinline__ int64_t out_count(const RowSet &A, const int64_t *Cp, int64_t r) {
@@ -197,13 +197,13 @@ __device__ __forceinline__ int64_t out_count(const RowSet &A, const int64_t *Cp,
   return Cp[o + 1] - Cp[o];
 }
 
-__global__ void k_num_count(RowSet A, const int64_t *f, const int64_t *Cp, int cap_large, int *key_cnt) {
+__global__ void k_num_count(RowSet A, const int64_t *f, const int64_t *Cp, BinCfg bins, int *key_cnt) {
   __shared__ int hist[NKEYS];
   for (int i = threadIdx.x; i < NKEYS; i += blockDim.x) hist[i] = 0;
   __syncthreads();
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < A.nslots;
        r += (int64_t)gridDim.x * blockDim.x) {
-    const int key = num_key(f[r], out_count(A, Cp, r), cap_large);
+    const int key = num_key(f[r], out_count(A, Cp, r), bins);
     if (key) atomicAdd(hist + key, 1);
   }
   __syncthreads();
@@ -211,27 +211,27 @@ __global__ void k_num_count(RowSet A, const int64_t *f, const int64_t *Cp, int c
     if (hist[i]) atomicAdd(key_cnt + i, hist[i]);
 }
 
-void launch_num_count(const RowSet &A, const int64_t *f, const int64_t *Cp, int cap_large, int *key_cnt,
+void launch_num_count(const RowSet &A, const int64_t *f, const int64_t *Cp, const BinCfg &bins, int *key_cnt,
                       cudaStream_t st) {
   if (A.nslots == 0) return;
   count_launch();
-  k_num_count<<<grid_for(A.nslots, 256, 8), 256, 0, st>>>(A, f, Cp, cap_large, key_cnt);
+  k_num_count<<<grid_for(A.nslots, 256, 8), 256, 0, st>>>(A, f, Cp, bins, key_cnt);
 }
 
-__global__ void k_scatter_num(RowSet A, const int64_t *f, const int64_t *Cp, int cap_large, int *key_cur,
+__global__ void k_scatter_num(RowSet A, const int64_t *f, const int64_t *Cp, BinCfg bins, int *key_cur,
                               int *list) {
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < A.nslots;
        r += (int64_t)gridDim.x * blockDim.x) {
-    const int key = num_key(f[r], out_count(A, Cp, r), cap_large);
+    const int key = num_key(f[r], out_count(A, Cp, r), bins);
     if (key) append_row(key, (int)r, key_cur, list, A.nslots, A.dbg);
   }
 }
 
-void launch_scatter_num(const RowSet &A, const int64_t *f, const int64_t *Cp, int cap_large, int *key_cur,
+void launch_scatter_num(const RowSet &A, const int64_t *f, const int64_t *Cp, const BinCfg &bins, int *key_cur,
                         int *list, cudaStream_t st) {
   if (A.nslots == 0) return;
   count_launch();
-  k_scatter_num<<<grid_for(A.nslots, 256, 8), 256, 0, st>>>(A, f, Cp, cap_large, key_cur, list);
+  k_scatter_num<<<grid_for(A.nslots, 256, 8), 256, 0, st>>>(A, f, Cp, bins, key_cur, list);
 }
 
 // ------------------------------------------------------------------- scan

@@ -36,31 +36,44 @@ __host__ __device__ inline int floor_log2_u64(uint64_t x) {
 #endif
 }
 __host__ __device__ inline int heavy_key(int64_t f) { return KEY_HEAVY + (62 - floor_log2_u64((uint64_t)f)); }
+// Bin thresholds.  The tier capacities (table sizes) are fixed by the
+// kernels; which rows take which tier is set here, at run time (defaults
+// below, or a tuning chosen by measurement), within those capacities.
+struct BinCfg {
+  int cap_large;       // numeric large capacity: 8192 (4-byte values, bool) or 4096 (8-byte)
+  int warp_s_max;      // numeric: rows with 32 < f <= this take the 256-slot warp tier (32..128)
+  int mid_s_max;       // numeric: rows with c <= this take the 1024-capacity CTA tier (0..1024)
+  int large_s_max;     // numeric: rows with CAP_MID < c <= this take the half-capacity large tier
+  int sym_mid_s_max;   // symbolic: rows with 512 < f <= this take the 2048-slot tier (512..1024)
+  int sym_heavy_from;  // symbolic: rows with f > this take the bitmap kernel (4096..cap_large)
+};
 // Symbolic bins.  Every row that may end in the numeric heavy bin (c >
 // cap_large needs f > cap_large) takes the bitmap kernel, which also writes
 // the row's sorted column list for the numeric pass.
-__host__ __device__ inline int sym_key(int64_t f, int cap_large) {
+__host__ __device__ inline int sym_key(int64_t f, const BinCfg &b) {
   if (f <= 0) return 0;
   if (f <= F_TINY) return KEY_TINY;
   if (f <= F_WARP) return KEY_WARP;
-  if (f <= F_MID_S) return KEY_MID_S;
+  if (f <= b.sym_mid_s_max) return KEY_MID_S;
   if (f <= F_MID) return KEY_MID;
-  if (f <= F_LARGE && f <= cap_large) return KEY_LARGE;
+  if (f <= F_LARGE && f <= b.sym_heavy_from) return KEY_LARGE;
   return heavy_key(f);
 }
 // Numeric bins: the smaller tiers take smaller tables, so more of their rows
 // are in flight on an SM at once.
-__host__ __device__ inline int num_key(int64_t f, int64_t c, int cap_large) {
+__host__ __device__ inline int num_key(int64_t f, int64_t c, const BinCfg &b) {
   if (c <= 0) return 0;
   if (f <= F_TINY) return KEY_TINY;
-  if (f <= F_WARP_S) return KEY_WARP_S;
+  if (f <= b.warp_s_max) return KEY_WARP_S;
   if (f <= F_WARP) return KEY_WARP;
-  if (c <= CAP_MID_S) return KEY_MID_S;
+  if (c <= b.mid_s_max) return KEY_MID_S;
   if (c <= CAP_MID) return KEY_MID;
-  if (c <= cap_large / 2) return KEY_LARGE_S;
-  if (c <= cap_large) return KEY_LARGE;
+  if (c <= b.large_s_max) return KEY_LARGE_S;
+  if (c <= b.cap_large) return KEY_LARGE;
   return heavy_key(f);
 }
+// the default thresholds for a value width, clamped tuning values otherwise
+BinCfg bin_config(int value_bytes);
 
 // ---------------------------------------------------------- device views
 struct RowSet {          // the left operand's stored rows
@@ -100,15 +113,14 @@ template <class K> inline void set_smem_attr(K kernel, size_t bytes) {
 // stats[0] total flops, [1] max row flops, [2] max row nnz of A, [3] sum of
 // min(f, n) over the rows of the symbolic heavy bin (their list pool bound)
 void launch_flops(const RowSet &A, const RightOp &B, int64_t *f, int *key_cnt, unsigned long long *stats,
-                  int cap_large, cudaStream_t st);
+                  const BinCfg &bins, cudaStream_t st);
 void launch_key_offsets(const int *key_cnt, int *key_off, int *key_cur, cudaStream_t st);
-// rows with more than hist_threshold (= cap_large) products get a column-segment
-// histogram slot; the same bound ends the symbolic large bin (sym_key)
+// rows with more than cap_large products get a column-segment histogram slot
 void launch_scatter_sym(const RowSet &A, const int64_t *f, int *key_cur, int *list, int32_t *hslot,
-                        int *nhist, int hist_threshold, cudaStream_t st);
-void launch_num_count(const RowSet &A, const int64_t *f, const int64_t *Cp, int cap_large, int *key_cnt,
+                        int *nhist, const BinCfg &bins, cudaStream_t st);
+void launch_num_count(const RowSet &A, const int64_t *f, const int64_t *Cp, const BinCfg &bins, int *key_cnt,
                       cudaStream_t st);
-void launch_scatter_num(const RowSet &A, const int64_t *f, const int64_t *Cp, int cap_large, int *key_cur,
+void launch_scatter_num(const RowSet &A, const int64_t *f, const int64_t *Cp, const BinCfg &bins, int *key_cur,
                         int *list, cudaStream_t st);
 void launch_scan_i64(int64_t *a, int64_t n, int64_t *tmp, cudaStream_t st);  // exclusive, in place
 int64_t scan_tmp_elems(int64_t n);

@@ -179,12 +179,13 @@ static int spgemm_noalloc_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat 
   if (ar.over) return HS_ESCRATCH;
   static thread_local NaBlock hb;  // host copy (ordinary memory)
 
+  const BinCfg bins = bin_config(vb);
   RowSet rs{A->ptr, A->idx, A->val, A->fmt == HS_DCSR ? A->ids : nullptr, nslots, A->nnz, m, sb->dbg};
   RightOp rb{B->ptr, B->idx, B->val, n, B->m, B->nnz, sb->dbg};
   NA_CK(cudaMemsetAsync(sb, 0, sizeof(NaBlock), st));
-  launch_flops(rs, rb, f, sb->key_cnt, sb->stats, vb == 8 ? 4096 : 8192, st);
+  launch_flops(rs, rb, f, sb->key_cnt, sb->stats, bins, st);
   launch_key_offsets(sb->key_cnt, sb->key_off, sb->key_cur, st);
-  launch_scatter_sym(rs, f, sb->key_cur, list, hslot, &sb->nhist, vb == 8 ? 4096 : 8192, st);
+  launch_scatter_sym(rs, f, sb->key_cur, list, hslot, &sb->nhist, bins, st);
   if (int e = check_last()) return e;
   NA_CK(cudaMemcpyAsync(&hb, sb, sizeof(NaBlock), cudaMemcpyDeviceToHost, st));
   NA_CK(cudaStreamSynchronize(st));
@@ -219,12 +220,11 @@ static int spgemm_noalloc_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat 
   launch_sym_heavy(sa, st);
   if (int e = check_last()) return e;
 
-  const int cap_large = vb == 8 ? 4096 : 8192;
   launch_scan_i64(Cp, m + 1, scan_tmp, st);
   NA_CK(cudaMemsetAsync(sb->key_cnt, 0, sizeof(int) * NKEYS, st));
-  launch_num_count(rs, f, Cp, cap_large, sb->key_cnt, st);
+  launch_num_count(rs, f, Cp, bins, sb->key_cnt, st);
   launch_key_offsets(sb->key_cnt, sb->key_off, sb->key_cur, st);
-  launch_scatter_num(rs, f, Cp, cap_large, sb->key_cur, list, st);
+  launch_scatter_num(rs, f, Cp, bins, sb->key_cur, list, st);
   NA_CK(cudaMemcpyAsync(&sb->nnz, Cp + m, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
   if (int e = check_last()) return e;
   NA_CK(cudaMemcpyAsync(&hb, sb, sizeof(NaBlock), cudaMemcpyDeviceToHost, st));

@@ -215,9 +215,9 @@ struct SmallBlock {  // device counters, read back in one copy
 
 static int phase_check(const char *phase, cudaStream_t st, const long long *dbg_dev) {
   if (int e = check_launch()) {
-    char tmp[256];
-    snprintf(tmp, sizeof(tmp), "%s: %s", phase, t_detail);
-    snprintf(t_detail, sizeof(t_detail), "%s", tmp);
+    char tmp[sizeof(t_detail) + 64];
+    snprintf(tmp, sizeof(tmp), "%.48s: %s", phase, t_detail);
+    snprintf(t_detail, sizeof(t_detail), "%.*s", (int)sizeof(t_detail) - 1, tmp);
     return e;
   }
   if (!debug_sync()) return HS_OK;
@@ -260,7 +260,29 @@ static bool numeric_supported(int sr, int adt, int bdt, int &out_dt) {
   return false;
 }
 
-static int cap_large_of(int out_dt) { return vbytes_of(out_dt) == 8 ? 4096 : 8192; }
+
+
+// ----------------------------------------------------------------- tuning
+static std::mutex g_tune_mu;
+static hs_tuning g_tune = {F_WARP_S, CAP_MID_S, 4096, F_MID_S, 0};
+
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+BinCfg bin_config(int value_bytes) {
+  hs_tuning t;
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    t = g_tune;
+  }
+  BinCfg b;
+  b.cap_large = value_bytes == 8 ? 4096 : 8192;
+  b.warp_s_max = clampi(t.warp_s_max, F_TINY, F_WARP_S);
+  b.mid_s_max = clampi(t.mid_s_max, 0, CAP_MID_S);
+  b.large_s_max = clampi(t.large_s_max, CAP_MID, b.cap_large / 2 > CAP_MID ? b.cap_large / 2 : CAP_MID);
+  b.sym_mid_s_max = clampi(t.sym_mid_s_max, F_WARP, F_MID_S);
+  b.sym_heavy_from = t.sym_heavy_from <= 0 ? b.cap_large : clampi(t.sym_heavy_from, F_MID, b.cap_large);
+  return b;
+}
 
 static bool launch_num(int sr, int out_dt, int kind, const NumArgs &a, cudaStream_t st) {
   switch (sr) {
@@ -338,6 +360,7 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
     return check_launch();
   }
 
+  const BinCfg bins = bin_config(vb);
   int64_t *f = mem.tmp<int64_t>(nslots);
   int *list = mem.tmp<int>(nslots);
   int32_t *hslot = mem.tmp<int32_t>(nslots);
@@ -355,9 +378,9 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
       launch_validate(A->ptr, A->idx, nslots, A->n, &sb->valflag, st);
       launch_validate(B->ptr, B->idx, B->m, B->n, &sb->valflag, st);
     }
-    launch_flops(rs, rb, f, sb->key_cnt, sb->stats, cap_large_of(out_dt), st);
+    launch_flops(rs, rb, f, sb->key_cnt, sb->stats, bins, st);
     launch_key_offsets(sb->key_cnt, sb->key_off, sb->key_cur, st);
-    launch_scatter_sym(rs, f, sb->key_cur, list, hslot, &sb->nhist, cap_large_of(out_dt), st);
+    launch_scatter_sym(rs, f, sb->key_cur, list, hslot, &sb->nhist, bins, st);
   }
   if (int e = phase_check("analysis", st, sb->dbg)) return e;
   CK(cudaMemcpyAsync(hb, sb, sizeof(SmallBlock), cudaMemcpyDeviceToHost, st));
@@ -437,16 +460,15 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
   }
 
   // ---- offsets and numeric bins
-  const int cap_large = cap_large_of(out_dt);
   int64_t *scan_tmp = mem.tmp<int64_t>(scan_tmp_elems(m + 1));
   if (!scan_tmp) return HS_ENOMEM;
   {
     PhaseTimer t("scan_bin", st);
     launch_scan_i64(Cp, m + 1, scan_tmp, st);
     CK(cudaMemsetAsync(sb->key_cnt, 0, sizeof(int) * NKEYS, st));
-    launch_num_count(rs, f, Cp, cap_large, sb->key_cnt, st);
+    launch_num_count(rs, f, Cp, bins, sb->key_cnt, st);
     launch_key_offsets(sb->key_cnt, sb->key_off, sb->key_cur, st);
-    launch_scatter_num(rs, f, Cp, cap_large, sb->key_cur, list, st);
+    launch_scatter_num(rs, f, Cp, bins, sb->key_cur, list, st);
     CK(cudaMemcpyAsync(&sb->nnz, Cp + m, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
   }
   if (int e = phase_check("scan_bin", st, sb->dbg)) return e;
@@ -812,6 +834,19 @@ int hs_spasgn(const hs_mat *A, const int32_t *I, int64_t nI, const int32_t *J, i
   return with_output(C, out, [&] {
     return spasgn_impl(A, I, nI, J, nJ, B, accumulate, add_semiring, C, mem, out, flags);
   });
+}
+
+int hs_set_tuning(const hs_tuning *t) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tune = t ? *t : hs_tuning{F_WARP_S, CAP_MID_S, 4096, F_MID_S, 0};
+  return HS_OK;
+}
+
+int hs_get_tuning(hs_tuning *t) {
+  if (!t) return HS_EINVAL;
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  *t = g_tune;
+  return HS_OK;
 }
 
 void hs_mat_free(hs_mat *M, const hs_allocator *al, void *stream) {

@@ -46,6 +46,14 @@ ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, c
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
 
+class hs_tuning(ctypes.Structure):
+    _fields_ = [("warp_s_max", ctypes.c_int32), ("mid_s_max", ctypes.c_int32), ("large_s_max", ctypes.c_int32),
+                ("sym_mid_s_max", ctypes.c_int32), ("sym_heavy_from", ctypes.c_int32)]
+
+
+TUNING_FIELDS = tuple(name for name, _ in hs_tuning._fields_)
+
+
 class hs_allocator(ctypes.Structure):
     _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", ctypes.c_void_p)]
 
@@ -92,6 +100,10 @@ def _lib():
             L.hs_batch_stack.argtypes = [i64, P(hs_mat), P(hs_mat), P(hs_mat), P(hs_mat), P(ctypes.c_int64),
                                          P(hs_allocator), vp]
             L.hs_batch_stack.restype = ci
+            L.hs_set_tuning.argtypes = [P(hs_tuning)]
+            L.hs_set_tuning.restype = ci
+            L.hs_get_tuning.argtypes = [P(hs_tuning)]
+            L.hs_get_tuning.restype = ci
             L.hs_mat_free.argtypes = [P(hs_mat), P(hs_allocator), vp]
             L.hs_mat_free.restype = None
             L.hs_strerror.argtypes = [ci]
@@ -409,6 +421,25 @@ def spasgn(A: DeviceCSR, I, J, B: DeviceCSR, accumulate: bool = False, add: str 
 
 
 # --------------------------------------------------------------- profiling
+def set_tuning(tuning: dict | None = None):
+    """Row-bin thresholds (hs_set_tuning); None restores the defaults.  Keys
+    not given keep their current values."""
+    L = _lib()
+    if tuning is None:
+        L.hs_set_tuning(None)
+        return
+    cur = get_tuning()
+    cur.update(tuning)
+    t = hs_tuning(*[int(cur[k]) for k in TUNING_FIELDS])
+    L.hs_set_tuning(ctypes.byref(t))
+
+
+def get_tuning() -> dict:
+    t = hs_tuning()
+    _lib().hs_get_tuning(ctypes.byref(t))
+    return {k: int(getattr(t, k)) for k in TUNING_FIELDS}
+
+
 def profile_enable(on: bool = True):
     _lib().hs_profile_enable(1 if on else 0)
 

@@ -47,3 +47,16 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(H, "_L", None)
     with pytest.raises(RuntimeError):
         H.library()
+
+
+def test_tuning_round_trip_without_gpu():
+    from paper_1109_3739_gb300 import hspgemm as H
+    H.set_tuning(None)
+    d = H.get_tuning()
+    assert d == {"warp_s_max": 128, "mid_s_max": 1024, "large_s_max": 4096, "sym_mid_s_max": 1024,
+                 "sym_heavy_from": 0}
+    H.set_tuning({"mid_s_max": 512, "sym_heavy_from": 6144})
+    d2 = H.get_tuning()
+    assert d2["mid_s_max"] == 512 and d2["sym_heavy_from"] == 6144 and d2["warp_s_max"] == 128
+    H.set_tuning(None)
+    assert H.get_tuning() == d
