@@ -398,20 +398,25 @@ template <typename T, int CH> struct CtaExpandSmem {
 // the warps of the CTA: each warp takes one contiguous range of the products
 // and deals it one product per lane (warp_expand).  Reads the staged arrays
 // only; all threads of the CTA must call it together.
-template <class SR, int U = 2, class Visit>
+// Each segment may also be charged K units of fixed cost (its setup in the
+// warp loop): warps then split the cost, not just the products, so a warp
+// whose range holds many short segments gets fewer products.
+template <class SR, int U = 2, int K = 0, class Visit>
 __device__ __forceinline__ void cta_expand_staged(const DevCsr &B, const int64_t *sbeg, const int *excl,
                                                   const typename SR::val_t *aval, int n, int total,
                                                   Visit &visit) {
   using T = typename SR::val_t;
   const int lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int pb = (int)(((int64_t)total * warp) / nw);
-  const int pe = (int)(((int64_t)total * (warp + 1)) / nw);
+  // entry e occupies [X_e, X_e+1) with X_e = excl[e] + K*e: K units of its
+  // fixed cost, then its products
+  const int64_t tcost = (int64_t)total + (int64_t)K * n;
+  const int64_t pb = tcost * warp / nw, pe = tcost * (warp + 1) / nw;
   if (pb >= pe) return;
-  // last entry whose exclusive start is <= pb
+  // last entry whose start is <= pb (entry 0 starts at 0, so l >= 1)
   int l = 0, h = n;
   while (l < h) {
     const int mid = (l + h) >> 1;
-    if (excl[mid] <= pb) l = mid + 1;
+    if (excl[mid] + (int64_t)K * mid <= pb) l = mid + 1;
     else h = mid;
   }
   for (int eb = l - 1; eb < n; eb += 32) {
@@ -420,16 +425,16 @@ __device__ __forceinline__ void cta_expand_staged(const DevCsr &B, const int64_t
     int len = 0;
     T a{};
     if (e < n) {
-      const int x0 = excl[e], x1 = excl[e + 1];
-      const int cb = max(x0, pb), ce = min(x1, pe);
+      const int64_t x0 = excl[e] + (int64_t)K * e + K, x1 = excl[e + 1] + (int64_t)K * (e + 1);
+      const int64_t cb = max(x0, pb), ce = min(x1, pe);
       if (ce > cb) {
-        len = ce - cb;
+        len = (int)(ce - cb);
         s = sbeg[e] + (cb - x0);
         if constexpr (SR::needs_a) a = aval[e];
       }
     }
     warp_expand<SR, U>(B, s, len, a, visit);
-    if (eb + 32 >= n || excl[eb + 32] >= pe) break;
+    if (eb + 32 >= n || excl[eb + 32] + (int64_t)K * (eb + 32) >= pe) break;
   }
 }
 

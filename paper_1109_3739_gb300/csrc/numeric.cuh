@@ -412,123 +412,165 @@ __global__ void __launch_bounds__(HV_NT, 2) k_num_heavy(NumArgs a) {
             }
           }
         }
-        // ---- B segments of the part (and, without a list, pass 1)
-        int total = 0;
-        for (int rd = 0; rd < nrounds; ++rd) {
-          const int64_t rq0 = q0 + (int64_t)rd * HV_CH;
-          const int cnt = (int)min((int64_t)HV_CH, q1 - rq0);
-          __syncthreads();
-          for (int e = tid; e < cnt; e += HV_NT) {
-            int64_t s = 0;
-            int len = 0;
-            if (cached) {
-              const int64_t base = sm.ebase[e];
-              const int cur = sm.ecur[e], t = sm.et[e], rl = sm.elen[e];
-              int eo = t >= 0 ? __ldg(a.bci + (int64_t)t * bstride + pe)
-                              : (int)(interp_lower_bound(B.j, base + cur, base + rl, hi) - base);
-              if (!HS_G(dbg, eo >= cur && eo <= rl, 65, eo)) eo = cur;
-              s = base + cur;
-              len = eo - cur;
-              sm.ecur[e] = eo;
-            } else {
-              const int64_t q = rq0 + e;
-              const int k = __ldg(A.j + q);
-              if (HS_G(dbg, k >= 0 && k < B.rows, 2, k)) {
-                const int64_t base = __ldg(B.p + k), end = __ldg(B.p + k + 1);
-                const int t = a.bci_id ? __ldg(a.bci_id + k) : -1;
-                s = base + gcur[q];
-                int64_t se = t >= 0 ? base + __ldg(a.bci + (int64_t)t * bstride + pe)
-                                    : interp_lower_bound(B.j, s, end, hi);
-                if (!HS_G(dbg, se >= s && se <= end, 65, se)) se = s;
-                len = (int)(se - s);
-                gend[q] = (int32_t)(se - base);
+        // segment [s, s + len) of cached entry e in this part; advances its cursor
+        auto seg_end = [&](int e, int64_t &s) -> int {
+          const int64_t base = sm.ebase[e];
+          const int cur = sm.ecur[e], t = sm.et[e], rl = sm.elen[e];
+          int eo = t >= 0 ? __ldg(a.bci + (int64_t)t * bstride + pe)
+                          : (int)(interp_lower_bound(B.j, base + cur, base + rl, hi) - base);
+          if (!HS_G(dbg, eo >= cur && eo <= rl, 65, eo)) eo = cur;
+          s = base + cur;
+          sm.ecur[e] = eo;
+          return eo - cur;
+        };
+        bool consistent = true;
+        if (cached && Lp) {
+          // nearly every heavy row: its entries are cached and its columns
+          // listed, so the segment ends, the value reset and the list's bitmap
+          // share one phase; rows of at most 32 entries scan in one warp
+          const int cnt = (int)(q1 - q0);
+          if constexpr (SR::has_val)
+            for (int i = tid; i < pc; i += HV_NT) sm.vals[i] = SR::identity();
+          if (cnt <= 32) {
+            if (warp == 0) {
+              int64_t s = 0;
+              const int len = lane < cnt ? seg_end(lane, s) : 0;
+              const int incl = warp_incl_scan(len);
+              if (lane < cnt) {
+                sm.excl[lane] = incl - len;
+                sm.sbeg[lane] = s;
               }
+              if (lane == 31) sm.excl[cnt] = incl;
             }
-            sm.excl[e] = len;
-            sm.sbeg[e] = s;
+            __syncthreads();
+          } else {
+            for (int e = tid; e < cnt; e += HV_NT) {
+              int64_t s = 0;
+              sm.excl[e] = seg_end(e, s);
+              sm.sbeg[e] = s;
+            }
+            __syncthreads();
+            const int t = group_excl_scan<CtaGroup>(sm.excl, cnt, sm.wtmp);
+            if (tid == 0) sm.excl[cnt] = t;
+            __syncthreads();
           }
-          if (!cached && Lp) continue;  // only the part ends are needed (pass 2 restages)
-          __syncthreads();
-          total = group_excl_scan<CtaGroup>(sm.excl, cnt, sm.wtmp);
-          if (tid == 0) sm.excl[cnt] = total;
-          __syncthreads();
-          if (!Lp) {
-            auto set_bit = [&](int col, NoVal, int) {
-              const int x = col - lo;
-              if (HS_G(dbg, x >= 0 && x < hi - lo, 60, col)) atomicOr(sm.bitmap + (x >> 5), 1u << (x & 31));
-            };
-            cta_expand_staged<StructOf<SR>>(B, sm.sbeg, sm.excl, reinterpret_cast<const NoVal *>(sm.aval), cnt,
-                                            total, set_bit);
-          }
-        }
-        __syncthreads();
-        if (!Lp) {
-          // ---- rank: prefix of set bits per word, in runs of 32 words per warp
-          const int wpw = ((words + nw - 1) / nw + 31) & ~31;
-          const int w0 = warp * wpw, w1 = min(words, w0 + wpw);
-          int carry = 0;
-          for (int wb = w0; wb < w1; wb += 32) {
-            const int w = wb + lane;
-            const int pc_w = w < w1 ? __popc(sm.bitmap[w]) : 0;
-            const int incl = warp_incl_scan(pc_w);
-            if (w < w1) sm.wpre[w] = (uint16_t)(carry + incl - pc_w);
-            carry += __shfl_sync(FULL, incl, 31);
-          }
-          if (lane == 0) sm.wtot[warp] = carry;
-          __syncthreads();
-          if (warp == 0) {
-            const int t = lane < nw ? sm.wtot[lane] : 0;
-            const int ti = warp_incl_scan(t);
-            if (lane < nw) sm.wtot[lane] = ti - t;
-            if (lane == nw - 1) sm.total = ti;
+          if constexpr (SR::has_val) {
+            HeavyAdd<SR> add_val{sm.bitmap, sm.wpre, sm.vals, lo, (unsigned)(hi - lo), pc, a.err, dbg};
+            cta_expand_staged<SR, 4, 32>(B, sm.sbeg, sm.excl, sm.aval, cnt, sm.excl[cnt], add_val);
           }
           __syncthreads();
-          const int add = sm.wtot[warp];
-          for (int w = w0 + lane; w < w1; w += 32) sm.wpre[w] = (uint16_t)(sm.wpre[w] + add);
-        } else if (tid == 0) {
-          sm.total = pc;
-        }
-        if constexpr (SR::has_val)
-          for (int i = tid; i < pc; i += HV_NT) sm.vals[i] = SR::identity();
-        __syncthreads();
-        const bool consistent = sm.total == pc;
-        if (!consistent && tid == 0) atomicExch(a.err, 9);
-        // ---- pass 2: values at their rank
-        if constexpr (SR::has_val) {
-          HeavyAdd<SR> add_val{sm.bitmap, sm.wpre, sm.vals, lo, (unsigned)(hi - lo), pc, a.err, dbg};
-          if (!cached) {
-            for (int rd = 0; rd < nrounds; ++rd) {
-              const int64_t rq0 = q0 + (int64_t)rd * HV_CH;
-              const int cnt = (int)min((int64_t)HV_CH, q1 - rq0);
-              __syncthreads();
-              for (int e = tid; e < cnt; e += HV_NT) {
-                int64_t s = 0;
-                int len = 0;
+        } else {
+          // ---- B segments of the part (and, without a list, pass 1)
+          int total = 0;
+          for (int rd = 0; rd < nrounds; ++rd) {
+            const int64_t rq0 = q0 + (int64_t)rd * HV_CH;
+            const int cnt = (int)min((int64_t)HV_CH, q1 - rq0);
+            __syncthreads();
+            for (int e = tid; e < cnt; e += HV_NT) {
+              int64_t s = 0;
+              int len = 0;
+              if (cached) {
+                len = seg_end(e, s);
+              } else {
                 const int64_t q = rq0 + e;
                 const int k = __ldg(A.j + q);
                 if (HS_G(dbg, k >= 0 && k < B.rows, 2, k)) {
-                  const int64_t base = __ldg(B.p + k);
+                  const int64_t base = __ldg(B.p + k), end = __ldg(B.p + k + 1);
+                  const int t = a.bci_id ? __ldg(a.bci_id + k) : -1;
                   s = base + gcur[q];
-                  len = gend[q] - gcur[q];
-                  gcur[q] = gend[q];
-                  if constexpr (SR::needs_a) sm.aval[e] = load_val<T>(A.v, q);
+                  int64_t se = t >= 0 ? base + __ldg(a.bci + (int64_t)t * bstride + pe)
+                                      : interp_lower_bound(B.j, s, end, hi);
+                  if (!HS_G(dbg, se >= s && se <= end, 65, se)) se = s;
+                  len = (int)(se - s);
+                  gend[q] = (int32_t)(se - base);
                 }
-                sm.excl[e] = len;
-                sm.sbeg[e] = s;
               }
-              __syncthreads();
-              total = group_excl_scan<CtaGroup>(sm.excl, cnt, sm.wtmp);
-              if (tid == 0) sm.excl[cnt] = total;
-              __syncthreads();
-              cta_expand_staged<SR, 4>(B, sm.sbeg, sm.excl, sm.aval, cnt, total, add_val);
+              sm.excl[e] = len;
+              sm.sbeg[e] = s;
             }
-          } else {
-            cta_expand_staged<SR, 4>(B, sm.sbeg, sm.excl, sm.aval, (int)(q1 - q0), total, add_val);
+            if (!cached && Lp) continue;  // only the part ends are needed (pass 2 restages)
+            __syncthreads();
+            total = group_excl_scan<CtaGroup>(sm.excl, cnt, sm.wtmp);
+            if (tid == 0) sm.excl[cnt] = total;
+            __syncthreads();
+            if (!Lp) {
+              auto set_bit = [&](int col, NoVal, int) {
+                const int x = col - lo;
+                if (HS_G(dbg, x >= 0 && x < hi - lo, 60, col)) atomicOr(sm.bitmap + (x >> 5), 1u << (x & 31));
+              };
+              cta_expand_staged<StructOf<SR>>(B, sm.sbeg, sm.excl, reinterpret_cast<const NoVal *>(sm.aval), cnt,
+                                              total, set_bit);
+            }
           }
           __syncthreads();
-        } else if (!cached) {
-          // structure only: still advance the cursors past this part
-          for (int64_t q = q0 + tid; q < q1; q += HV_NT) gcur[q] = gend[q];
+          if (!Lp) {
+            // ---- rank: prefix of set bits per word, in runs of 32 words per warp
+            const int wpw = ((words + nw - 1) / nw + 31) & ~31;
+            const int w0 = warp * wpw, w1 = min(words, w0 + wpw);
+            int carry = 0;
+            for (int wb = w0; wb < w1; wb += 32) {
+              const int w = wb + lane;
+              const int pc_w = w < w1 ? __popc(sm.bitmap[w]) : 0;
+              const int incl = warp_incl_scan(pc_w);
+              if (w < w1) sm.wpre[w] = (uint16_t)(carry + incl - pc_w);
+              carry += __shfl_sync(FULL, incl, 31);
+            }
+            if (lane == 0) sm.wtot[warp] = carry;
+            __syncthreads();
+            if (warp == 0) {
+              const int t = lane < nw ? sm.wtot[lane] : 0;
+              const int ti = warp_incl_scan(t);
+              if (lane < nw) sm.wtot[lane] = ti - t;
+              if (lane == nw - 1) sm.total = ti;
+            }
+            __syncthreads();
+            const int add = sm.wtot[warp];
+            for (int w = w0 + lane; w < w1; w += 32) sm.wpre[w] = (uint16_t)(sm.wpre[w] + add);
+          } else if (tid == 0) {
+            sm.total = pc;
+          }
+          if constexpr (SR::has_val)
+            for (int i = tid; i < pc; i += HV_NT) sm.vals[i] = SR::identity();
+          __syncthreads();
+          consistent = sm.total == pc;
+          if (!consistent && tid == 0) atomicExch(a.err, 9);
+          // ---- pass 2: values at their rank
+          if constexpr (SR::has_val) {
+            HeavyAdd<SR> add_val{sm.bitmap, sm.wpre, sm.vals, lo, (unsigned)(hi - lo), pc, a.err, dbg};
+            if (!cached) {
+              for (int rd = 0; rd < nrounds; ++rd) {
+                const int64_t rq0 = q0 + (int64_t)rd * HV_CH;
+                const int cnt = (int)min((int64_t)HV_CH, q1 - rq0);
+                __syncthreads();
+                for (int e = tid; e < cnt; e += HV_NT) {
+                  int64_t s = 0;
+                  int len = 0;
+                  const int64_t q = rq0 + e;
+                  const int k = __ldg(A.j + q);
+                  if (HS_G(dbg, k >= 0 && k < B.rows, 2, k)) {
+                    const int64_t base = __ldg(B.p + k);
+                    s = base + gcur[q];
+                    len = gend[q] - gcur[q];
+                    gcur[q] = gend[q];
+                    if constexpr (SR::needs_a) sm.aval[e] = load_val<T>(A.v, q);
+                  }
+                  sm.excl[e] = len;
+                  sm.sbeg[e] = s;
+                }
+                __syncthreads();
+                total = group_excl_scan<CtaGroup>(sm.excl, cnt, sm.wtmp);
+                if (tid == 0) sm.excl[cnt] = total;
+                __syncthreads();
+                cta_expand_staged<SR, 4, 32>(B, sm.sbeg, sm.excl, sm.aval, cnt, total, add_val);
+              }
+            } else {
+              cta_expand_staged<SR, 4, 32>(B, sm.sbeg, sm.excl, sm.aval, (int)(q1 - q0), total, add_val);
+            }
+            __syncthreads();
+          } else if (!cached) {
+            // structure only: still advance the cursors past this part
+            for (int64_t q = q0 + tid; q < q1; q += HV_NT) gcur[q] = gend[q];
+          }
         }
         // ---- emit (columns ascending, values in rank order), then clear the bitmap
         const int64_t out = cb + done;
