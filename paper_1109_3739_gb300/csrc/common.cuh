@@ -522,7 +522,7 @@ __device__ __forceinline__ void cta_products(const DevCsr &A, const DevCsr &B, i
     const int total = group_excl_scan<CtaGroup>(sm.excl, n, wtmp);
     if (tid == 0) sm.excl[n] = total;
     __syncthreads();
-    cta_expand_staged<SR, U>(B, sm.sbeg, sm.excl, sm.aval, n, total, visit);
+    cta_expand_staged<SR, U, 32>(B, sm.sbeg, sm.excl, sm.aval, n, total, visit);
     __syncthreads();
   }
 }

@@ -249,7 +249,8 @@ template <typename T> struct HeavySmem {
   T aval[HV_CH];
   T vals[heavy_cap<T>()];
   int wtmp[33];
-  int row, part_end, part_cnt, total;
+  int row, total;
+  int part_end2[2], part_cnt2[2];   // this part's and the next part's plan
   int pre[SEG_SMEM + 1];            // exclusive prefix of the row's segment counts
 };
 
@@ -354,37 +355,42 @@ __global__ void __launch_bounds__(HV_NT, 2) k_num_heavy(NumArgs a) {
       const int tot = group_excl_scan<CtaGroup>(sm.pre, nseg, sm.wtmp);
       if (tid == 0) sm.pre[nseg] = tot;
     }
-    int64_t done = 0;
-    int seg = 0;
-    while (seg < nseg && h >= 0) {
-      if (tid == 0) {
-        const int emax = min(nseg, seg + HV_WMAX / SEG_W);
-        int e = seg, sum = 0;
-        if (plan) {
-          // the last end in (seg, emax] whose part holds at most CAPH outputs
-          const int base = sm.pre[seg];
-          int lo_e = seg + 1, hi_e = emax;
-          while (lo_e < hi_e) {
-            const int mid = (lo_e + hi_e + 1) >> 1;
-            if (sm.pre[mid] - base <= CAPH) lo_e = mid;
-            else hi_e = mid - 1;
-          }
-          e = lo_e;
-          sum = sm.pre[e] - base;
-          if (sum > CAPH) e = seg;  // cannot happen: a segment holds at most SEG_W <= CAPH outputs
-        } else {
-          while (e < emax && sum + (int)hist[e] <= CAPH) sum += (int)hist[e++];
+    // part planning (thread 0): the part starting at segment sg ends at the
+    // last segment end in (sg, sg + HV_WMAX/SEG_W] that keeps at most CAPH
+    // outputs; the next part is planned during the current one into the
+    // other of two slots, so parts need no barrier of their own
+    auto plan_part = [&](int sg, int slot) {
+      const int emax = min(nseg, sg + HV_WMAX / SEG_W);
+      int e = sg, sum = 0;
+      if (plan) {
+        const int base = sm.pre[sg];
+        int lo_e = sg + 1, hi_e = emax;
+        while (lo_e < hi_e) {
+          const int mid = (lo_e + hi_e + 1) >> 1;
+          if (sm.pre[mid] - base <= CAPH) lo_e = mid;
+          else hi_e = mid - 1;
         }
-        if (e == seg) {
-          atomicExch(a.err, 5);
-          e = nseg;
-          sum = 0;
-        }
-        sm.part_end = e;
-        sm.part_cnt = sum;
+        e = lo_e;
+        sum = sm.pre[e] - base;
+        if (sum > CAPH) e = sg;  // cannot happen: a segment holds at most SEG_W <= CAPH outputs
+      } else {
+        while (e < emax && sum + (int)hist[e] <= CAPH) sum += (int)hist[e++];
       }
-      __syncthreads();  // also orders the row set-up before the first part's reads
-      const int pe = sm.part_end, pc = sm.part_cnt;
+      if (e == sg) {
+        atomicExch(a.err, 5);
+        e = nseg;
+        sum = 0;
+      }
+      sm.part_end2[slot] = e;
+      sm.part_cnt2[slot] = sum;
+    };
+    int64_t done = 0;
+    int seg = 0, slot = 0;
+    if (tid == 0 && h >= 0 && nseg > 0) plan_part(0, 0);
+    __syncthreads();  // also orders the row set-up before the first part's reads
+    while (seg < nseg && h >= 0) {
+      const int pe = sm.part_end2[slot], pc = sm.part_cnt2[slot];
+      if (tid == 0 && pe < nseg) plan_part(pe, slot ^ 1);
       if (pc > 0) {
         const int lo = seg * SEG_W;
         const int hi = (int)min((int64_t)pe * SEG_W, n);
@@ -610,6 +616,7 @@ __global__ void __launch_bounds__(HV_NT, 2) k_num_heavy(NumArgs a) {
         done += pc;
       }
       seg = pe;
+      slot ^= 1;
       __syncthreads();
     }
     if (tid == 0 && r_ok && done != c) atomicExch(a.err, 6);
