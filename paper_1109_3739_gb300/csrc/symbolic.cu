@@ -174,7 +174,7 @@ struct SymHeavySmem {
   long long loff;        // the row's list in the pool, or -1
   int scnt[SH_SEGS + 1];  // new columns per segment of the chunk, then their exclusive scan
   int wbuf[32][SH_BUF];
-  unsigned bitmap[BITMAP_COLS / 32];
+  alignas(16) unsigned bitmap[BITMAP_COLS / 32];
 };
 
 __global__ void __launch_bounds__(1024, 1) k_sym_heavy(SymArgs a) {
@@ -230,38 +230,44 @@ __global__ void __launch_bounds__(1024, 1) k_sym_heavy(SymArgs a) {
       if (lst) {
         for (int g = warp; g < nsc; g += nw) {
           const int wb = g * (SEG_W / 32) + 4 * lane;
-          unsigned b[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) b[u] = wb + u < words ? sm.bitmap[wb + u] : 0u;
-          const int pcl = __popc(b[0]) + __popc(b[1]) + __popc(b[2]) + __popc(b[3]);
+          // the lane's four words (128 columns) in one 16-byte load
+          uint4 v = make_uint4(0u, 0u, 0u, 0u);
+          if (wb + 3 < words) v = *reinterpret_cast<const uint4 *>(sm.bitmap + wb);
+          else if (wb < words) {
+            v.x = sm.bitmap[wb];
+            if (wb + 1 < words) v.y = sm.bitmap[wb + 1];
+            if (wb + 2 < words) v.z = sm.bitmap[wb + 2];
+          }
+          unsigned long long b0 = ((unsigned long long)v.y << 32) | v.x;
+          unsigned long long b1 = ((unsigned long long)v.w << 32) | v.z;
+          const int pcl = __popcll(b0) + __popcll(b1);
           const int incl = warp_incl_scan(pcl);
           const int tot = __shfl_sync(FULL, incl, 31);
           const int64_t at0 = written + sm.scnt[g];
           if (!HS_G(a.A.dbg, at0 + tot <= lmax, 34, at0 + tot)) continue;
+          const int cbase = lo + (wb << 5);
           if (tot <= SH_BUF) {
             int p = incl - pcl;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              unsigned bits = b[u];
-              const int cbase = lo + ((wb + u) << 5);
-              while (bits) {
-                buf[p++] = cbase + __ffs(bits) - 1;
-                bits &= bits - 1;
-              }
+            while (b0) {
+              buf[p++] = cbase + __ffsll(b0) - 1;
+              b0 &= b0 - 1;
+            }
+            while (b1) {
+              buf[p++] = cbase + 64 + __ffsll(b1) - 1;
+              b1 &= b1 - 1;
             }
             __syncwarp();
             for (int i = lane; i < tot; i += 32) lst[at0 + i] = buf[i];
             __syncwarp();
           } else {  // a dense segment: each lane's columns are one long run
             int64_t at = at0 + incl - pcl;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              unsigned bits = b[u];
-              const int cbase = lo + ((wb + u) << 5);
-              while (bits) {
-                lst[at++] = cbase + __ffs(bits) - 1;
-                bits &= bits - 1;
-              }
+            while (b0) {
+              lst[at++] = cbase + __ffsll(b0) - 1;
+              b0 &= b0 - 1;
+            }
+            while (b1) {
+              lst[at++] = cbase + 64 + __ffsll(b1) - 1;
+              b1 &= b1 - 1;
             }
           }
         }
