@@ -153,6 +153,26 @@ int hs_spasgn(const hs_mat *A, const int32_t *I, int64_t nI, const int32_t *J, i
 int hs_spgemm_batched(int semiring, int64_t count, const hs_mat *A, const hs_mat *B, hs_mat *C,
                       int64_t *row_offsets, const hs_allocator *al, void *stream, uint32_t flags);
 
+/* C = A*B delivered to host memory, with the copies overlapped: A's rows are
+ * cut into nblocks consecutive blocks; each block's product is computed on
+ * `stream` while the previous block's rows travel to the host on a stream of
+ * the call's own.  A must be CSR.  h_ptr (A->m + 1 int64), h_idx (capacity
+ * int32) and h_val (capacity values of C's dtype; unused for bool) are host
+ * arrays, best page-locked (cudaHostAlloc) for full copy bandwidth.  On
+ * success they hold C in CSR (offsets from 0) and *nnz_out = nnz(C).  If
+ * nnz(C) > capacity the call returns HS_ECAPACITY with *nnz_out the size
+ * needed (blocks that fit were copied; call again with larger arrays).
+ * Temporaries come from a memory pool of the library's own on the current
+ * device, which keeps its memory for later calls until hs_trim_memory().
+ * Same semirings, dtypes, results and errors as hs_spgemm; the call returns
+ * when everything is on the host. */
+int hs_spgemm_to_host(int semiring, const hs_mat *A, const hs_mat *B, int64_t nblocks, int64_t *h_ptr,
+                      int32_t *h_idx, void *h_val, int64_t capacity, int64_t *nnz_out, void *stream,
+                      uint32_t flags);
+/* Waits for the current device and returns the memory the library's own pool
+ * keeps (see hs_spgemm_to_host) to the system.  HS_OK or HS_ECUDA. */
+int hs_trim_memory(void);
+
 /* Row-bin thresholds (process-wide; every later call on any thread uses
  * them).  Rows are binned by their product count f and output count c, and
  * each bin runs the accumulator sized for it (Sections 2.1-2.2: work follows

@@ -146,6 +146,20 @@ void launch_fill_from_pos(const int32_t *pos, int64_t m, const int64_t *ptr, int
     k_fill_from_pos<<<grid1(m), 256, 0, st>>>(pos, m, ptr, out);
   }
 }
+__global__ void k_add_i64(int64_t *p, int64_t n, int64_t add) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] += add;
+}
+
+void launch_add_i64(int64_t *p, int64_t n, int64_t add, cudaStream_t st) {
+  if (n <= 0) return;
+  int64_t g = (n + 255) / 256;
+  const int64_t cap = (int64_t)sm_count() * 8;
+  if (g > cap) g = cap;
+  count_launch();
+  k_add_i64<<<(int)g, 256, 0, st>>>(p, n, add);
+}
+
 void launch_iota_i64(int64_t *p, int64_t n, cudaStream_t st) {
   if (n > 0) {
     count_launch();

@@ -202,6 +202,7 @@ void launch_fill_i32(int32_t *a, int64_t n, int32_t v, cudaStream_t st);
 void launch_rows_from_pos(const int32_t *pos, int64_t m, int64_t *cnt, cudaStream_t st);
 void launch_fill_from_pos(const int32_t *pos, int64_t m, const int64_t *ptr, int32_t *out, cudaStream_t st);
 void launch_iota_i64(int64_t *p, int64_t n, cudaStream_t st);
+void launch_add_i64(int64_t *p, int64_t n, int64_t add, cudaStream_t st);  // p[i] += add
 struct AsgnArgs {
   const int64_t *Ap; const int32_t *Aj; const void *Av;   // A (m x n)
   const int64_t *Xp; const int32_t *Xj; const void *Xv;   // X = R*B*Q (m x n)

@@ -98,6 +98,7 @@ struct PhaseTimer {
 struct Mem {
   const hs_allocator *al;
   cudaStream_t st;
+  cudaMemPool_t pool = nullptr;  // without an allocator: this pool if set, else the device's default pool
   struct Blk {
     void *p;
     size_t n;
@@ -110,7 +111,8 @@ struct Mem {
     void *p = nullptr;
     if (al && al->alloc) {
       p = al->alloc(bytes, (void *)st, al->ctx);
-    } else if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+    } else if ((pool ? cudaMallocFromPoolAsync(&p, bytes, pool, st) : cudaMallocAsync(&p, bytes, st)) !=
+               cudaSuccess) {
       cudaGetLastError();
       p = nullptr;
     }
@@ -132,6 +134,36 @@ struct Mem {
     for (auto &b : scratch) release(b.p, b.n);
   }
 };
+
+// A pool of the library's own for calls that allocate and free the same large
+// blocks many times (hs_spgemm_to_host): it keeps freed memory mapped for the
+// next block and the next call (hs_trim_memory returns it) instead of giving
+// it back at every synchronisation.
+static cudaMemPool_t own_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> g(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    if (cudaMemPoolCreate(&pools[dev], &props) != cudaSuccess) {
+      cudaGetLastError();
+      pools[dev] = nullptr;
+      return nullptr;
+    }
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+    cudaGetLastError();
+  }
+  return pools[dev];
+}
 
 static int vbytes_of(int dt) {
   switch (dt) {
@@ -814,6 +846,89 @@ void hs_plan_destroy(hs_plan *P, void *stream) {
   for (auto &b : P->blocks) mem.release(b.p, b.n);
   P->blocks.clear();
   delete P;
+}
+
+int hs_spgemm_to_host(int semiring, const hs_mat *A, const hs_mat *B, int64_t nblocks, int64_t *h_ptr,
+                      int32_t *h_idx, void *h_val, int64_t capacity, int64_t *nnz_out, void *stream,
+                      uint32_t flags) {
+  if (!A || !B || !h_ptr || !nnz_out || nblocks < 1 || capacity < 0) return HS_EINVAL;
+  if (A->fmt != HS_CSR || A->m < 0) return HS_EINVAL;
+  int out_dt = 0;
+  if (!numeric_supported(semiring, A->dtype, B->dtype, out_dt)) return HS_EINVAL;
+  const int vb = vbytes_of(out_dt);
+  if ((capacity > 0 && !h_idx) || (vb && capacity > 0 && !h_val)) return HS_EINVAL;
+  *nnz_out = 0;
+  t_detail[0] = 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaStream_t cs = nullptr;  // copies of finished blocks run here, beside the next block's product
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaEvent_t ev = nullptr;
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamDestroy(cs);
+    return HS_ECUDA;
+  }
+  cudaMemPool_t pool = own_pool();
+  const int64_t m = A->m;
+  const int64_t rows_per = (m + nblocks - 1) / nblocks;
+  int64_t base = 0;
+  int status = HS_OK;
+  for (int64_t r0 = 0; r0 < m || (m == 0 && r0 == 0); r0 += (rows_per ? rows_per : 1)) {
+    const int64_t r1 = m == 0 ? 0 : (r0 + rows_per < m ? r0 + rows_per : m);
+    // rows r0..r1 of A as a matrix of their own (offsets stay absolute)
+    hs_mat Ab = *A;
+    Ab.m = r1 - r0;
+    Ab.ptr = A->ptr + r0;
+    hs_mat Cb;
+    memset(&Cb, 0, sizeof(Cb));
+    Mem mem{nullptr, st, pool};
+    Mem out{nullptr, st, pool};
+    status = with_output(&Cb, out, [&] { return spgemm_impl(semiring, &Ab, B, &Cb, mem, out, flags); });
+    if (status != HS_OK) break;
+    const int64_t rows = r1 - r0;
+    if (base + Cb.nnz <= capacity) {
+      if (base) launch_add_i64(Cb.ptr, rows + 1, base, st);
+      if (cudaEventRecord(ev, st) != cudaSuccess || cudaStreamWaitEvent(cs, ev, 0) != cudaSuccess ||
+          cudaMemcpyAsync(h_ptr + r0, Cb.ptr, sizeof(int64_t) * (size_t)(rows + 1), cudaMemcpyDeviceToHost, cs) !=
+              cudaSuccess ||
+          (Cb.nnz && cudaMemcpyAsync(h_idx + base, Cb.idx, sizeof(int32_t) * (size_t)Cb.nnz,
+                                     cudaMemcpyDeviceToHost, cs) != cudaSuccess) ||
+          (vb && Cb.nnz &&
+           cudaMemcpyAsync(reinterpret_cast<char *>(h_val) + (size_t)base * vb, Cb.val, (size_t)vb * (size_t)Cb.nnz,
+                           cudaMemcpyDeviceToHost, cs) != cudaSuccess)) {
+        cudaGetLastError();
+        status = HS_ECUDA;
+      }
+    } else if (cudaEventRecord(ev, st) != cudaSuccess || cudaStreamWaitEvent(cs, ev, 0) != cudaSuccess) {
+      cudaGetLastError();
+      status = HS_ECUDA;
+    }
+    // the block's output goes back to the pool on the copy stream, after its copies
+    cudaFreeAsync(Cb.ptr, cs);
+    cudaFreeAsync(Cb.idx, cs);
+    if (Cb.val) cudaFreeAsync(Cb.val, cs);
+    base += Cb.nnz;
+    if (status != HS_OK || m == 0) break;
+  }
+  if (cudaStreamSynchronize(cs) != cudaSuccess && status == HS_OK) {
+    cudaGetLastError();
+    status = HS_ECUDA;
+  }
+  cudaEventDestroy(ev);
+  cudaStreamDestroy(cs);
+  *nnz_out = base;
+  if (status == HS_OK && base > capacity) status = HS_ECAPACITY;
+  return status;
+}
+
+int hs_trim_memory(void) {
+  cudaMemPool_t pool = own_pool();
+  if (!pool) return HS_ECUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess || cudaMemPoolTrimTo(pool, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return HS_ECUDA;
+  }
+  return HS_OK;
 }
 
 int hs_spref(const hs_mat *A, const int32_t *I, int64_t nI, const int32_t *J, int64_t nJ, hs_mat *B,

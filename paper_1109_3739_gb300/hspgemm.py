@@ -100,6 +100,9 @@ def _lib():
             L.hs_batch_stack.argtypes = [i64, P(hs_mat), P(hs_mat), P(hs_mat), P(hs_mat), P(ctypes.c_int64),
                                          P(hs_allocator), vp]
             L.hs_batch_stack.restype = ci
+            L.hs_spgemm_to_host.argtypes = [ci, P(hs_mat), P(hs_mat), i64, vp, vp, vp, i64, P(ctypes.c_int64), vp, u32]
+            L.hs_spgemm_to_host.restype = ci
+            L.hs_trim_memory.restype = ci
             L.hs_set_tuning.argtypes = [P(hs_tuning)]
             L.hs_set_tuning.restype = ci
             L.hs_get_tuning.argtypes = [P(hs_tuning)]
@@ -272,6 +275,33 @@ def spgemm_batched(semiring: str, As: list, Bs: list, validate: bool = False, st
     if st != 0:
         raise HsError(st, "hs_spgemm_batched")
     return _adopt_output(al, c), np.array(offs[:], dtype=np.int64)
+
+
+def spgemm_to_host(semiring: str, A: DeviceCSR, B: DeviceCSR, rowptr, col, val, blocks: int = 8,
+                   validate: bool = False, stream=None) -> int:
+    """C = A*B written into host tensors rowptr (A.m+1 int64), col (int32) and
+    val (C's dtype; None for bool), best pinned, with each row block's copy
+    overlapped with the next block's product (hs_spgemm_to_host).  Returns
+    nnz(C); raises HsError with .nnz_needed if the arrays are too small."""
+    L = _lib()
+    a, b = A.desc(), B.desc()
+    nnz = ctypes.c_int64(0)
+    cap = int(col.numel())
+    st = L.hs_spgemm_to_host(SEMIRING[semiring], ctypes.byref(a), ctypes.byref(b), int(blocks), rowptr.data_ptr(),
+                             col.data_ptr(), None if val is None else val.data_ptr(), cap, ctypes.byref(nnz),
+                             _stream_ptr(stream), FLAG_VALIDATE if validate else 0)
+    if st != 0:
+        e = HsError(st, "hs_spgemm_to_host")
+        e.nnz_needed = int(nnz.value)
+        raise e
+    return int(nnz.value)
+
+
+def trim_memory():
+    """Return the memory the library's own pool keeps (hs_trim_memory)."""
+    st = _lib().hs_trim_memory()
+    if st != 0:
+        raise HsError(st, "hs_trim_memory")
 
 
 def batch_stack(As: list, Bs: list, stream=None):

@@ -1,0 +1,61 @@
+"""hs_spgemm_to_host: C delivered to host memory block by block (each row
+block's copy overlapped with the next block's product) equals hs_spgemm's C
+and the oracle's; too small arrays give HS_ECAPACITY with the size needed."""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1109_3739_gb300 import inputs as I
+from tests.helpers import assert_bitexact, assert_within
+
+pytestmark = pytest.mark.gpu
+NT = os.cpu_count() or 1
+
+
+def H():
+    from paper_1109_3739_gb300 import hspgemm
+    return hspgemm
+
+
+def host_out(m, cap, dtype):
+    import torch
+    tdt = {"f64": torch.float64, "f32": torch.float32, "i32": torch.int32, "i64": torch.int64}.get(dtype)
+    rp = torch.empty(m + 1, dtype=torch.int64, pin_memory=True)
+    col = torch.empty(cap, dtype=torch.int32, pin_memory=True)
+    val = None if tdt is None else torch.empty(cap, dtype=tdt, pin_memory=True)
+    return rp, col, val
+
+
+@pytest.mark.parametrize("sr,dt,blocks", [("plus_times", "f32", 1), ("plus_times", "f32", 8),
+                                          ("or_and", "bool", 3), ("plus_times", "f64", 5), ("min_plus", "i32", 4)])
+def test_to_host_equals_device_product(sr, dt, blocks):
+    h = H()
+    A = I.rmat_matrix(14, 8, seed=7, dtype=dt) if dt in ("f32", "bool") else I.er_matrix(2000, 2000, 10, seed=8, dtype=dt)
+    dA = h.DeviceCSR.from_host(A)
+    ref = h.spgemm(sr, dA, dA)
+    rp, col, val = host_out(A.m, ref.nnz, ref.dtype)
+    nnz = h.spgemm_to_host(sr, dA, dA, rp, col, val, blocks=blocks)
+    assert nnz == ref.nnz
+    assert np.array_equal(rp.numpy(), ref.rowptr.cpu().numpy())
+    assert np.array_equal(col.numpy(), ref.col.cpu().numpy())
+    C = I.CSR(A.m, A.n, rp.numpy(), col.numpy(), None if val is None else val.numpy(), ref.dtype)
+    if sr == "plus_times" and dt in ("f32", "f64"):
+        R, bound = oracle.spgemm(sr, A, A, with_bound=True, nthreads=NT)
+        assert_within(C, R, bound, dt, "to_host")
+    else:
+        assert_bitexact(C, oracle.spgemm(sr, A, A, nthreads=NT), "to_host")
+
+
+def test_to_host_reports_capacity_needed():
+    h = H()
+    A = I.rmat_matrix(12, 8, seed=9, dtype="f32")
+    dA = h.DeviceCSR.from_host(A)
+    need = h.spgemm("plus_times", dA, dA).nnz
+    rp, col, val = host_out(A.m, need // 2, "f32")
+    with pytest.raises(h.HsError) as ei:
+        h.spgemm_to_host("plus_times", dA, dA, rp, col, val, blocks=4)
+    assert ei.value.code == -10 and ei.value.nnz_needed == need
