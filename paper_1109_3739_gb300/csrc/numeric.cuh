@@ -398,6 +398,10 @@ __global__ void __launch_bounds__(HV_NT, 2) k_num_heavy(NumArgs a) {
         const int32_t *Lp = (L && HS_G(dbg, done + pc <= c, 64, done + pc)) ? L + done : nullptr;
         // ---- occupancy and word ranks from the list: one bit per column and
         // one rank store per nonempty word
+        // rows on the fast path below write their columns here, straight from
+        // the list (they are C's columns of this part, in order)
+        const bool cols_now = cached && Lp;
+        const int64_t out = cb + done;
         if (Lp) {
           constexpr int U = 4;  // loads in flight per thread
           for (int i0 = tid; i0 < pc; i0 += U * HV_NT) {
@@ -411,7 +415,9 @@ __global__ void __launch_bounds__(HV_NT, 2) k_num_heavy(NumArgs a) {
 #pragma unroll
             for (int u = 0; u < U; ++u) {
               const int i = i0 + u * HV_NT;
-              if (i >= pc || !HS_G(dbg, x[u] >= 0 && x[u] < hi - lo, 63, x[u])) continue;
+              if (i >= pc) continue;
+              if (cols_now) __stcs(a.Cj + out + i, x[u] + lo);
+              if (!HS_G(dbg, x[u] >= 0 && x[u] < hi - lo, 63, x[u])) continue;
               const int w = x[u] >> 5;
               atomicOr(sm.bitmap + w, 1u << (x[u] & 31));
               if (i == 0 || (xp[u] >> 5) != w) sm.wpre[w] = (uint16_t)i;
@@ -579,9 +585,11 @@ __global__ void __launch_bounds__(HV_NT, 2) k_num_heavy(NumArgs a) {
           }
         }
         // ---- emit (columns ascending, values in rank order), then clear the bitmap
-        const int64_t out = cb + done;
         const bool fits = consistent && HS_G(dbg, done + pc <= c, 62, done + pc);
-        if (Lp) {
+        if (cols_now) {
+          // columns already written; clear the part's words
+          for (int w = tid; w < words; w += HV_NT) sm.bitmap[w] = 0u;
+        } else if (Lp) {
           constexpr int U = 4;
           for (int i0 = tid; i0 < pc; i0 += U * HV_NT) {
             int col[U];
