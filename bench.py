@@ -87,6 +87,22 @@ def csrc_hash():
 E2E_BLOCKS = 1
 
 
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The largest x over all ranks of the process group (x itself without one)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_step: int, steps: int, world: int, max_total_ms: float) -> float:
+    """Units per second of the whole job: every rank processes units_per_step
+    per step (replicas), timed by the slowest rank."""
+    return units_per_step * steps * world / (max_total_ms / 1000.0)
+
+
 def make_input(scale):
     from paper_1109_3739_gb300 import inputs as I
     return I.rmat_matrix(scale, 8, 0.57, 0.19, 0.19, seed=2, dtype="f32")
@@ -422,13 +438,10 @@ def main():
     launches = h.launch_count() - l0
     prof = h.profile_read()
     h.profile_enable(False)
-    total_ms = sum(times)
+    total_ms = max_over_ranks(sum(times), dist, dev)
     if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
-    value = flops * args.steps * world / (total_ms / 1000.0)
+    value = whole_job_rate(flops, args.steps, world, total_ms)
 
     # ---- roofline of the dominant kernel (largest total time among the library's kernel phases)
     hbm, peak_kind = peaks()

@@ -151,3 +151,38 @@ def test_stacked_batch_plan_matches_batched_call():
         Ci = h.csr_rows(Cn, int(offs[i]), int(offs[i + 1]), n=B2.n).to_host()
         check("plus_times", Ci, A2, B2, f"problem {i}")
     plan.close()
+
+
+def test_plan_edge_cases():
+    import torch
+    h = H()
+    # B without entries: C has no entries; executes are no-ops
+    A = I.er_matrix(300, 200, 4, seed=13, dtype="f64")
+    Bz = I.CSR(200, 150, np.zeros(201, np.int64), np.zeros(0, np.int32), np.zeros(0), "f64")
+    p = h.Plan("plus_times", h.DeviceCSR.from_host(A), h.DeviceCSR.from_host(Bz))
+    assert p.C.nnz == 0 and int(p.C.rowptr[-1]) == 0
+    p.execute()
+    p.status()
+    p.close()
+    # DCSR left operand (only non-empty rows stored)
+    A2 = I.rmat_matrix(13, 8, seed=14, dtype="f32")
+    dA2 = h.DeviceCSR.from_host(A2, dcsr=True)
+    dB2 = h.DeviceCSR.from_host(A2)
+    p2 = h.Plan("plus_times", dA2, dB2)
+    A3 = revalue(A2, 15)
+    cv = torch.empty_like(p2.C.val)
+    p2.execute(to_dev(A3.val, dA2.val), to_dev(A3.val, dB2.val), cv)
+    p2.status()
+    Cn = h.DeviceCSR(p2.C.m, p2.C.n, p2.C.rowptr, p2.C.col, cv, "f32")
+    check("plus_times", Cn.to_host(), A3, A3, "DCSR plan execute")
+    p2.close()
+
+
+def test_single_problem_batch_stack():
+    h = H()
+    import torch
+    A = I.er_matrix(10, 10, 2, seed=16)
+    dA = h.DeviceCSR.from_host(A)
+    SA, SB, offs = h.batch_stack([dA], [dA])
+    assert SA.m == 10 and SB.m == 10 and list(offs) == [0, 10]
+    assert torch.equal(SA.col.cpu(), dA.col.cpu())  # one problem: columns shifted by 0

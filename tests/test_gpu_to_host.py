@@ -59,3 +59,19 @@ def test_to_host_reports_capacity_needed():
     with pytest.raises(h.HsError) as ei:
         h.spgemm_to_host("plus_times", dA, dA, rp, col, val, blocks=4)
     assert ei.value.code == -10 and ei.value.nnz_needed == need
+
+
+def test_to_host_rejects_dcsr_and_handles_empty():
+    h = H()
+    A = I.rmat_matrix(10, 8, seed=11, dtype="f32")
+    dA = h.DeviceCSR.from_host(A, dcsr=True)
+    dB = h.DeviceCSR.from_host(A)
+    rp, col, val = host_out(A.m, 10, "f32")
+    with pytest.raises(h.HsError) as ei:
+        h.spgemm_to_host("plus_times", dA, dB, rp, col, val)
+    assert ei.value.code == -1
+    Z = I.CSR(0, A.n, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.float32), "f32")
+    dZ = h.DeviceCSR.from_host(Z)
+    rp0, col0, val0 = host_out(0, 0, "f32")
+    assert h.spgemm_to_host("plus_times", dZ, dB, rp0, col0, val0, blocks=3) == 0
+    assert int(rp0[0]) == 0

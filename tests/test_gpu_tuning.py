@@ -66,3 +66,21 @@ def test_autotuner_sets_a_valid_tuning():
         assert_within(h.spgemm("plus_times", dA, dA).to_host(), R, bound, "f32", "tuned product")
     finally:
         h.set_tuning(None)
+
+
+def test_out_of_range_thresholds_are_clamped():
+    import torch
+    h = H()
+    A = I.rmat_matrix(13, 8, seed=5, dtype="f32")
+    dA = h.DeviceCSR.from_host(A)
+    h.set_tuning(None)
+    ref = h.spgemm("plus_times", dA, dA)
+    try:
+        h.set_tuning({"warp_s_max": 100000, "mid_s_max": -5, "large_s_max": 1 << 30, "sym_mid_s_max": 0,
+                      "sym_heavy_from": 1})
+        C = h.spgemm("plus_times", dA, dA, validate=True)
+        assert torch.equal(C.rowptr, ref.rowptr) and torch.equal(C.col, ref.col)
+        R, bound = oracle.spgemm("plus_times", A, A, with_bound=True, nthreads=NT)
+        assert_within(C.to_host(), R, bound, "f32", "clamped thresholds")
+    finally:
+        h.set_tuning(None)
