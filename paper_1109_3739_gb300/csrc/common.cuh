@@ -725,10 +725,10 @@ __device__ void group_sort_emit(const int *keys, const T *vals, int slots, int c
     }
   }
   G::sync();
-  // (4) coalesced stores
+  // (4) coalesced stores, evict-first: C is not read again here, B is
   for (int e = r; e < c; e += gs) {
-    out_j[e] = sk[e];
-    if constexpr (HAS_VAL) out_v[e] = sv[e];
+    __stcs(out_j + e, sk[e]);
+    if constexpr (HAS_VAL) __stcs(out_v + e, sv[e]);
   }
   G::sync();
 }
