@@ -200,8 +200,30 @@ __global__ void __launch_bounds__(NT, 1) k_num_cta(NumArgs a) {
     __syncthreads();
     cta_products<SR, nch<CAP>()>(A, B, A.p[r], A.p[r + 1], false, 0, 0, ex, tl.wtmp,
                           [&](int col, T v, int) { hash_insert_val<SR>(keys, vals, mask, col, v, a.err); });
-    group_sort_emit<CtaGroup, T, SR::has_val>(keys, vals, slots, c, ck, cv, smem_raw, tl.wtmp, &tl.es,
-                                              a.Cj + cb, SR::has_val ? Cv + cb : nullptr, a.err, CAP, a.A.dbg);
+    const int64_t lofs = (a.loff && a.glist) ? a.loff[r] : -1;
+    if (lofs >= 0) {
+      // the symbolic pass left the row's sorted columns: no sort, each
+      // column's value is looked up in the table
+      const int32_t *Lr = a.glist + lofs;
+      for (int i = threadIdx.x; i < c; i += blockDim.x) {
+        const int col = __ldg(Lr + i);
+        unsigned hh = hash_slot(col, mask);
+        int probes = 0;
+        while (keys[hh] != col && probes <= (int)mask) {
+          hh = (hh + 1) & mask;
+          ++probes;
+        }
+        if (probes > (int)mask) {  // a listed column the products never reached
+          atomicExch(a.err, 11);
+          continue;
+        }
+        __stcs(a.Cj + cb + i, col);
+        if constexpr (SR::has_val) __stcs(Cv + cb + i, vals[hh]);
+      }
+    } else {
+      group_sort_emit<CtaGroup, T, SR::has_val>(keys, vals, slots, c, ck, cv, smem_raw, tl.wtmp, &tl.es,
+                                                a.Cj + cb, SR::has_val ? Cv + cb : nullptr, a.err, CAP, a.A.dbg);
+    }
     __syncthreads();
   }
 }
