@@ -134,13 +134,13 @@ __global__ void __launch_bounds__(NT) k_sym_cta(SymArgs a) {
 // Per row and per chunk of 2^20 columns: the products set their bits, and a
 // bit that was clear counts one new column of its 4096-column segment.  The
 // segment counts give the chunk's histogram and, scanned, each segment's
-// place in the row's sorted column list.  Each warp then walks whole
-// segments, every lane four consecutive words: the lanes' bit counts are
+// place in the row's sorted column list.  Each warp then walks pairs of
+// segments, every lane eight consecutive words: the lanes' bit counts are
 // scanned across the warp, the columns go to a per-warp staging buffer in
 // ascending order and leave it in coalesced stores.
 constexpr int SH_SEGS = BITMAP_COLS / SEG_W;  // segments per chunk (256)
-constexpr int SH_BUF = 256;                   // per-warp list staging entries
-static_assert(SEG_W == 4096, "a segment is 128 words: four per lane");
+constexpr int SH_BUF = 384;                   // per-warp list staging entries
+static_assert(SEG_W == 4096, "two segments are 256 words: eight per lane");
 
 // Product visitor: prep sets the column's bit (the old word comes back),
 // commit counts the column for its segment if the bit was clear.
@@ -226,48 +226,54 @@ __global__ void __launch_bounds__(1024, 1) k_sym_heavy(SymArgs a) {
         for (int g = threadIdx.x; g < nsc; g += blockDim.x)
           if (HS_G(a.A.dbg, lo / SEG_W + g < a.nseg, 32, g)) hist[lo / SEG_W + g] = (uint32_t)sm.scnt[g];
       const int ctotal = group_excl_scan<CtaGroup>(sm.scnt, nsc, sm.wtmp);
-      // list: warp w takes segments w, w + 32, ...
+      // list: a warp takes two consecutive segments at a time (8192
+      // columns: eight words per lane), pairs w, w + 32, ...
       if (lst) {
-        for (int g = warp; g < nsc; g += nw) {
-          const int wb = g * (SEG_W / 32) + 4 * lane;
-          // the lane's four words (128 columns) in one 16-byte load
-          uint4 v = make_uint4(0u, 0u, 0u, 0u);
-          if (wb + 3 < words) v = *reinterpret_cast<const uint4 *>(sm.bitmap + wb);
-          else if (wb < words) {
-            v.x = sm.bitmap[wb];
-            if (wb + 1 < words) v.y = sm.bitmap[wb + 1];
-            if (wb + 2 < words) v.z = sm.bitmap[wb + 2];
+        for (int g = 2 * warp; g < nsc; g += 2 * nw) {
+          const int wb = g * (SEG_W / 32) + 8 * lane;
+          unsigned long long b[4] = {0ull, 0ull, 0ull, 0ull};
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int w0 = wb + 4 * h;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (w0 + 3 < words) v = *reinterpret_cast<const uint4 *>(sm.bitmap + w0);
+            else if (w0 < words) {
+              v.x = sm.bitmap[w0];
+              if (w0 + 1 < words) v.y = sm.bitmap[w0 + 1];
+              if (w0 + 2 < words) v.z = sm.bitmap[w0 + 2];
+            }
+            b[2 * h] = ((unsigned long long)v.y << 32) | v.x;
+            b[2 * h + 1] = ((unsigned long long)v.w << 32) | v.z;
           }
-          unsigned long long b0 = ((unsigned long long)v.y << 32) | v.x;
-          unsigned long long b1 = ((unsigned long long)v.w << 32) | v.z;
-          const int pcl = __popcll(b0) + __popcll(b1);
+          const int pcl = __popcll(b[0]) + __popcll(b[1]) + __popcll(b[2]) + __popcll(b[3]);
           const int incl = warp_incl_scan(pcl);
           const int tot = __shfl_sync(FULL, incl, 31);
+          // the pair's columns start where segment g's do (g + 1 follows it)
           const int64_t at0 = written + sm.scnt[g];
           if (!HS_G(a.A.dbg, at0 + tot <= lmax, 34, at0 + tot)) continue;
           const int cbase = lo + (wb << 5);
           if (tot <= SH_BUF) {
             int p = incl - pcl;
-            while (b0) {
-              buf[p++] = cbase + __ffsll(b0) - 1;
-              b0 &= b0 - 1;
-            }
-            while (b1) {
-              buf[p++] = cbase + 64 + __ffsll(b1) - 1;
-              b1 &= b1 - 1;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              unsigned long long bb = b[q];
+              while (bb) {
+                buf[p++] = cbase + 64 * q + __ffsll(bb) - 1;
+                bb &= bb - 1;
+              }
             }
             __syncwarp();
             for (int i = lane; i < tot; i += 32) lst[at0 + i] = buf[i];
             __syncwarp();
-          } else {  // a dense segment: each lane's columns are one long run
+          } else {  // dense segments: each lane's columns are one long run
             int64_t at = at0 + incl - pcl;
-            while (b0) {
-              lst[at++] = cbase + __ffsll(b0) - 1;
-              b0 &= b0 - 1;
-            }
-            while (b1) {
-              lst[at++] = cbase + 64 + __ffsll(b1) - 1;
-              b1 &= b1 - 1;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              unsigned long long bb = b[q];
+              while (bb) {
+                lst[at++] = cbase + 64 * q + __ffsll(bb) - 1;
+                bb &= bb - 1;
+              }
             }
           }
         }
