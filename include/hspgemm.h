@@ -97,10 +97,13 @@ typedef struct hs_allocator {
 #define HS_EINTERNAL -8    /* device-side consistency check failed            */
 #define HS_ESCRATCH -9     /* hs_spgemm_noalloc: the product needs more scratch
                               than HS_NOALLOC_SCRATCH_MAX bytes                */
-#define HS_ECAPACITY -10   /* hs_spgemm_noalloc: output capacity too small     */
+#define HS_ECAPACITY -10   /* hs_spgemm_noalloc / hs_spgemm_to_host: output
+                              capacity too small                               */
 
 /* Flags. */
-#define HS_FLAG_VALIDATE 1u /* check canonical inputs and index ranges */
+#define HS_FLAG_VALIDATE 1u      /* check canonical inputs and index ranges */
+#define HS_FLAG_STAGE_ON_DEVICE 2u /* hs_spgemm_to_host: compute C in device memory and
+                                      copy it, even into host memory the GPU maps */
 
 /* C = A*B over `semiring` (Section 1; Algorithm 1 and Section 2.1).
  * A: m x k, CSR or DCSR.  B: k x n, CSR.  C: m x n CSR, filled in by the
@@ -162,8 +165,15 @@ int hs_spgemm_batched(int semiring, int64_t count, const hs_mat *A, const hs_mat
  * success they hold C in CSR (offsets from 0) and *nnz_out = nnz(C).  If
  * nnz(C) > capacity the call returns HS_ECAPACITY with *nnz_out the size
  * needed (blocks that fit were copied; call again with larger arrays).
- * Temporaries come from a memory pool of the library's own on the current
- * device, which keeps its memory for later calls until hs_trim_memory().
+ * With nblocks = 1 and arrays in page-locked host memory that the GPU maps
+ * (cudaHostAlloc / cudaHostRegister under unified addressing), the numeric
+ * kernels store C's columns and values straight into h_idx / h_val while
+ * they run (over NVLink-C2C on Grace systems; C then needs no device memory)
+ * and only the row offsets are copied afterwards, unless
+ * HS_FLAG_STAGE_ON_DEVICE is set; otherwise each block is computed in device
+ * memory and copied.  Temporaries come from a memory pool of the library's own on the
+ * current device, which keeps its memory for later calls until
+ * hs_trim_memory().
  * Same semirings, dtypes, results and errors as hs_spgemm; the call returns
  * when everything is on the host. */
 int hs_spgemm_to_host(int semiring, const hs_mat *A, const hs_mat *B, int64_t nblocks, int64_t *h_ptr,

@@ -346,8 +346,16 @@ struct hs_plan {
 
 namespace hs {
 
+// Where C's column ids and values go when the caller places them (device
+// pointers to memory of at least cap entries, e.g. host memory the GPU maps).
+struct OutPlace {
+  int32_t *idx;
+  void *val;
+  int64_t cap;
+};
+
 static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem &mem, Mem &outmem,
-                       uint32_t flags, hs_plan *plan = nullptr) {
+                       uint32_t flags, hs_plan *plan = nullptr, const OutPlace *place = nullptr) {
   cudaStream_t st = mem.st;
   if (!A || !B || !C) return HS_EINVAL;
   if (A->fmt != HS_CSR && A->fmt != HS_DCSR) return HS_EINVAL;
@@ -383,6 +391,11 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
     plan->b_nnz = B->nnz;
   }
   if (nslots == 0 || A->nnz == 0 || B->nnz == 0 || n == 0) {
+    if (place) {  // nothing to write
+      C->idx = place->idx;
+      C->val = place->val;
+      return check_launch();
+    }
     C->idx = (int32_t *)outmem.raw(4);
     if (!C->idx) return HS_ENOMEM;
     if (vb) {  // typed outputs always carry a (here empty) value array
@@ -517,11 +530,17 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
   const int64_t nnz = hb->nnz;
   memcpy(key_off, hb->key_off, sizeof(key_off));
   C->nnz = nnz;
-  C->idx = (int32_t *)outmem.raw(sizeof(int32_t) * (size_t)nnz);
-  if (!C->idx) return HS_ENOMEM;
-  if (vb) {
-    C->val = outmem.raw((size_t)vb * (size_t)nnz);
-    if (!C->val) return HS_ENOMEM;
+  if (place) {
+    if (nnz > place->cap) return HS_ECAPACITY;
+    C->idx = place->idx;
+    C->val = vb ? place->val : nullptr;
+  } else {
+    C->idx = (int32_t *)outmem.raw(sizeof(int32_t) * (size_t)nnz);
+    if (!C->idx) return HS_ENOMEM;
+    if (vb) {
+      C->val = outmem.raw((size_t)vb * (size_t)nnz);
+      if (!C->val) return HS_ENOMEM;
+    }
   }
 
   // ---- numeric
@@ -870,6 +889,42 @@ int hs_spgemm_to_host(int semiring, const hs_mat *A, const hs_mat *B, int64_t nb
   }
   cudaMemPool_t pool = own_pool();
   const int64_t m = A->m;
+  // Host arrays that the GPU maps (page-locked memory under unified
+  // addressing; on NVLink-C2C systems the stores travel while the kernels
+  // run): the numeric kernels write C's columns and values there directly,
+  // so nothing is copied afterwards but the row offsets.
+  auto mapped = [](const void *h) -> void * {
+    if (!h) return nullptr;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, h) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+  };
+  int32_t *d_idx = (int32_t *)mapped(h_idx);
+  void *d_val = vb ? mapped(h_val) : nullptr;
+  if (nblocks == 1 && capacity > 0 && d_idx && (!vb || d_val) && !(flags & HS_FLAG_STAGE_ON_DEVICE)) {
+    hs_mat Cd;
+    memset(&Cd, 0, sizeof(Cd));
+    Mem mem{nullptr, st, pool};
+    Mem out{nullptr, st, pool};
+    const OutPlace place{d_idx, d_val, capacity};
+    int status = spgemm_impl(semiring, A, B, &Cd, mem, out, flags, nullptr, &place);
+    *nnz_out = Cd.nnz;
+    if (status == HS_OK) {
+      if (cudaMemcpyAsync(h_ptr, Cd.ptr, sizeof(int64_t) * (size_t)(m + 1), cudaMemcpyDeviceToHost, st) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        status = HS_ECUDA;
+      }
+    }
+    if (Cd.ptr) out.release(Cd.ptr, sizeof(int64_t) * (size_t)(m + 1));
+    cudaEventDestroy(ev);
+    cudaStreamDestroy(cs);
+    return status;
+  }
   const int64_t rows_per = (m + nblocks - 1) / nblocks;
   int64_t base = 0;
   int status = HS_OK;

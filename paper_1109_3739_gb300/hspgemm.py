@@ -277,8 +277,11 @@ def spgemm_batched(semiring: str, As: list, Bs: list, validate: bool = False, st
     return _adopt_output(al, c), np.array(offs[:], dtype=np.int64)
 
 
+FLAG_STAGE_ON_DEVICE = 2
+
+
 def spgemm_to_host(semiring: str, A: DeviceCSR, B: DeviceCSR, rowptr, col, val, blocks: int = 8,
-                   validate: bool = False, stream=None) -> int:
+                   validate: bool = False, stage_on_device: bool = False, stream=None) -> int:
     """C = A*B written into host tensors rowptr (A.m+1 int64), col (int32) and
     val (C's dtype; None for bool), best pinned, with each row block's copy
     overlapped with the next block's product (hs_spgemm_to_host).  Returns
@@ -289,7 +292,8 @@ def spgemm_to_host(semiring: str, A: DeviceCSR, B: DeviceCSR, rowptr, col, val, 
     cap = int(col.numel())
     st = L.hs_spgemm_to_host(SEMIRING[semiring], ctypes.byref(a), ctypes.byref(b), int(blocks), rowptr.data_ptr(),
                              col.data_ptr(), None if val is None else val.data_ptr(), cap, ctypes.byref(nnz),
-                             _stream_ptr(stream), FLAG_VALIDATE if validate else 0)
+                             _stream_ptr(stream), (FLAG_VALIDATE if validate else 0)
+                             | (FLAG_STAGE_ON_DEVICE if stage_on_device else 0))
     if st != 0:
         e = HsError(st, "hs_spgemm_to_host")
         e.nnz_needed = int(nnz.value)

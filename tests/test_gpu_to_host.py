@@ -75,3 +75,31 @@ def test_to_host_rejects_dcsr_and_handles_empty():
     rp0, col0, val0 = host_out(0, 0, "f32")
     assert h.spgemm_to_host("plus_times", dZ, dB, rp0, col0, val0, blocks=3) == 0
     assert int(rp0[0]) == 0
+
+
+def test_direct_and_copied_paths_agree():
+    """Page-locked arrays with one block take the direct path (kernels store
+    into host memory); pageable arrays take the copy path; same C."""
+    import torch
+    h = H()
+    A = I.rmat_matrix(13, 8, seed=12, dtype="f32")
+    dA = h.DeviceCSR.from_host(A)
+    ref = h.spgemm("plus_times", dA, dA)
+    outs = []
+    for pinned, stage in ((True, False), (False, False), (True, True)):
+        rp = torch.empty(A.m + 1, dtype=torch.int64, pin_memory=pinned)
+        col = torch.empty(ref.nnz, dtype=torch.int32, pin_memory=pinned)
+        val = torch.empty(ref.nnz, dtype=torch.float32, pin_memory=pinned)
+        assert h.spgemm_to_host("plus_times", dA, dA, rp, col, val, blocks=1, stage_on_device=stage) == ref.nnz
+        outs.append((rp.numpy().copy(), col.numpy().copy(), val.numpy().copy()))
+    for rp, col, _ in outs:
+        assert np.array_equal(rp, ref.rowptr.cpu().numpy())
+        assert np.array_equal(col, ref.col.cpu().numpy())
+    R, bound = oracle.spgemm("plus_times", A, A, with_bound=True, nthreads=NT)
+    for rp, col, val in outs:
+        assert_within(I.CSR(A.m, A.n, rp, col, val, "f32"), R, bound, "f32", "to_host")
+    # the direct path reports a short capacity too
+    rp, col, val = host_out(A.m, ref.nnz - 1, "f32")
+    with pytest.raises(h.HsError) as ei:
+        h.spgemm_to_host("plus_times", dA, dA, rp, col, val, blocks=1)
+    assert ei.value.code == -10 and ei.value.nnz_needed == ref.nnz
