@@ -8,8 +8,10 @@ library and never imports it.
 
 Pinned against: dense brute force on tiny inputs, identity and permutation
 products, transpose and associativity identities, the Galerkin closed form,
-the SpRef/SpAsgn identities of Section 3 and the DCSC worked example of
-Section 2.2 (see tests/test_oracle_*.py).
+the SpRef/SpAsgn identities of Section 3, the DCSC worked example of
+Section 2.2, and for sparse(): SciPy's COO->CSR duplicate summation, a
+pure-Python dictionary build and the SpRef identity with sparse()-built
+selection matrices (see tests/test_oracle_*.py).
 """
 from __future__ import annotations
 
@@ -71,6 +73,8 @@ def _load():
             lib.oracle_spref.argtypes = [P, vp, i64, vp, i64, vp, vp, vp, vp]
             lib.oracle_spasgn.restype = i64
             lib.oracle_spasgn.argtypes = [P, vp, i64, vp, i64, P, ci, ci, vp, vp, vp, vp]
+            lib.oracle_sparse.restype = i64
+            lib.oracle_sparse.argtypes = [vp, vp, vp, i64, i64, i64, ci, ci, vp, vp, vp, vp, vp]
             lib.oracle_doubly_compress.restype = i64
             lib.oracle_doubly_compress.argtypes = [vp, i64, vp, vp]
             _lib = lib
@@ -210,6 +214,41 @@ def spasgn(A, I, J, B, accumulate: bool = False, sr: str = "plus_times"):
     if st < 0:
         raise OracleError(f"spasgn failed: {st}")
     return _csr(A.m, A.n, cp, cj, cv, A.dtype)
+
+
+def sparse(i, j, v, m: int, n: int, sr: str = "plus_times", dtype: str | None = None,
+           with_bound: bool = False):
+    """C = sparse(i, j, v, m, n) (Section 2 notation), tuples sharing a position
+    combined with sr's add in increasing tuple order (sum, min or or).
+
+    v is None for dtype "bool".  With with_bound also returns, per entry of C,
+    the sum of |v| over its tuples."""
+    lib = _load()
+    I = np.ascontiguousarray(i, dtype=np.int32)
+    J = np.ascontiguousarray(j, dtype=np.int32)
+    if len(I) != len(J):
+        raise OracleError("i and j differ in length")
+    if dtype is None:
+        dtype = "bool" if v is None else {np.dtype(t): k for k, t in _NP.items()}[np.asarray(v).dtype]
+    V = None if dtype == "bool" else np.ascontiguousarray(v, dtype=_NP[dtype])
+    if V is not None and len(V) != len(I):
+        raise OracleError("v differs in length")
+    rn = np.zeros(max(m, 0), dtype=np.int64)
+    tot = lib.oracle_sparse(_ptr(I), _ptr(J), _ptr(V), len(I), m, n, TYPES[dtype], SEMIRINGS[sr],
+                            _ptr(rn), None, None, None, None)
+    if tot < 0:
+        raise OracleError(f"sparse failed: {tot}")
+    cp = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(rn, out=cp[1:])
+    cj = np.empty(tot, dtype=np.int32)
+    cv = None if dtype == "bool" else np.empty(tot, dtype=_NP[dtype])
+    bound = np.empty(tot, dtype=np.float64)
+    st = lib.oracle_sparse(_ptr(I), _ptr(J), _ptr(V), len(I), m, n, TYPES[dtype], SEMIRINGS[sr],
+                           _ptr(rn), _ptr(cp), _ptr(cj), _ptr(cv), _ptr(bound))
+    if st < 0:
+        raise OracleError(f"sparse failed: {st}")
+    C = _csr(m, n, cp, cj, cv, dtype)
+    return (C, bound) if with_bound else C
 
 
 def doubly_compress(ptr):

@@ -66,3 +66,25 @@ def spgemm(sr: str, A, B):
                 pat[i, j] = True
                 val[i][j] = acc
     return pat, val, bnd
+
+
+def sparse(i, j, v, m: int, n: int, sr: str = "plus_times"):
+    """sparse(i, j, v, m, n) by a dictionary keyed on (row, column), tuples
+    folded in the order given.  Returns {(r, c): value} (True for bool)."""
+    out = {}
+    for k in range(len(i)):
+        key = (int(i[k]), int(j[k]))
+        if not (0 <= key[0] < m and 0 <= key[1] < n):
+            raise ValueError("index out of range")
+        x = True if v is None else v[k].item()
+        if key not in out:
+            out[key] = x
+        elif sr == "plus_times":
+            out[key] = out[key] + x
+        elif sr == "min_plus":
+            out[key] = min(out[key], x)
+        elif sr == "or_and":
+            out[key] = True
+        else:
+            raise ValueError(sr)
+    return out

@@ -453,6 +453,92 @@ int64_t oracle_spasgn(const ocsr *A, const int32_t *I, int64_t nI, const int32_t
   return total;
 }
 
+/* ----------------------------------------------------------------- sparse --
+ * C = sparse(i, j, v, m, n) in the notation of Section 2: the m x n matrix
+ * whose entry (i(k), j(k)) holds v(k), k = 0..nnz-1.  Several tuples may name
+ * one position; they are then combined with the semiring's add, taken in
+ * increasing k: the sum (O_PLUS_TIMES; F64, F32, I64), the minimum
+ * (O_MIN_PLUS; F32, I32) or the logical or (O_OR_AND; O_BOOL, v unused).
+ * Floating-point sums are formed in double and rounded once to the value
+ * type; integer sums wrap modulo 2^64.  bound (optional) receives, per entry
+ * of C, the sum of |v(k)| over its tuples: the scale of the rounding error of
+ * a sum formed in the value type in any order.
+ * Called twice: with cp == NULL it fills rownnz[m] and returns nnz(C); then,
+ * with cp the scanned offsets, it fills cj, cv and bound.                   */
+typedef struct {
+  int32_t i, j;
+  int64_t k;
+} ijk_t;
+
+static int cmp_ijk(const void *a, const void *b) {
+  const ijk_t *x = (const ijk_t *)a, *y = (const ijk_t *)b;
+  if (x->i != y->i) return (x->i > y->i) - (x->i < y->i);
+  if (x->j != y->j) return (x->j > y->j) - (x->j < y->j);
+  return (x->k > y->k) - (x->k < y->k);
+}
+
+int64_t oracle_sparse(const int32_t *I, const int32_t *J, const void *V, int64_t nnz, int64_t m,
+                      int64_t n, int t, int sr, int64_t *rownnz, const int64_t *cp, int32_t *cj,
+                      void *cv, double *bound) {
+  int ok = (sr == O_PLUS_TIMES && (t == O_F64 || t == O_F32 || t == O_I64)) ||
+           (sr == O_MIN_PLUS && (t == O_F32 || t == O_I32)) || (sr == O_OR_AND && t == O_BOOL);
+  if (!ok || nnz < 0 || m < 0 || n < 0 || (t != O_BOOL && nnz > 0 && !V)) return O_EINVAL;
+  for (int64_t k = 0; k < nnz; ++k)
+    if (I[k] < 0 || I[k] >= m || J[k] < 0 || J[k] >= n) return O_EINVAL;
+  ijk_t *s = (ijk_t *)malloc(sizeof(ijk_t) * (size_t)(nnz > 0 ? nnz : 1));
+  if (!s) return O_ENOMEM;
+  for (int64_t k = 0; k < nnz; ++k) { s[k].i = I[k]; s[k].j = J[k]; s[k].k = k; }
+  qsort(s, (size_t)nnz, sizeof(ijk_t), cmp_ijk);
+  if (!cp)
+    for (int64_t r = 0; r < m; ++r) rownnz[r] = 0;
+  int64_t out = 0;
+  for (int64_t e = 0; e < nnz;) {
+    int64_t f = e + 1; /* tuples e..f-1 share one position */
+    while (f < nnz && s[f].i == s[e].i && s[f].j == s[e].j) ++f;
+    if (!cp) {
+      ++rownnz[s[e].i];
+    } else {
+      /* rows are visited in increasing order, so entry `out` is the next slot */
+      cj[out] = s[e].j;
+      double sa = 0.0;
+      for (int64_t q = e; q < f; ++q) sa += fabs(getd(V, t, s[q].k));
+      if (bound) bound[out] = (t == O_BOOL) ? 0.0 : sa;
+      switch (t) {
+        case O_F64: case O_F32: {
+          double acc = getd(V, t, s[e].k);
+          for (int64_t q = e + 1; q < f; ++q) {
+            double x = getd(V, t, s[q].k);
+            acc = (sr == O_MIN_PLUS) ? (x < acc ? x : acc) : acc + x;
+          }
+          if (t == O_F64) ((double *)cv)[out] = acc;
+          else ((float *)cv)[out] = (float)acc;
+          break;
+        }
+        case O_I32: {
+          int32_t acc = ((const int32_t *)V)[s[e].k];
+          for (int64_t q = e + 1; q < f; ++q) {
+            int32_t x = ((const int32_t *)V)[s[q].k];
+            acc = x < acc ? x : acc;
+          }
+          ((int32_t *)cv)[out] = acc;
+          break;
+        }
+        case O_I64: {
+          uint64_t acc = (uint64_t)((const int64_t *)V)[s[e].k];
+          for (int64_t q = e + 1; q < f; ++q) acc += (uint64_t)((const int64_t *)V)[s[q].k];
+          ((int64_t *)cv)[out] = (int64_t)acc;
+          break;
+        }
+        default: break;
+      }
+    }
+    ++out;
+    e = f;
+  }
+  free(s);
+  return out;
+}
+
 /* ------------------------------------------------------------- DCSC / DCSR --
  * Doubly compressed form (Section 2.2): drop the repeated pointers of empty
  * columns (rows) and keep the ids of the non-empty ones in JC, parallel to

@@ -29,6 +29,7 @@ __all__ = [
     "er_matrix", "rmat_matrix", "laplacian7", "aggregation_R", "aggregation_RT",
     "cluster_S", "cluster_ST", "random_subset_sorted", "random_unique_sequence",
     "random_sequence", "csr_from_unique_sorted_keys", "identity", "permutation_matrix",
+    "random_tuples", "rmat_tuples",
 ]
 
 _GAMMA = np.uint64(0x9E3779B97F4A7C15)
@@ -370,6 +371,28 @@ def random_unique_sequence(n: int, k: int, seed: int, stream: int = 9) -> np.nda
 def random_sequence(n: int, k: int, seed: int, stream: int = 10) -> np.ndarray:
     """k indices of 0..n-1 drawn with replacement (duplicates allowed), random order."""
     return _below(draws(seed, stream, 0, k), n).astype(np.int32)
+
+
+# ----------------------------------------------------------------------------- tuples
+def random_tuples(m: int, n: int, nnz: int, seed: int, dtype: str = "f64", kind: str = "signed"):
+    """(i, j, v) of nnz uniform random positions of an m x n matrix, drawn with
+    replacement (so positions repeat once nnz approaches m*n), in random order;
+    v is None for bool."""
+    i = random_sequence(m, nnz, seed, stream=13) if m > 0 else np.zeros(nnz, np.int32)
+    j = random_sequence(n, nnz, seed, stream=14) if n > 0 else np.zeros(nnz, np.int32)
+    return i, j, random_values(nnz, dtype, seed, stream=15, kind=kind)
+
+
+def rmat_tuples(scale: int, edge_factor: int = 8, seed: int = 2, dtype: str = "f32", kind: str = "unit",
+                a: float = 0.57, b: float = 0.19, c: float = 0.19):
+    """The raw R-MAT edge list of rmat_matrix (duplicates kept, vertices
+    relabelled by the same seeded permutation) as int32 (i, j) with one value
+    per edge: the input of building the adjacency matrix with sparse()."""
+    n = 1 << scale
+    r, cc = rmat_edges(scale, edge_factor, a, b, c, seed)
+    p = random_permutation(n, seed)
+    i, j = p[r].astype(np.int32), p[cc].astype(np.int32)
+    return i, j, random_values(len(i), dtype, seed, stream=16, kind=kind)
 
 
 # ----------------------------------------------------------------------------- batches
