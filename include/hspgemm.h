@@ -12,7 +12,9 @@
  *   - SpAsgn A(I,J) = B computed as A + R*B*Q - S*A*T, the subtraction being
  *     an elementwise product with the structural negation of S*A*T
  *     (Section 3.1, SpAsgn listing and the theorem after it),
- *   - Liu's extend-add A(I,J) = A(I,J) + B (Section 3).
+ *   - Liu's extend-add A(I,J) = A(I,J) + B (Section 3),
+ *   - the constructor sparse(i, j, v, m, n) with repeated positions combined
+ *     (Section 2's notation), computed as a product of two such matrices.
  *
  * Conventions shared by every entry point
  *   - Indices are 0-based (the paper is 1-based).  Column ids are int32, row
@@ -43,9 +45,9 @@
 extern "C" {
 #endif
 
-/* Semirings (Section 1, "SpGEMM ... over a general semiring"; Section 3.1:
- * SpRef/SpAsgn use "mixed-mode SpGEMM between a boolean matrix and a
- * general-type matrix", here the two selector semirings). */
+/* Semirings (Section 1: the product is defined over any semiring; Section
+ * 3.1: SpRef and SpAsgn multiply a 0/1 selection matrix with a matrix of any
+ * value type, here the two selector semirings). */
 typedef enum {
   HS_PLUS_TIMES = 0, /* (+, x): F64, F32, I64                                  */
   HS_OR_AND = 1,     /* (or, and): structure only; output dtype HS_BOOL         */
@@ -140,6 +142,25 @@ int hs_spref(const hs_mat *A, const int32_t *I, int64_t nI, const int32_t *J, in
 int hs_spasgn(const hs_mat *A, const int32_t *I, int64_t nI, const int32_t *J, int64_t nJ,
               const hs_mat *B, int accumulate, int add_semiring, hs_mat *C,
               const hs_allocator *al, void *stream, uint32_t flags);
+
+/* C = sparse(i, j, v, m, n) (Section 2's constructor): the m x n CSR matrix
+ * with C(i[k], j[k]) = v[k] for k < nnz.  Tuples that name the same position
+ * are combined with `add_semiring`'s add: HS_PLUS_TIMES sums (dtype HS_F64,
+ * HS_F32 or HS_I64), HS_MIN_PLUS keeps the minimum (HS_F32, HS_I32), HS_OR_AND
+ * builds the structure only (HS_BOOL; v is ignored and may be NULL).  i, j:
+ * int32 device arrays of nnz indices in [0,m) and [0,n), any order; v: device
+ * array of nnz values of `dtype`.  Every position named by a tuple is stored,
+ * even where its values sum to zero.  Integer sums wrap modulo 2^64;
+ * floating-point sums are formed in the value type in an unspecified order.
+ * Computed as the product T*V of T = sparse(i, 1:nnz, 1, m, nnz) and
+ * V = sparse(1:nnz, j, v, nnz, n) through the hs_spgemm pipeline (Section
+ * 3.1's reduction of indexing to SpGEMM), so it costs one product of nnz
+ * multiplications plus a counting pass over i.  Errors: HS_EINVAL (an index
+ * out of range -- always checked --, a dtype/semiring pair not listed, NULL
+ * pointers), HS_EUNSUPPORTED (nnz, m or n above 2^31-1), HS_ENOMEM, HS_ECUDA. */
+int hs_sparse(const int32_t *i, const int32_t *j, const void *v, int64_t nnz, int64_t m, int64_t n,
+              int dtype, int add_semiring, hs_mat *C, const hs_allocator *al, void *stream,
+              uint32_t flags);
 
 /* Many independent products C_i = A_i * B_i, i < count, in one pass of the
  * pipeline (the batched form; Section 1's SpGEMM applied to a batch): the

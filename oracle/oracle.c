@@ -21,7 +21,7 @@
 #include <string.h>
 #include <math.h>
 
-/* semirings (Section 1: SpGEMM "over a general semiring") */
+/* semirings (Section 1: SpGEMM over any semiring) */
 #define O_PLUS_TIMES 0 /* (+, x)                                        */
 #define O_OR_AND 1     /* (or, and): structure only                     */
 #define O_MIN_PLUS 2   /* (min, +)                                      */
@@ -261,7 +261,7 @@ int oracle_spgemm_numeric(int sr, const ocsr *A, const ocsr *B, int64_t r0, int6
 
 /* ------------------------------------------------------------------ SpRef --
  * B = A(I,J) (Section 3): row t of B is row I[t] of A, and column p of B is
- * column J[p] of A, "respecting the order of indices"; repeated indices
+ * column J[p] of A, in the order the indices are given; repeated indices
  * repeat rows/columns.  Computed directly by index, not through products:
  * pos lists, for every column k of A, the positions p with J[p] == k in
  * increasing p; entry (I[t],k,v) of A yields (t,p,v) for each p in pos(k).

@@ -122,7 +122,7 @@ void launch_num_count(const RowSet &A, const int64_t *f, const int64_t *Cp, cons
                       cudaStream_t st);
 void launch_scatter_num(const RowSet &A, const int64_t *f, const int64_t *Cp, const BinCfg &bins, int *key_cur,
                         int *list, cudaStream_t st);
-void launch_scan_i64(int64_t *a, int64_t n, int64_t *tmp, cudaStream_t st);  // exclusive, in place
+void launch_scan_i64(int64_t *a, int64_t n, int64_t *tmp, cudaStream_t st);  // inclusive, in place
 int64_t scan_tmp_elems(int64_t n);
 // B segment index: for every B row longer than `min_len`, the offset (within
 // the row) of its first entry in each SEG_W-column segment, nseg+1 values
@@ -199,6 +199,7 @@ void launch_check_range(const int32_t *X, int64_t n, int64_t bound, int *flag, c
 // pos[X[i]] = i for in-range X[i] (bit 1 of flag: out of range; bit 2: repeated)
 void launch_mark_positions(const int32_t *X, int64_t n, int64_t bound, int32_t *pos, int *flag, cudaStream_t st);
 void launch_fill_i32(int32_t *a, int64_t n, int32_t v, cudaStream_t st);
+void launch_fill_i64(int64_t *a, int64_t n, int64_t v, cudaStream_t st);
 void launch_rows_from_pos(const int32_t *pos, int64_t m, int64_t *cnt, cudaStream_t st);
 void launch_fill_from_pos(const int32_t *pos, int64_t m, const int64_t *ptr, int32_t *out, cudaStream_t st);
 void launch_iota_i64(int64_t *p, int64_t n, cudaStream_t st);

@@ -685,6 +685,71 @@ static int spref_impl(const hs_mat *A, const int32_t *I, int64_t nI, const int32
   return e;
 }
 
+// C = sparse(i, j, v, m, n) (Section 2's constructor) as the product T*V,
+// the way Section 3.1 turns indexing into SpGEMM:
+//   T = sparse(i, 1:nnz, 1, m, nnz)  row r lists the tuples k with i[k] == r
+//   V = sparse(1:nnz, j, v, nnz, n)  row k is the single entry (j[k], v[k])
+// so C(r, c) is the semiring sum, over the tuples k at (r, c), of
+// T(r, k) (x) v[k].  T's value is the multiplicative identity, which leaves
+// every v[k] unchanged: 1 for (+,x); for (min,+) integer 0 and, in floating
+// point, -0.0 (IEEE -0 + x is x for every x, +0 would turn -0 into +0).  The
+// semiring's add then combines the tuples that share a position.  V uses j
+// and v in place; only T's offsets, tuple ids and constant values are built.
+static int sparse_impl(const int32_t *I, const int32_t *J, const void *V, int64_t nnz, int64_t m, int64_t n,
+                       int dtype, int sr, hs_mat *C, Mem &mem, Mem &outmem, uint32_t flags) {
+  cudaStream_t st = mem.st;
+  if (!C || nnz < 0 || m < 0 || n < 0) return HS_EINVAL;
+  const bool ok = (sr == HS_PLUS_TIMES && (dtype == HS_F64 || dtype == HS_F32 || dtype == HS_I64)) ||
+                  (sr == HS_MIN_PLUS && (dtype == HS_F32 || dtype == HS_I32)) ||
+                  (sr == HS_OR_AND && dtype == HS_BOOL);
+  if (!ok) return HS_EINVAL;
+  if (nnz > 0 && (!I || !J || (dtype != HS_BOOL && !V))) return HS_EINVAL;
+  if (nnz > 0x7fffffffLL || m > 0x7fffffffLL || n > 0x7fffffffLL) return HS_EUNSUPPORTED;
+  const int vb = vbytes_of(dtype);
+  if (nnz > 0) {  // index ranges are always checked: they address T's rows and C's columns
+    int *flag = mem.tmp<int>(2);
+    int *hflag = (int *)pinned(8);
+    if (!flag || !hflag) return HS_ENOMEM;
+    CK(cudaMemsetAsync(flag, 0, 8, st));
+    launch_check_range(I, nnz, m, flag, st);
+    launch_check_range(J, nnz, n, flag, st);
+    CK(cudaMemcpyAsync(hflag, flag, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (hflag[0]) return HS_EINVAL;
+  }
+  int64_t *Tp = mem.tmp<int64_t>(m + 1);
+  int64_t *Tcur = mem.tmp<int64_t>(m + 1);
+  int32_t *Tj = mem.tmp<int32_t>(nnz > 0 ? nnz : 1);
+  void *Tv = vb ? (void *)mem.tmp<char>((size_t)vb * (size_t)(nnz > 0 ? nnz : 1)) : nullptr;
+  int64_t *Vp = mem.tmp<int64_t>(nnz + 1);
+  int64_t *scan_tmp = mem.tmp<int64_t>(scan_tmp_elems(m + 1));
+  if (mem.failed) return HS_ENOMEM;
+  {
+    PhaseTimer t("sparse_build", st);
+    CK(cudaMemsetAsync(Tp, 0, sizeof(int64_t) * (size_t)(m + 1), st));
+    launch_build_Q_count(I, nnz, Tp, st);
+    launch_scan_i64(Tp, m + 1, scan_tmp, st);
+    CK(cudaMemcpyAsync(Tcur, Tp, sizeof(int64_t) * (size_t)(m + 1), cudaMemcpyDeviceToDevice, st));
+    launch_build_Q_fill(I, nnz, Tcur, Tj, st);
+    launch_iota_i64(Vp, nnz + 1, st);
+    if (vb == 8) {
+      const double one = 1.0;
+      int64_t bits = 1;  // HS_I64
+      if (dtype == HS_F64) memcpy(&bits, &one, 8);
+      launch_fill_i64((int64_t *)Tv, nnz, bits, st);
+    } else if (vb == 4) {
+      const float w = sr == HS_PLUS_TIMES ? 1.0f : -0.0f;
+      int32_t bits = 0;  // HS_I32 (min,+)
+      if (dtype == HS_F32) memcpy(&bits, &w, 4);
+      launch_fill_i32((int32_t *)Tv, nnz, bits, st);
+    }
+  }
+  if (int e = check_launch()) return e;
+  hs_mat T{HS_CSR, dtype, m, nnz, nnz, 0, Tp, Tj, nullptr, Tv};
+  hs_mat Vm{HS_CSR, dtype, nnz, n, nnz, 0, Vp, const_cast<int32_t *>(J), nullptr, const_cast<void *>(V)};
+  return spgemm_impl(sr, &T, &Vm, C, mem, outmem, flags & ~HS_FLAG_VALIDATE);
+}
+
 static int spasgn_impl(const hs_mat *A, const int32_t *I, int64_t nI, const int32_t *J, int64_t nJ,
                        const hs_mat *B, int accumulate, int add_sr, hs_mat *C, Mem &mem, Mem &outmem,
                        uint32_t flags) {
@@ -993,6 +1058,15 @@ int hs_spref(const hs_mat *A, const int32_t *I, int64_t nI, const int32_t *J, in
   Mem mem{al, (cudaStream_t)stream};
   Mem out{al, (cudaStream_t)stream};
   return with_output(B, out, [&] { return spref_impl(A, I, nI, J, nJ, B, mem, out, flags); });
+}
+
+int hs_sparse(const int32_t *i, const int32_t *j, const void *v, int64_t nnz, int64_t m, int64_t n, int dtype,
+              int add_semiring, hs_mat *C, const hs_allocator *al, void *stream, uint32_t flags) {
+  if (!C) return HS_EINVAL;
+  memset(C, 0, sizeof(*C));
+  Mem mem{al, (cudaStream_t)stream};
+  Mem out{al, (cudaStream_t)stream};
+  return with_output(C, out, [&] { return sparse_impl(i, j, v, nnz, m, n, dtype, add_semiring, C, mem, out, flags); });
 }
 
 int hs_spasgn(const hs_mat *A, const int32_t *I, int64_t nI, const int32_t *J, int64_t nJ, const hs_mat *B,

@@ -20,6 +20,7 @@ SEMIRING = {"plus_times": 0, "or_and": 1, "min_plus": 2, "select2nd": 3, "select
 DTYPE = {"f64": 0, "f32": 1, "i32": 2, "i64": 3, "bool": 4}
 DTYPE_NAME = {v: k for k, v in DTYPE.items()}
 VBYTES = {"f64": 8, "f32": 4, "i32": 4, "i64": 8, "bool": 0}
+I_NP = {"f64": np.float64, "f32": np.float32, "i32": np.int32, "i64": np.int64}
 FLAG_VALIDATE = 1
 STATUS = {0: "HS_OK", -1: "HS_EINVAL", -2: "HS_ENONCANON", -3: "HS_EDUP", -4: "HS_ENOMEM",
           -5: "HS_ETIMEDOUT", -6: "HS_ECUDA", -7: "HS_EUNSUPPORTED", -8: "HS_EINTERNAL",
@@ -84,6 +85,7 @@ def _lib():
             L.hs_spasgn.argtypes = [P(hs_mat), vp, i64, vp, i64, P(hs_mat), ci, ci, P(hs_mat),
                                     P(hs_allocator), vp, u32]
             L.hs_spasgn.restype = ci
+            L.hs_sparse.argtypes = [vp, vp, vp, i64, i64, i64, ci, ci, P(hs_mat), P(hs_allocator), vp, u32]
             L.hs_spgemm_batched.argtypes = [ci, i64, P(hs_mat), P(hs_mat), P(hs_mat), P(ctypes.c_int64),
                                              P(hs_allocator), vp, u32]
             L.hs_spgemm_batched.restype = ci
@@ -453,6 +455,45 @@ def spasgn(A: DeviceCSR, I, J, B: DeviceCSR, accumulate: bool = False, add: str 
         raise HsError(st, "hs_spasgn")
     return _adopt_output(al, c)
 
+
+
+def sparse(i, j, v, m: int, n: int, add: str = "plus_times", dtype: str | None = None, stream=None,
+           device=None) -> DeviceCSR:
+    """C = sparse(i, j, v, m, n) with repeated positions combined by add's add (hs_sparse).
+
+    i, j: index arrays (host or device); v: values (None for bool).  dtype
+    defaults to v's type ("bool" when v is None)."""
+    torch = _torch()
+    L = _lib()
+    if device is None:
+        device = next((x.device for x in (i, j, v) if isinstance(x, torch.Tensor) and x.is_cuda), "cuda")
+    It, Jt = _idx(i, device), _idx(j, device)
+    if It.numel() != Jt.numel():
+        raise ValueError("i and j differ in length")
+    if dtype is None:
+        if v is None:
+            dtype = "bool"
+        else:
+            vd = v.dtype if isinstance(v, torch.Tensor) else np.asarray(v).dtype
+            dtype = {torch.float64: "f64", torch.float32: "f32", torch.int32: "i32", torch.int64: "i64",
+                     np.dtype(np.float64): "f64", np.dtype(np.float32): "f32", np.dtype(np.int32): "i32",
+                     np.dtype(np.int64): "i64"}[vd]
+    Vt = None
+    if dtype != "bool":
+        tdt = {"f64": torch.float64, "f32": torch.float32, "i32": torch.int32, "i64": torch.int64}[dtype]
+        Vt = (v.to(device=device, dtype=tdt) if isinstance(v, torch.Tensor)
+              else torch.from_numpy(np.ascontiguousarray(np.asarray(v), dtype=I_NP[dtype])).to(device)).contiguous()
+        if Vt.numel() != It.numel():
+            raise ValueError("v differs in length")
+    al = _TorchAlloc(torch.device(device))
+    c = hs_mat()
+    nnz = It.numel()
+    st = L.hs_sparse(It.data_ptr() if nnz else None, Jt.data_ptr() if nnz else None,
+                     Vt.data_ptr() if (Vt is not None and nnz) else None, nnz, int(m), int(n), DTYPE[dtype],
+                     SEMIRING[add], ctypes.byref(c), ctypes.byref(al.struct), _stream_ptr(stream), 0)
+    if st != 0:
+        raise HsError(st, "hs_sparse")
+    return _adopt_output(al, c)
 
 # --------------------------------------------------------------- profiling
 def set_tuning(tuning: dict | None = None):
