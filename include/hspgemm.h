@@ -14,7 +14,7 @@
  *     (Section 3.1, SpAsgn listing and the theorem after it),
  *   - Liu's extend-add A(I,J) = A(I,J) + B (Section 3),
  *   - the constructor sparse(i, j, v, m, n) with repeated positions combined
- *     (Section 2's notation), computed as a product of two such matrices.
+ *     (Section 2's notation).
  *
  * Conventions shared by every entry point
  *   - Indices are 0-based (the paper is 1-based).  Column ids are int32, row
@@ -151,13 +151,14 @@ int hs_spasgn(const hs_mat *A, const int32_t *I, int64_t nI, const int32_t *J, i
  * int32 device arrays of nnz indices in [0,m) and [0,n), any order; v: device
  * array of nnz values of `dtype`.  Every position named by a tuple is stored,
  * even where its values sum to zero.  Integer sums wrap modulo 2^64;
- * floating-point sums are formed in the value type in an unspecified order.
- * Computed as the product T*V of T = sparse(i, 1:nnz, 1, m, nnz) and
- * V = sparse(1:nnz, j, v, nnz, n) through the hs_spgemm pipeline (Section
- * 3.1's reduction of indexing to SpGEMM), so it costs one product of nnz
- * multiplications plus a counting pass over i.  Errors: HS_EINVAL (an index
- * out of range -- always checked --, a dtype/semiring pair not listed, NULL
- * pointers), HS_EUNSUPPORTED (nnz, m or n above 2^31-1), HS_ENOMEM, HS_ECUDA. */
+ * floating-point sums are formed in the value type.  Computed by a stable
+ * radix sort of the keys (i, j) that carries v, so the tuples of a position
+ * are folded in input order (runs of more than 32 tuples: in 32 consecutive
+ * slices, folded in order) and results are deterministic.  Temporaries: two
+ * key arrays (8 bytes per tuple) and two value arrays; one host
+ * synchronisation with `stream`.  Errors: HS_EINVAL (an index out of range --
+ * always checked --, a dtype/semiring pair not listed, NULL pointers),
+ * HS_EUNSUPPORTED (nnz, m or n above 2^31-1), HS_ENOMEM, HS_ECUDA. */
 int hs_sparse(const int32_t *i, const int32_t *j, const void *v, int64_t nnz, int64_t m, int64_t n,
               int dtype, int add_semiring, hs_mat *C, const hs_allocator *al, void *stream,
               uint32_t flags);

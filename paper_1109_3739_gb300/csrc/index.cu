@@ -13,8 +13,6 @@
 // structure of S*A*T exactly when r is in I and c is in J, so the negation is
 // applied through the inverse index maps rpos/cpos, so neither S*A*T nor its
 // negation is ever materialised (Section 3.1).
-// The general constructor sparse(i, j, v, m, n) uses the same counting build
-// for its row-grouping matrix T = sparse(i, 1:nnz, 1, m, nnz).
 #include "common.cuh"
 #include "internal.h"
 
@@ -37,14 +35,6 @@ void launch_fill_i32(int32_t *a, int64_t n, int32_t v, cudaStream_t st) {
   if (n > 0) {
     count_launch();
     k_fill_i32<<<grid1(n), 256, 0, st>>>(a, n, v);
-  }
-}
-
-__global__ void k_fill_i64(int64_t *a, int64_t n, int64_t v) { GRID_STRIDE(i, n) a[i] = v; }
-void launch_fill_i64(int64_t *a, int64_t n, int64_t v, cudaStream_t st) {
-  if (n > 0) {
-    count_launch();
-    k_fill_i64<<<grid1(n), 256, 0, st>>>(a, n, v);
   }
 }
 

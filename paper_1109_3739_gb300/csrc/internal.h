@@ -199,7 +199,22 @@ void launch_check_range(const int32_t *X, int64_t n, int64_t bound, int *flag, c
 // pos[X[i]] = i for in-range X[i] (bit 1 of flag: out of range; bit 2: repeated)
 void launch_mark_positions(const int32_t *X, int64_t n, int64_t bound, int32_t *pos, int *flag, cudaStream_t st);
 void launch_fill_i32(int32_t *a, int64_t n, int32_t v, cudaStream_t st);
-void launch_fill_i64(int64_t *a, int64_t n, int64_t v, cudaStream_t st);
+
+// sparse.cu: sparse(i, j, v, m, n) by a stable radix sort of (row, column)
+// keys.  Tiles of sp_tiles(nnz); digit tables of 256 * tiles entries.
+int64_t sp_tiles(int64_t nnz);
+int sp_radix_bits();
+int64_t sp_long_capacity(int64_t nnz);  // runs longer than the emit kernel folds alone
+void launch_sp_hist(bool first, const uint64_t *K, const int32_t *I, const int32_t *J, int64_t nnz, int nbj,
+                    int64_t m, int64_t n, int shift, int64_t *cnt, int64_t ntiles, int *flag, cudaStream_t st);
+void launch_sp_scatter(bool first, int vb, const uint64_t *Kin, const int32_t *I, const int32_t *J, const void *Vin,
+                       int64_t nnz, int nbj, int64_t m, int64_t n, int shift, const int64_t *cnt_incl,
+                       int64_t ntiles, uint64_t *Kout, void *Vout, int *flag, cudaStream_t st);
+void launch_sp_heads(const uint64_t *K, int64_t nnz, int64_t *theads, int64_t ntiles, cudaStream_t st);
+// op: 0 (+) f64, 1 (+) f32, 2 (+) i64, 3 min f32, 4 min i32, 5 structure only
+void launch_sp_emit(int op, const uint64_t *K, const void *V, int64_t nnz, int nbj, const int64_t *theads_incl,
+                    int64_t ntiles, int32_t *Cidx, void *Cval, int64_t *rowcnt, int64_t *longlist, int *nlong,
+                    cudaStream_t st);
 void launch_rows_from_pos(const int32_t *pos, int64_t m, int64_t *cnt, cudaStream_t st);
 void launch_fill_from_pos(const int32_t *pos, int64_t m, const int64_t *ptr, int32_t *out, cudaStream_t st);
 void launch_iota_i64(int64_t *p, int64_t n, cudaStream_t st);

@@ -1,0 +1,409 @@
+// sparse.cu -- the constructor sparse(i, j, v, m, n) of Section 2's notation:
+// the m x n matrix with entry (i[k], j[k]) = v[k], tuples that name one
+// position combined with the semiring's add.
+//
+// Each tuple becomes one key, row i in the high bits and column j in the low
+// bits, so the keys' order is CSR order.  A stable least-significant-digit
+// radix sort (8-bit digits, as many passes as the key has bytes of
+// information) carries the values along; stability keeps the tuples of one
+// position in their input order.  A pass is reduce-then-scan: every tile of
+// 4096 keys counts its digits (k_sp_hist), one scan of the digit-major count
+// table gives every (digit, tile) its output offset, and the tile is ranked
+// stably in shared memory and written out digit run by digit run
+// (k_sp_scatter).  The first pass reads i, j and v directly and checks their
+// ranges.  Then runs of equal keys are the entries of C: k_sp_heads counts
+// run heads per tile, and k_sp_emit writes one column id and one combined
+// value per run and counts the entries of each row; runs longer than
+// SP_SHORT are combined by a warp each (k_sp_long).  Every kernel streams its
+// keys once: the work is HBM-bound, about 32 bytes per tuple and pass.
+#include "common.cuh"
+#include "internal.h"
+
+namespace hs {
+
+constexpr int SP_NT = 256, SP_IPT = 16, SP_TILE = SP_NT * SP_IPT, SP_RADIX = 256;
+constexpr int SP_WARPS = SP_NT / 32;
+constexpr int SP_SHORT = 32;  // longer runs of one position go to k_sp_long
+static_assert(SP_NT == SP_RADIX, "one thread per digit in the per-tile digit scan");
+
+template <bool FIRST>
+__device__ __forceinline__ uint64_t sp_key(const uint64_t *K, const int32_t *I, const int32_t *J, int64_t t,
+                                           int nbj, int64_t m, int64_t n, int *flag) {
+  if (!FIRST) return K[t];
+  const int32_t i = I[t], j = J[t];
+  if (i < 0 || i >= m || j < 0 || j >= n) {  // the host reports HS_EINVAL; the key only has to be some digit
+    atomicOr(flag, 1);
+    return 0;
+  }
+  return ((uint64_t)(uint32_t)i << nbj) | (uint64_t)(uint32_t)j;
+}
+
+// digit counts of one tile: cnt[d * ntiles + tile]
+template <bool FIRST>
+__global__ void __launch_bounds__(SP_NT) k_sp_hist(const uint64_t *K, const int32_t *I, const int32_t *J,
+                                                   int64_t nnz, int nbj, int64_t m, int64_t n, int shift,
+                                                   int64_t *cnt, int64_t ntiles, int *flag) {
+  __shared__ int h[SP_WARPS][SP_RADIX];
+  for (int x = threadIdx.x; x < SP_WARPS * SP_RADIX; x += SP_NT) (&h[0][0])[x] = 0;
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t t0 = (int64_t)blockIdx.x * SP_TILE;
+#pragma unroll 4
+  for (int it = 0; it < SP_IPT; ++it) {
+    const int64_t t = t0 + (int64_t)it * SP_NT + threadIdx.x;
+    const bool ok = t < nnz;
+    const unsigned act = __ballot_sync(FULL, ok);
+    if (ok) {
+      const int d = (int)((sp_key<FIRST>(K, I, J, t, nbj, m, n, flag) >> shift) & (SP_RADIX - 1));
+      const unsigned peers = __match_any_sync(act, d);
+      // one lane per distinct digit adds the group's size: no two lanes touch one counter
+      if (lane == __ffs(peers) - 1) h[w][d] += __popc(peers);
+    }
+  }
+  __syncthreads();
+  const int d = threadIdx.x;
+  int s = 0;
+#pragma unroll
+  for (int ww = 0; ww < SP_WARPS; ++ww) s += h[ww][d];
+  cnt[(int64_t)d * ntiles + blockIdx.x] = s;
+}
+
+template <int VB> struct SpVal { using T = uint32_t; };
+template <> struct SpVal<8> { using T = uint64_t; };
+
+template <int VB> constexpr size_t sp_scatter_smem() {
+  return (size_t)SP_TILE * 8 + (size_t)SP_TILE * (VB ? VB : 0) + sizeof(int) * SP_WARPS * SP_RADIX +
+         sizeof(int) * SP_RADIX + sizeof(long long) * SP_RADIX;
+}
+
+// one stable pass: cnt_incl is the inclusive scan of k_sp_hist's table
+template <bool FIRST, int VB>
+__global__ void __launch_bounds__(SP_NT) k_sp_scatter(const uint64_t *Kin, const int32_t *I, const int32_t *J,
+                                                      const void *Vin, int64_t nnz, int nbj, int64_t m,
+                                                      int64_t n, int shift, const int64_t *cnt_incl,
+                                                      int64_t ntiles, uint64_t *Kout, void *Vout, int *flag) {
+  using VT = typename SpVal<VB>::T;
+  extern __shared__ __align__(16) unsigned char sp_smem[];
+  uint64_t *skey = reinterpret_cast<uint64_t *>(sp_smem);
+  VT *sval = reinterpret_cast<VT *>(sp_smem + (size_t)SP_TILE * 8);
+  int *wcnt = reinterpret_cast<int *>(sp_smem + (size_t)SP_TILE * 8 + (size_t)SP_TILE * VB);  // [warp][digit]
+  int *start = wcnt + SP_WARPS * SP_RADIX;
+  long long *goff = reinterpret_cast<long long *>(start + SP_RADIX);
+  __shared__ int wsum[SP_WARPS];
+
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int x = threadIdx.x; x < SP_WARPS * SP_RADIX; x += SP_NT) wcnt[x] = 0;
+  __syncthreads();
+  const int64_t t0 = (int64_t)blockIdx.x * SP_TILE;
+  const int nt = (int)(nnz - t0 < SP_TILE ? nnz - t0 : SP_TILE);
+  const unsigned lt = (1u << lane) - 1u;
+  uint64_t k[SP_IPT];
+  VT v[SP_IPT];
+  int r[SP_IPT];
+  // warp w ranks the tile's items w*512 .. w*512+511 in order, 32 at a time
+#pragma unroll
+  for (int it = 0; it < SP_IPT; ++it) {
+    const int e = w * (SP_IPT * 32) + it * 32 + lane;
+    const bool ok = e < nt;
+    k[it] = 0;
+    v[it] = 0;
+    r[it] = 0;
+    const unsigned act = __ballot_sync(FULL, ok);
+    if (ok) {
+      k[it] = sp_key<FIRST>(Kin, I, J, t0 + e, nbj, m, n, flag);
+      if (VB) v[it] = reinterpret_cast<const VT *>(Vin)[t0 + e];
+      const int d = (int)((k[it] >> shift) & (SP_RADIX - 1));
+      const unsigned peers = __match_any_sync(act, d);
+      const int base = wcnt[w * SP_RADIX + d];
+      r[it] = base + __popc(peers & lt);
+      __syncwarp(act);
+      if (lane == 31 - __clz(peers)) wcnt[w * SP_RADIX + d] = base + __popc(peers);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  // per digit: offsets of the warps' groups inside the tile's digit run, and
+  // the tile's run starts (exclusive scan over the digits)
+  const int d = threadIdx.x;
+  int tot = 0;
+#pragma unroll
+  for (int ww = 0; ww < SP_WARPS; ++ww) {
+    const int c = wcnt[ww * SP_RADIX + d];
+    wcnt[ww * SP_RADIX + d] = tot;
+    tot += c;
+  }
+  const int incl = warp_incl_scan(tot);
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  int before = 0;
+#pragma unroll
+  for (int ww = 0; ww < SP_WARPS; ++ww) before += ww < w ? wsum[ww] : 0;
+  start[d] = before + incl - tot;
+  goff[d] = cnt_incl[(int64_t)d * ntiles + blockIdx.x] - tot;
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < SP_IPT; ++it) {
+    const int e = w * (SP_IPT * 32) + it * 32 + lane;
+    if (e < nt) {
+      const int dd = (int)((k[it] >> shift) & (SP_RADIX - 1));
+      const int pos = start[dd] + wcnt[w * SP_RADIX + dd] + r[it];
+      skey[pos] = k[it];
+      if (VB) sval[pos] = v[it];
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nt; e += SP_NT) {
+    const uint64_t key = skey[e];
+    const int dd = (int)((key >> shift) & (SP_RADIX - 1));
+    const long long out = goff[dd] + (e - start[dd]);
+    Kout[out] = key;
+    if (VB) reinterpret_cast<VT *>(Vout)[out] = sval[e];
+  }
+}
+
+// number of runs of equal keys starting in each tile
+__global__ void __launch_bounds__(SP_NT) k_sp_heads(const uint64_t *K, int64_t nnz, int64_t *theads) {
+  __shared__ int ws[SP_WARPS];
+  const int64_t t0 = (int64_t)blockIdx.x * SP_TILE;
+  int c = 0;
+  for (int e = threadIdx.x; e < SP_TILE; e += SP_NT) {
+    const int64_t t = t0 + e;
+    if (t < nnz && (t == 0 || K[t] != K[t - 1])) ++c;
+  }
+  c = warp_sum(c);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int ww = 0; ww < SP_WARPS; ++ww) s += ws[ww];
+    theads[blockIdx.x] = s;
+  }
+}
+
+// combine operations: 0 (+) on f64, 1 (+) on f32, 2 (+) on i64 (mod 2^64),
+// 3 min on f32, 4 min on i32, 5 none (bool)
+template <int OP> struct SpOp;
+template <> struct SpOp<0> {
+  using T = double;
+  static __device__ T add(T a, T b) { return a + b; }
+};
+template <> struct SpOp<1> {
+  using T = float;
+  static __device__ T add(T a, T b) { return a + b; }
+};
+template <> struct SpOp<2> {
+  using T = int64_t;
+  static __device__ T add(T a, T b) { return (int64_t)((uint64_t)a + (uint64_t)b); }
+};
+template <> struct SpOp<3> {
+  using T = float;
+  static __device__ T add(T a, T b) { return b < a ? b : a; }  // earlier value kept on ties
+};
+template <> struct SpOp<4> {
+  using T = int32_t;
+  static __device__ T add(T a, T b) { return b < a ? b : a; }
+};
+template <> struct SpOp<5> {
+  using T = int32_t;  // unused
+  static __device__ T add(T a, T) { return a; }
+};
+
+// one column id and one value per run; row counts into rowcnt[row + 1]
+template <int OP>
+__global__ void __launch_bounds__(SP_NT) k_sp_emit(const uint64_t *K, const void *Vs, int64_t nnz, int nbj,
+                                                   const int64_t *theads_incl, int32_t *Cidx, void *Cval,
+                                                   int64_t *rowcnt, int64_t *longlist, int *nlong) {
+  using T = typename SpOp<OP>::T;
+  constexpr bool HAS_VAL = OP != 5;
+  __shared__ int ws[SP_WARPS];
+  const T *V = reinterpret_cast<const T *>(Vs);
+  const int64_t t0 = (int64_t)blockIdx.x * SP_TILE + (int64_t)threadIdx.x * SP_IPT;
+  const uint64_t maskj = nbj ? ((1ull << nbj) - 1ull) : 0ull;
+  uint64_t k[SP_IPT];
+  if (t0 + SP_IPT <= nnz) {  // 128 contiguous bytes per thread
+    const uint4 *src = reinterpret_cast<const uint4 *>(K + t0);
+#pragma unroll
+    for (int q = 0; q < SP_IPT / 2; ++q) {
+      const uint4 x = src[q];
+      k[2 * q] = ((uint64_t)x.y << 32) | x.x;
+      k[2 * q + 1] = ((uint64_t)x.w << 32) | x.z;
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < SP_IPT; ++e) k[e] = t0 + e < nnz ? K[t0 + e] : 0;
+  }
+  const uint64_t prev = (t0 > 0 && t0 <= nnz) ? K[t0 - 1] : 0;
+  unsigned heads = 0;
+#pragma unroll
+  for (int e = 0; e < SP_IPT; ++e) {
+    const int64_t t = t0 + e;
+    const bool h = t < nnz && (t == 0 || k[e] != (e ? k[e - 1] : prev));
+    heads |= (unsigned)h << e;
+  }
+  const int c = __popc(heads);
+  const int incl = warp_incl_scan(c);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 31) ws[w] = incl;
+  __syncthreads();
+  int64_t p = blockIdx.x ? theads_incl[blockIdx.x - 1] : 0;
+  for (int ww = 0; ww < SP_WARPS; ++ww) p += ww < w ? ws[ww] : 0;
+  p += incl - c;
+  int64_t cur_row = -1;
+  int rc = 0;
+#pragma unroll
+  for (int e = 0; e < SP_IPT; ++e) {
+    if (!((heads >> e) & 1u)) continue;
+    const int64_t t = t0 + e;
+    const int64_t row = (int64_t)(k[e] >> nbj);
+    Cidx[p] = (int32_t)(k[e] & maskj);
+    if (HAS_VAL) {
+      T acc = V[t];
+      int64_t q = t + 1;
+      while (q < nnz && q - t < SP_SHORT && K[q] == k[e]) acc = SpOp<OP>::add(acc, V[q++]);
+      if (q < nnz && q - t == SP_SHORT && K[q] == k[e]) {
+        const int at = atomicAdd(nlong, 1);  // at most nnz / (SP_SHORT + 1) runs qualify
+        longlist[2 * at] = t;
+        longlist[2 * at + 1] = p;
+      } else {
+        reinterpret_cast<T *>(Cval)[p] = acc;
+      }
+    }
+    if (row != cur_row) {
+      if (rc) atomicAdd(reinterpret_cast<unsigned long long *>(rowcnt + cur_row + 1), (unsigned long long)rc);
+      cur_row = row;
+      rc = 0;
+    }
+    ++rc;
+    ++p;
+  }
+  if (rc) atomicAdd(reinterpret_cast<unsigned long long *>(rowcnt + cur_row + 1), (unsigned long long)rc);
+}
+
+// runs longer than SP_SHORT: one warp each; lane l folds the l-th of 32
+// consecutive slices in order, lane 0 folds the slices' results in order
+template <int OP>
+__global__ void __launch_bounds__(SP_NT) k_sp_long(const uint64_t *K, const void *Vs, int64_t nnz,
+                                                   const int64_t *longlist, const int *nlong, void *Cval) {
+  using T = typename SpOp<OP>::T;
+  const T *V = reinterpret_cast<const T *>(Vs);
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * SP_NT + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * SP_NT) >> 5;
+  const int cnt = *nlong;
+  for (int64_t x = gw; x < cnt; x += nw) {
+    const int64_t t = longlist[2 * x], p = longlist[2 * x + 1];
+    const uint64_t key = K[t];
+    // end of the run: first q > t with a different key
+    int64_t e = t + SP_SHORT;
+    for (;;) {
+      const int64_t q = e + lane;
+      const bool diff = q >= nnz || K[q] != key;
+      const unsigned b = __ballot_sync(FULL, diff);
+      if (b) {
+        e += __ffs(b) - 1;
+        break;
+      }
+      e += 32;
+    }
+    const int64_t len = e - t, per = (len + 31) / 32;
+    const int64_t a = t + lane * per, z = a + per < e ? a + per : e;
+    T acc{};
+    bool has = a < z;
+    if (has) {
+      acc = V[a];
+      for (int64_t q = a + 1; q < z; ++q) acc = SpOp<OP>::add(acc, V[q]);
+    }
+    T tot{};
+    bool any = false;
+    for (int l = 0; l < 32; ++l) {
+      const T x2 = __shfl_sync(FULL, acc, l);
+      const bool h2 = __shfl_sync(FULL, (int)has, l);
+      if (h2) {
+        tot = any ? SpOp<OP>::add(tot, x2) : x2;
+        any = true;
+      }
+    }
+    if (lane == 0) reinterpret_cast<T *>(Cval)[p] = tot;
+  }
+}
+
+static int sp_grid(int64_t tiles) { return (int)tiles; }
+
+void launch_sp_hist(bool first, const uint64_t *K, const int32_t *I, const int32_t *J, int64_t nnz, int nbj,
+                    int64_t m, int64_t n, int shift, int64_t *cnt, int64_t ntiles, int *flag, cudaStream_t st) {
+  if (ntiles <= 0) return;
+  count_launch();
+  if (first)
+    k_sp_hist<true><<<sp_grid(ntiles), SP_NT, 0, st>>>(K, I, J, nnz, nbj, m, n, shift, cnt, ntiles, flag);
+  else
+    k_sp_hist<false><<<sp_grid(ntiles), SP_NT, 0, st>>>(K, I, J, nnz, nbj, m, n, shift, cnt, ntiles, flag);
+}
+
+template <bool FIRST, int VB>
+static void sp_scatter_one(const uint64_t *Kin, const int32_t *I, const int32_t *J, const void *Vin, int64_t nnz,
+                           int nbj, int64_t m, int64_t n, int shift, const int64_t *cnt_incl, int64_t ntiles,
+                           uint64_t *Kout, void *Vout, int *flag, cudaStream_t st) {
+  constexpr size_t smem = sp_scatter_smem<VB>();
+  set_smem_attr(k_sp_scatter<FIRST, VB>, smem);
+  count_launch();
+  k_sp_scatter<FIRST, VB><<<sp_grid(ntiles), SP_NT, smem, st>>>(Kin, I, J, Vin, nnz, nbj, m, n, shift, cnt_incl,
+                                                                ntiles, Kout, Vout, flag);
+}
+
+void launch_sp_scatter(bool first, int vb, const uint64_t *Kin, const int32_t *I, const int32_t *J, const void *Vin,
+                       int64_t nnz, int nbj, int64_t m, int64_t n, int shift, const int64_t *cnt_incl,
+                       int64_t ntiles, uint64_t *Kout, void *Vout, int *flag, cudaStream_t st) {
+  if (ntiles <= 0) return;
+#define SP_SC(F, B) sp_scatter_one<F, B>(Kin, I, J, Vin, nnz, nbj, m, n, shift, cnt_incl, ntiles, Kout, Vout, flag, st)
+  if (first) {
+    if (vb == 8) SP_SC(true, 8);
+    else if (vb == 4) SP_SC(true, 4);
+    else SP_SC(true, 0);
+  } else {
+    if (vb == 8) SP_SC(false, 8);
+    else if (vb == 4) SP_SC(false, 4);
+    else SP_SC(false, 0);
+  }
+#undef SP_SC
+}
+
+void launch_sp_heads(const uint64_t *K, int64_t nnz, int64_t *theads, int64_t ntiles, cudaStream_t st) {
+  if (ntiles <= 0) return;
+  count_launch();
+  k_sp_heads<<<sp_grid(ntiles), SP_NT, 0, st>>>(K, nnz, theads);
+}
+
+void launch_sp_emit(int op, const uint64_t *K, const void *V, int64_t nnz, int nbj, const int64_t *theads_incl,
+                    int64_t ntiles, int32_t *Cidx, void *Cval, int64_t *rowcnt, int64_t *longlist, int *nlong,
+                    cudaStream_t st) {
+  if (ntiles <= 0) return;
+  count_launch();
+#define SP_EM(O) k_sp_emit<O><<<sp_grid(ntiles), SP_NT, 0, st>>>(K, V, nnz, nbj, theads_incl, Cidx, Cval, rowcnt, longlist, nlong)
+  switch (op) {
+    case 0: SP_EM(0); break;
+    case 1: SP_EM(1); break;
+    case 2: SP_EM(2); break;
+    case 3: SP_EM(3); break;
+    case 4: SP_EM(4); break;
+    default: SP_EM(5); break;
+  }
+#undef SP_EM
+  if (op == 5) return;
+  count_launch();
+  const int grid = sm_count() * 4;
+#define SP_LG(O) k_sp_long<O><<<grid, SP_NT, 0, st>>>(K, V, nnz, longlist, nlong, Cval)
+  switch (op) {
+    case 0: SP_LG(0); break;
+    case 1: SP_LG(1); break;
+    case 2: SP_LG(2); break;
+    case 3: SP_LG(3); break;
+    default: SP_LG(4); break;
+  }
+#undef SP_LG
+}
+
+int64_t sp_tiles(int64_t nnz) { return (nnz + SP_TILE - 1) / SP_TILE; }
+int sp_radix_bits() { return 8; }
+int64_t sp_long_capacity(int64_t nnz) { return nnz / (SP_SHORT + 1) + 1; }
+
+}  // namespace hs

@@ -685,69 +685,97 @@ static int spref_impl(const hs_mat *A, const int32_t *I, int64_t nI, const int32
   return e;
 }
 
-// C = sparse(i, j, v, m, n) (Section 2's constructor) as the product T*V,
-// the way Section 3.1 turns indexing into SpGEMM:
-//   T = sparse(i, 1:nnz, 1, m, nnz)  row r lists the tuples k with i[k] == r
-//   V = sparse(1:nnz, j, v, nnz, n)  row k is the single entry (j[k], v[k])
-// so C(r, c) is the semiring sum, over the tuples k at (r, c), of
-// T(r, k) (x) v[k].  T's value is the multiplicative identity, which leaves
-// every v[k] unchanged: 1 for (+,x); for (min,+) integer 0 and, in floating
-// point, -0.0 (IEEE -0 + x is x for every x, +0 would turn -0 into +0).  The
-// semiring's add then combines the tuples that share a position.  V uses j
-// and v in place; only T's offsets, tuple ids and constant values are built.
+// C = sparse(i, j, v, m, n) (Section 2's constructor).  Every tuple is the
+// key (i << bits(n-1)) | j, so that ascending keys are CSR order; a stable
+// radix sort of the keys, carrying v, puts the tuples of one position next to
+// each other in input order, and each run of equal keys becomes one entry of
+// C, its values folded with the semiring's add (kernels in sparse.cu).  One
+// host synchronisation: after the sort, to learn nnz(C) and whether an index
+// was out of range.
+static int bits_of(int64_t x) { return x > 0 ? 64 - __builtin_clzll((unsigned long long)x) : 0; }
+
 static int sparse_impl(const int32_t *I, const int32_t *J, const void *V, int64_t nnz, int64_t m, int64_t n,
-                       int dtype, int sr, hs_mat *C, Mem &mem, Mem &outmem, uint32_t flags) {
+                       int dtype, int sr, hs_mat *C, Mem &mem, Mem &outmem, uint32_t) {
   cudaStream_t st = mem.st;
   if (!C || nnz < 0 || m < 0 || n < 0) return HS_EINVAL;
-  const bool ok = (sr == HS_PLUS_TIMES && (dtype == HS_F64 || dtype == HS_F32 || dtype == HS_I64)) ||
-                  (sr == HS_MIN_PLUS && (dtype == HS_F32 || dtype == HS_I32)) ||
-                  (sr == HS_OR_AND && dtype == HS_BOOL);
-  if (!ok) return HS_EINVAL;
+  int op = -1;
+  if (sr == HS_PLUS_TIMES) op = dtype == HS_F64 ? 0 : dtype == HS_F32 ? 1 : dtype == HS_I64 ? 2 : -1;
+  else if (sr == HS_MIN_PLUS) op = dtype == HS_F32 ? 3 : dtype == HS_I32 ? 4 : -1;
+  else if (sr == HS_OR_AND) op = dtype == HS_BOOL ? 5 : -1;
+  if (op < 0) return HS_EINVAL;
   if (nnz > 0 && (!I || !J || (dtype != HS_BOOL && !V))) return HS_EINVAL;
   if (nnz > 0x7fffffffLL || m > 0x7fffffffLL || n > 0x7fffffffLL) return HS_EUNSUPPORTED;
   const int vb = vbytes_of(dtype);
-  if (nnz > 0) {  // index ranges are always checked: they address T's rows and C's columns
-    int *flag = mem.tmp<int>(2);
-    int *hflag = (int *)pinned(8);
-    if (!flag || !hflag) return HS_ENOMEM;
-    CK(cudaMemsetAsync(flag, 0, 8, st));
-    launch_check_range(I, nnz, m, flag, st);
-    launch_check_range(J, nnz, n, flag, st);
-    CK(cudaMemcpyAsync(hflag, flag, 8, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (hflag[0]) return HS_EINVAL;
+  memset(C, 0, sizeof(*C));
+  C->fmt = HS_CSR;
+  C->dtype = dtype;
+  C->m = m;
+  C->n = n;
+  C->ptr = (int64_t *)outmem.raw(sizeof(int64_t) * (size_t)(m + 1));
+  if (!C->ptr) return HS_ENOMEM;
+  CK(cudaMemsetAsync(C->ptr, 0, sizeof(int64_t) * (size_t)(m + 1), st));
+  if (nnz == 0) {
+    C->idx = (int32_t *)outmem.raw(4);
+    C->val = vb ? outmem.raw((size_t)vb) : nullptr;
+    if (!C->idx || (vb && !C->val)) return HS_ENOMEM;
+    return check_launch();
   }
-  int64_t *Tp = mem.tmp<int64_t>(m + 1);
-  int64_t *Tcur = mem.tmp<int64_t>(m + 1);
-  int32_t *Tj = mem.tmp<int32_t>(nnz > 0 ? nnz : 1);
-  void *Tv = vb ? (void *)mem.tmp<char>((size_t)vb * (size_t)(nnz > 0 ? nnz : 1)) : nullptr;
-  int64_t *Vp = mem.tmp<int64_t>(nnz + 1);
-  int64_t *scan_tmp = mem.tmp<int64_t>(scan_tmp_elems(m + 1));
-  if (mem.failed) return HS_ENOMEM;
+  const int nbj = bits_of(n - 1), nbi = bits_of(m - 1);
+  const int rb = sp_radix_bits();
+  int passes = (nbi + nbj + rb - 1) / rb;
+  if (passes < 1) passes = 1;
+  const int64_t tiles = sp_tiles(nnz);
+  const int64_t table = tiles << rb;
+  const int64_t longcap = sp_long_capacity(nnz);
+  int64_t scan_n = table > m + 1 ? table : m + 1;
+  uint64_t *kbuf[2] = {mem.tmp<uint64_t>((size_t)nnz), mem.tmp<uint64_t>((size_t)nnz)};
+  void *vbuf[2] = {nullptr, nullptr};
+  if (vb) {
+    vbuf[0] = mem.tmp<char>((size_t)nnz * vb);
+    vbuf[1] = mem.tmp<char>((size_t)nnz * vb);
+  }
+  int64_t *cnt = mem.tmp<int64_t>((size_t)table);
+  int64_t *theads = mem.tmp<int64_t>((size_t)tiles);
+  int64_t *scan_tmp = mem.tmp<int64_t>((size_t)scan_tmp_elems(scan_n));
+  int64_t *longlist = vb ? mem.tmp<int64_t>((size_t)(2 * longcap)) : nullptr;
+  int *flags = mem.tmp<int>(2);  // [0] index out of range, [1] long runs
+  int64_t *host = (int64_t *)pinned(16);
+  if (mem.failed || !host) return HS_ENOMEM;
+  CK(cudaMemsetAsync(flags, 0, 8, st));
+  int cur = 0;
   {
-    PhaseTimer t("sparse_build", st);
-    CK(cudaMemsetAsync(Tp, 0, sizeof(int64_t) * (size_t)(m + 1), st));
-    launch_build_Q_count(I, nnz, Tp, st);
-    launch_scan_i64(Tp, m + 1, scan_tmp, st);
-    CK(cudaMemcpyAsync(Tcur, Tp, sizeof(int64_t) * (size_t)(m + 1), cudaMemcpyDeviceToDevice, st));
-    launch_build_Q_fill(I, nnz, Tcur, Tj, st);
-    launch_iota_i64(Vp, nnz + 1, st);
-    if (vb == 8) {
-      const double one = 1.0;
-      int64_t bits = 1;  // HS_I64
-      if (dtype == HS_F64) memcpy(&bits, &one, 8);
-      launch_fill_i64((int64_t *)Tv, nnz, bits, st);
-    } else if (vb == 4) {
-      const float w = sr == HS_PLUS_TIMES ? 1.0f : -0.0f;
-      int32_t bits = 0;  // HS_I32 (min,+)
-      if (dtype == HS_F32) memcpy(&bits, &w, 4);
-      launch_fill_i32((int32_t *)Tv, nnz, bits, st);
+    PhaseTimer t("sparse_sort", st);
+    for (int p = 0; p < passes; ++p) {
+      const bool first = p == 0;
+      const uint64_t *kin = first ? nullptr : kbuf[cur];
+      const void *vin = first ? V : vbuf[cur];
+      const int out = first ? 0 : cur ^ 1;
+      launch_sp_hist(first, kin, I, J, nnz, nbj, m, n, p * rb, cnt, tiles, flags, st);
+      launch_scan_i64(cnt, table, scan_tmp, st);
+      launch_sp_scatter(first, vb, kin, I, J, vin, nnz, nbj, m, n, p * rb, cnt, tiles, kbuf[out], vbuf[out],
+                        flags, st);
+      cur = out;
     }
+    launch_sp_heads(kbuf[cur], nnz, theads, tiles, st);
+    launch_scan_i64(theads, tiles, scan_tmp, st);
   }
   if (int e = check_launch()) return e;
-  hs_mat T{HS_CSR, dtype, m, nnz, nnz, 0, Tp, Tj, nullptr, Tv};
-  hs_mat Vm{HS_CSR, dtype, nnz, n, nnz, 0, Vp, const_cast<int32_t *>(J), nullptr, const_cast<void *>(V)};
-  return spgemm_impl(sr, &T, &Vm, C, mem, outmem, flags & ~HS_FLAG_VALIDATE);
+  CK(cudaMemcpyAsync(host, theads + tiles - 1, 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(host + 1, flags, 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (*(int *)(host + 1)) return HS_EINVAL;
+  const int64_t U = host[0];
+  C->nnz = U;
+  C->idx = (int32_t *)outmem.raw(sizeof(int32_t) * (size_t)U);
+  C->val = vb ? outmem.raw((size_t)vb * (size_t)U) : nullptr;
+  if (!C->idx || (vb && !C->val)) return HS_ENOMEM;
+  {
+    PhaseTimer t("sparse_emit", st);
+    launch_sp_emit(op, kbuf[cur], vbuf[cur], nnz, nbj, theads, tiles, C->idx, C->val, C->ptr, longlist,
+                   flags + 1, st);
+    launch_scan_i64(C->ptr, m + 1, scan_tmp, st);
+  }
+  return check_launch();
 }
 
 static int spasgn_impl(const hs_mat *A, const int32_t *I, int64_t nI, const int32_t *J, int64_t nJ,
