@@ -38,27 +38,27 @@ __device__ __forceinline__ uint64_t sp_key(const uint64_t *K, const int32_t *I, 
   return ((uint64_t)(uint32_t)i << nbj) | (uint64_t)(uint32_t)j;
 }
 
-// digit counts of one tile: cnt[d * ntiles + tile]
+// digit counts of one tile: cnt[d * ntiles + tile].  All of a thread's keys
+// are loaded before any is counted, so its loads are in flight together.
 template <bool FIRST>
 __global__ void __launch_bounds__(SP_NT) k_sp_hist(const uint64_t *K, const int32_t *I, const int32_t *J,
                                                    int64_t nnz, int nbj, int64_t m, int64_t n, int shift,
                                                    int64_t *cnt, int64_t ntiles, int *flag) {
   __shared__ int h[SP_WARPS][SP_RADIX];
   for (int x = threadIdx.x; x < SP_WARPS * SP_RADIX; x += SP_NT) (&h[0][0])[x] = 0;
-  __syncthreads();
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
   const int64_t t0 = (int64_t)blockIdx.x * SP_TILE;
-#pragma unroll 4
+  uint64_t k[SP_IPT];
+#pragma unroll
   for (int it = 0; it < SP_IPT; ++it) {
     const int64_t t = t0 + (int64_t)it * SP_NT + threadIdx.x;
-    const bool ok = t < nnz;
-    const unsigned act = __ballot_sync(FULL, ok);
-    if (ok) {
-      const int d = (int)((sp_key<FIRST>(K, I, J, t, nbj, m, n, flag) >> shift) & (SP_RADIX - 1));
-      const unsigned peers = __match_any_sync(act, d);
-      // one lane per distinct digit adds the group's size: no two lanes touch one counter
-      if (lane == __ffs(peers) - 1) h[w][d] += __popc(peers);
-    }
+    k[it] = t < nnz ? sp_key<FIRST>(K, I, J, t, nbj, m, n, flag) : 0;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < SP_IPT; ++it) {
+    const int64_t t = t0 + (int64_t)it * SP_NT + threadIdx.x;
+    if (t < nnz) atomicAdd(&h[w][(int)((k[it] >> shift) & (SP_RADIX - 1))], 1);
   }
   __syncthreads();
   const int d = threadIdx.x;
@@ -100,18 +100,25 @@ __global__ void __launch_bounds__(SP_NT) k_sp_scatter(const uint64_t *Kin, const
   uint64_t k[SP_IPT];
   VT v[SP_IPT];
   int r[SP_IPT];
-  // warp w ranks the tile's items w*512 .. w*512+511 in order, 32 at a time
+  // warp w ranks the tile's items w*512 .. w*512+511 in order, 32 at a time;
+  // every load is issued before the first ranking step
+#pragma unroll
+  for (int it = 0; it < SP_IPT; ++it) {
+    const int e = w * (SP_IPT * 32) + it * 32 + lane;
+    k[it] = 0;
+    v[it] = 0;
+    if (e < nt) {
+      k[it] = sp_key<FIRST>(Kin, I, J, t0 + e, nbj, m, n, flag);
+      if (VB) v[it] = reinterpret_cast<const VT *>(Vin)[t0 + e];
+    }
+  }
 #pragma unroll
   for (int it = 0; it < SP_IPT; ++it) {
     const int e = w * (SP_IPT * 32) + it * 32 + lane;
     const bool ok = e < nt;
-    k[it] = 0;
-    v[it] = 0;
     r[it] = 0;
     const unsigned act = __ballot_sync(FULL, ok);
     if (ok) {
-      k[it] = sp_key<FIRST>(Kin, I, J, t0 + e, nbj, m, n, flag);
-      if (VB) v[it] = reinterpret_cast<const VT *>(Vin)[t0 + e];
       const int d = (int)((k[it] >> shift) & (SP_RADIX - 1));
       const unsigned peers = __match_any_sync(act, d);
       const int base = wcnt[w * SP_RADIX + d];
@@ -208,7 +215,11 @@ template <> struct SpOp<5> {
   static __device__ T add(T a, T) { return a; }
 };
 
-// one column id and one value per run; row counts into rowcnt[row + 1]
+// one column id and one value per run; row counts into rowcnt[row + 1].
+// Thread x owns the 16 sorted tuples x*16 .. x*16+15 of the tile and every
+// run that starts among them; keys and values are loaded once, runs are
+// folded in registers, and only a run that continues past the thread's last
+// tuple reads further (up to SP_SHORT tuples, longer ones go to k_sp_long).
 template <int OP>
 __global__ void __launch_bounds__(SP_NT) k_sp_emit(const uint64_t *K, const void *Vs, int64_t nnz, int nbj,
                                                    const int64_t *theads_incl, int32_t *Cidx, void *Cval,
@@ -220,7 +231,9 @@ __global__ void __launch_bounds__(SP_NT) k_sp_emit(const uint64_t *K, const void
   const int64_t t0 = (int64_t)blockIdx.x * SP_TILE + (int64_t)threadIdx.x * SP_IPT;
   const uint64_t maskj = nbj ? ((1ull << nbj) - 1ull) : 0ull;
   uint64_t k[SP_IPT];
-  if (t0 + SP_IPT <= nnz) {  // 128 contiguous bytes per thread
+  T v[SP_IPT];
+  const bool full = t0 + SP_IPT <= nnz;
+  if (full) {  // 128 contiguous key bytes per thread
     const uint4 *src = reinterpret_cast<const uint4 *>(K + t0);
 #pragma unroll
     for (int q = 0; q < SP_IPT / 2; ++q) {
@@ -231,6 +244,10 @@ __global__ void __launch_bounds__(SP_NT) k_sp_emit(const uint64_t *K, const void
   } else {
 #pragma unroll
     for (int e = 0; e < SP_IPT; ++e) k[e] = t0 + e < nnz ? K[t0 + e] : 0;
+  }
+  if (HAS_VAL) {
+#pragma unroll
+    for (int e = 0; e < SP_IPT; ++e) v[e] = t0 + e < nnz ? V[t0 + e] : T{};
   }
   const uint64_t prev = (t0 > 0 && t0 <= nnz) ? K[t0 - 1] : 0;
   unsigned heads = 0;
@@ -248,35 +265,55 @@ __global__ void __launch_bounds__(SP_NT) k_sp_emit(const uint64_t *K, const void
   int64_t p = blockIdx.x ? theads_incl[blockIdx.x - 1] : 0;
   for (int ww = 0; ww < SP_WARPS; ++ww) p += ww < w ? ws[ww] : 0;
   p += incl - c;
+  if (!heads) return;
+  const int nv = full ? SP_IPT : (int)(nnz - t0);
   int64_t cur_row = -1;
   int rc = 0;
+  T acc{};
+  int run_len = 0;     // tuples folded into acc
+  int64_t run_p = -1;  // output slot of the open run
+  uint64_t last = 0;   // key of the thread's last tuple
 #pragma unroll
   for (int e = 0; e < SP_IPT; ++e) {
-    if (!((heads >> e) & 1u)) continue;
-    const int64_t t = t0 + e;
-    const int64_t row = (int64_t)(k[e] >> nbj);
-    Cidx[p] = (int32_t)(k[e] & maskj);
-    if (HAS_VAL) {
-      T acc = V[t];
-      int64_t q = t + 1;
-      while (q < nnz && q - t < SP_SHORT && K[q] == k[e]) acc = SpOp<OP>::add(acc, V[q++]);
-      if (q < nnz && q - t == SP_SHORT && K[q] == k[e]) {
-        const int at = atomicAdd(nlong, 1);  // at most nnz / (SP_SHORT + 1) runs qualify
-        longlist[2 * at] = t;
-        longlist[2 * at + 1] = p;
-      } else {
-        reinterpret_cast<T *>(Cval)[p] = acc;
+    if (e < nv) {
+      last = k[e];
+      if ((heads >> e) & 1u) {
+        if (HAS_VAL && run_p >= 0) reinterpret_cast<T *>(Cval)[run_p] = acc;
+        const int64_t row = (int64_t)(k[e] >> nbj);
+        Cidx[p] = (int32_t)(k[e] & maskj);
+        if (row != cur_row) {
+          if (rc) atomicAdd(reinterpret_cast<unsigned long long *>(rowcnt + cur_row + 1), (unsigned long long)rc);
+          cur_row = row;
+          rc = 0;
+        }
+        ++rc;
+        if (HAS_VAL) {
+          acc = v[e];
+          run_len = 1;
+          run_p = p;
+        }
+        ++p;
+      } else if (HAS_VAL && run_p >= 0) {
+        acc = SpOp<OP>::add(acc, v[e]);
+        ++run_len;
       }
     }
-    if (row != cur_row) {
-      if (rc) atomicAdd(reinterpret_cast<unsigned long long *>(rowcnt + cur_row + 1), (unsigned long long)rc);
-      cur_row = row;
-      rc = 0;
-    }
-    ++rc;
-    ++p;
   }
   if (rc) atomicAdd(reinterpret_cast<unsigned long long *>(rowcnt + cur_row + 1), (unsigned long long)rc);
+  if (HAS_VAL) {
+    // the last run may continue into the next threads' tuples
+    const uint64_t key = last;
+    const int64_t start = t0 + nv - run_len;
+    int64_t q = t0 + nv;
+    while (q < nnz && q - start < SP_SHORT && K[q] == key) acc = SpOp<OP>::add(acc, V[q++]);
+    if (q < nnz && q - start == SP_SHORT && K[q] == key) {
+      const int at = atomicAdd(nlong, 1);  // at most nnz / (SP_SHORT + 1) runs qualify
+      longlist[2 * at] = start;
+      longlist[2 * at + 1] = run_p;
+    } else {
+      reinterpret_cast<T *>(Cval)[run_p] = acc;
+    }
+  }
 }
 
 // runs longer than SP_SHORT: one warp each; lane l folds the l-th of 32

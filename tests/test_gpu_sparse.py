@@ -1,11 +1,13 @@
 """GPU sparse(i, j, v, m, n) (hs_sparse through the C ABI) against the CPU oracle.
 
 Structure, integer sums, minima and bool results are compared bit for bit;
-floating-point sums, which the GPU forms in the value type in an unspecified
-order, within TOL[dtype] x (sum of |v| over the entry's tuples) per entry.
-Shapes span every row bin: rows with a single tuple, rows of a few hundred
-tuples, rows of tens of thousands (the heavy bin), and the R-MAT edge lists
-of the paper's graph experiments (power-law rows, repeated edges).
+floating-point sums, which the GPU forms in the value type (in input order,
+runs of more than 32 tuples in 32 ordered slices), within TOL[dtype] x (sum
+of |v| over the entry's tuples) per entry.  Shapes cover positions named
+once, runs folded by one thread, runs of hundreds to 100000 tuples folded by a
+warp, mostly distinct tuples with many empty rows, keys of 0 to 40 bits, and
+the R-MAT edge lists of the paper's graph experiments (power-law rows,
+repeated edges).
 """
 from __future__ import annotations
 
@@ -42,8 +44,11 @@ def check(i, j, v, m, n, sr, dt, what):
     (300, 250, 5000),       # mixed
     (50000, 40000, 30000),  # mostly distinct, many empty rows
     (1000, 3, 20000),       # three columns: long runs of one position
-    (5, 70000, 100000),     # five rows of ~20000 tuples (heavy bin)
+    (5, 70000, 100000),     # five rows of ~20000 tuples
     (1, 1, 1),
+    (2, 2, 5000),           # four positions of ~1250 tuples (runs folded by a warp each)
+    (3, 40, 20000),         # 120 positions of ~170 tuples
+    (1, 1, 100000),         # one position
 ])
 def test_sparse_random(sr, dt, m, n, nnz):
     i, j, v = I.random_tuples(m, n, nnz, seed=m + n + nnz, dtype=dt)
