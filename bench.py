@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target length of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default row-bin thresholds")
-    ap.add_argument("--workload", default="rmat", choices=["rmat", "batched", "serving", "sparse"],
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "batched", "serving", "sparse", "tallskinny", "spref"],
                     help="rmat: the headline product; batched: 2000 independent ER products, "
                          "one batched call against one call per problem")
     ap.add_argument("--batch", type=int, default=2000)
@@ -370,6 +370,139 @@ def run_serving(args):
     print(json.dumps(out), flush=True)
 
 
+# -------------------------------------------------------------------- SpRef
+def run_spref(args):
+    """The paper's two SpRef experiments on the R-MAT matrix of scale --scale
+    (edge factor 8, f32): E1 the random symmetric permutation B = A(p, p);
+    E2 ten induced subgraphs A(r_i, r_i), r_1..r_10 the chunks of a random
+    permutation, extracted one after another.  value: entries of B produced
+    per second in E1."""
+    import torch
+
+    from paper_1109_3739_gb300 import hspgemm as h
+    from paper_1109_3739_gb300 import inputs as I
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    A = I.rmat_matrix(args.scale, 8, seed=2, dtype="f32")
+    dA = h.DeviceCSR.from_host(A, device=dev)
+    n = A.n
+    perm = I.random_permutation(n, seed=12, stream=20).astype(np.int32)
+    dp = torch.from_numpy(perm).to(dev)
+    chunks = [dp[c * n // 10:(c + 1) * n // 10] for c in range(10)]
+    hbm, peak_kind = peaks()
+
+    def timed(fn):
+        out = None
+        for _ in range(args.warmup):
+            out = None
+            out = fn()
+        torch.cuda.synchronize(dev)
+        l0 = h.launch_count()
+        ts = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            out = None
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts), out, (h.launch_count() - l0) // args.steps
+
+    t1, B1, l1 = timed(lambda: h.spref(dA, dp, dp, stream=stream))
+    nnz1 = B1.nnz
+    B1 = None
+    t2, B2, l2 = timed(lambda: [h.spref(dA, r, r, stream=stream) for r in chunks])
+    nnz2 = sum(b.nnz for b in B2)
+    B2 = None
+    # algorithmic bytes of E1: read A once (offsets, columns, values), write B once
+    alg1 = (n + 1) * 8 * 2 + A.nnz * 8 + nnz1 * 8
+    print(json.dumps({
+        "metric": "spref_entries_per_s", "value": nnz1 / (t1 / 1000.0), "unit": "entries/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t1, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"spref_rmat{args.scale}_ef8_f32", "nnz_A": A.nnz,
+                   "l2": "flushed between steps (512 MB write)"},
+        "random_symmetric_permutation": {"ms": t1, "nnz_B": nnz1, "gpu_launches": l1,
+                                         "step_hbm_fraction": alg1 / (t1 / 1000.0) / 1e9 / hbm,
+                                         "peak_kind": peak_kind},
+        "ten_induced_subgraphs": {"ms": t2, "nnz_total": nnz2, "gpu_launches": l2,
+                                  "entries_per_s": nnz2 / (t2 / 1000.0)},
+        "gpu_launches": l1,
+    }), flush=True)
+
+
+# -------------------------------------------------------------- tall-skinny
+def run_tallskinny(args):
+    """C = A*B with A the R-MAT matrix (scale --scale, 8 nonzeros per column,
+    f32) and B an n x (n/8192) Erdos-Renyi matrix with d2 = 1, 10, ..., 10^5
+    nonzeros per column: the multi-source breadth-first-search products of the
+    paper's last experiment, at the paper's aspect ratio.  One line; value is
+    the d2 = 10^5 product's rate, every d2 is listed."""
+    import torch
+
+    from paper_1109_3739_gb300 import hspgemm as h
+    from paper_1109_3739_gb300 import inputs as I
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    A = I.rmat_matrix(args.scale, 8, seed=2, dtype="f32")
+    dA = h.DeviceCSR.from_host(A, device=dev)
+    n = A.n
+    k = max(1, n // 8192)
+    hbm, peak_kind = peaks()
+    runs = []
+    for d2 in (1, 10, 100, 1000, 10000, 100000):
+        if d2 > n:
+            break
+        B = I.er_matrix(n, k, d2, seed=3, dtype="f32")
+        deg_b = np.diff(B.rowptr)
+        flops = int(deg_b[A.col].sum())
+        dB = h.DeviceCSR.from_host(B, device=dev)
+        C = None
+        for _ in range(args.warmup):
+            C = None
+            C = h.spgemm("plus_times", dA, dB, stream=stream)
+        torch.cuda.synchronize(dev)
+        nnz_c = C.nnz
+        C = None
+        l0 = h.launch_count()
+        h.profile_enable(True)
+        h.profile_reset()
+        ts = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            C = h.spgemm("plus_times", dA, dB, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            C = None
+        phases = {k_: round(v_[0] / args.steps, 4) for k_, v_ in h.profile_read().items()}
+        h.profile_enable(False)
+        launches = (h.launch_count() - l0) // args.steps
+        med = statistics.median(ts)
+        alg = (A.nnz + B.nnz + nnz_c) * 8 + (A.m + B.m + A.m + 3) * 8
+        runs.append({"d2": d2, "k": k, "nnz_B": B.nnz, "flops_mults": flops, "nnz_C": nnz_c, "ms": med,
+                     "mults_per_s": flops / (med / 1000.0), "gpu_launches": launches,
+                     "step_hbm_fraction": alg / (med / 1000.0) / 1e9 / hbm, "phases_ms": phases})
+        dB = B = None
+    last = runs[-1]
+    print(json.dumps({
+        "metric": METRIC, "value": last["mults_per_s"], "unit": "mults/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": last["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"tallskinny_rmat{args.scale}_ef8_x_er_n_by_{k}", "nnz_A": A.nnz,
+                   "aspect_n_over_k": 8192, "l2": "flushed between steps (512 MB write)", "peak_kind": peak_kind},
+        "per_d2": runs, "gpu_launches": last["gpu_launches"],
+    }), flush=True)
+
+
 # ------------------------------------------------------------------ sparse()
 def run_sparse(args):
     """sparse(i, j, v, n, n) of the raw R-MAT edge list (scale --scale, 16 edges
@@ -461,6 +594,10 @@ def main():
         return run_serving(args)
     if args.workload == "sparse":
         return run_sparse(args)
+    if args.workload == "tallskinny":
+        return run_tallskinny(args)
+    if args.workload == "spref":
+        return run_spref(args)
     import torch
 
     from paper_1109_3739_gb300 import hspgemm as h

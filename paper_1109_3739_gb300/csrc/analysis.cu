@@ -93,6 +93,114 @@ void launch_flops(const RowSet &A, const RightOp &B, int64_t *f, int *key_cnt, u
   k_flops<<<grid_for(A.nslots, 8, 16), 256, 0, st>>>(A, B, f, key_cnt, stats, bins);
 }
 
+// ------------------------------------------------ flat products per entry
+// The same counts, computed per A entry instead of per row, so that no row
+// is walked by one warp: s[q - lo] = nnz(B(A.j[q], :)) for q in [lo, hi) =
+// [A.p[0], A.p[nslots]); zeros[0] counts the entries whose B row is empty
+// (they make no product).  After an inclusive scan S of s, a row's count is
+// S[q1 - 1 - lo] - S[q0 - 1 - lo].
+__global__ void k_entry_flops(RowSet A, RightOp B, int64_t *s, unsigned long long *zeros) {
+  // offsets are trusted only as far as s's length (A.nnz entries)
+  const int64_t lo = A.p[0], hi = min(A.p[A.nslots], lo + A.nnz);
+  int z = 0;
+  for (int64_t q = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < hi;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int k = A.j[q];
+    const int64_t v = HS_G(A.dbg, k >= 0 && k < B.m, 52, k) ? B.p[k + 1] - B.p[k] : 0;
+    s[q - lo] = v;
+    z += v == 0;
+  }
+  z = warp_sum(z);
+  if (lane_id() == 0 && z) atomicAdd(zeros, (unsigned long long)z);
+}
+
+// thread per row: f from the scanned entry counts, then the row's key and
+// the statistics k_flops gathers
+__global__ void k_row_flops(RowSet A, const int64_t *S, int64_t *f, int *key_cnt, unsigned long long *stats,
+                            BinCfg bins, int64_t bn) {
+  __shared__ int hist[NKEYS];
+  for (int i = threadIdx.x; i < NKEYS; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
+  const int64_t lo = A.p[0], len = min(A.p[A.nslots] - lo, A.nnz);
+  unsigned long long my_tot = 0, my_max = 0, my_amax = 0, my_heavy = 0;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < A.nslots;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q0 = min(max(A.p[r] - lo, (int64_t)0), len), q1 = min(max(A.p[r + 1] - lo, (int64_t)0), len);
+    const int64_t fr = q1 > q0 ? S[q1 - 1] - (q0 > 0 ? S[q0 - 1] : 0) : 0;
+    f[r] = fr;
+    const int key = sym_key(fr, bins);
+    if (key) atomicAdd(hist + key, 1);
+    if (key >= KEY_HEAVY) my_heavy += (unsigned long long)min(fr, bn);
+    my_tot += (unsigned long long)fr;
+    my_max = max(my_max, (unsigned long long)fr);
+    my_amax = max(my_amax, (unsigned long long)(q1 - q0));
+  }
+  my_tot = warp_sum(my_tot);
+  my_heavy = warp_sum(my_heavy);
+  my_max = warp_max(my_max);
+  my_amax = warp_max(my_amax);
+  if (lane_id() == 0) {
+    if (my_tot) atomicAdd(stats + 0, my_tot);
+    atomicMax(stats + 1, my_max);
+    atomicMax(stats + 2, my_amax);
+    if (my_heavy) atomicAdd(stats + 3, my_heavy);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < NKEYS; i += blockDim.x)
+    if (hist[i]) atomicAdd(key_cnt + i, hist[i]);
+}
+
+void launch_entry_flops(const RowSet &A, const RightOp &B, int64_t *s, unsigned long long *zeros,
+                        cudaStream_t st) {
+  if (A.nslots == 0 || A.nnz == 0) return;
+  count_launch();
+  k_entry_flops<<<grid_for(A.nnz, 256, 8), 256, 0, st>>>(A, B, s, zeros);
+}
+void launch_row_flops(const RowSet &A, const int64_t *S, int64_t *f, int *key_cnt, unsigned long long *stats,
+                      const BinCfg &bins, int64_t bn, cudaStream_t st) {
+  if (A.nslots == 0) return;
+  count_launch();
+  k_row_flops<<<grid_for(A.nslots, 256, 8), 256, 0, st>>>(A, S, f, key_cnt, stats, bins, bn);
+}
+
+// Dropping the A entries whose B row is empty (their products are none, so
+// C is unchanged): keep[q - lo] = 1 where s > 0, recovered from the scanned
+// counts; after an inclusive scan K of keep, entry q goes to K[q - lo] - 1
+// and row r starts at K[A.p[r] - 1 - lo].
+__global__ void k_keep_flags(RowSet A, const int64_t *S, int64_t *keep) {
+  const int64_t n = min(A.p[A.nslots] - A.p[0], A.nnz);
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
+    keep[x] = (S[x] - (x > 0 ? S[x - 1] : 0)) > 0;
+}
+__global__ void k_compact_entries(RowSet A, const int64_t *K, int32_t *j2, void *v2, int vb) {
+  const int64_t lo = A.p[0], n = min(A.p[A.nslots] - lo, A.nnz);
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t before = x > 0 ? K[x - 1] : 0;
+    if (K[x] == before) continue;
+    j2[before] = A.j[lo + x];
+    if (vb == 8) reinterpret_cast<uint64_t *>(v2)[before] = reinterpret_cast<const uint64_t *>(A.v)[lo + x];
+    else if (vb == 4) reinterpret_cast<uint32_t *>(v2)[before] = reinterpret_cast<const uint32_t *>(A.v)[lo + x];
+  }
+}
+__global__ void k_compact_offsets(RowSet A, const int64_t *K, int64_t *p2) {
+  const int64_t lo = A.p[0], n = min(A.p[A.nslots] - lo, A.nnz);
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r <= A.nslots;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = min(max(A.p[r] - lo, (int64_t)0), n);
+    p2[r] = x > 0 ? K[x - 1] : 0;
+  }
+}
+void launch_compact_a(const RowSet &A, const int64_t *S, int64_t *keep, int64_t *scan_tmp, int32_t *j2, void *v2,
+                      int vb, int64_t *p2, cudaStream_t st) {
+  count_launch();
+  k_keep_flags<<<grid_for(A.nnz, 256, 8), 256, 0, st>>>(A, S, keep);
+  launch_scan_i64(keep, A.nnz, scan_tmp, st);
+  count_launch();
+  k_compact_entries<<<grid_for(A.nnz, 256, 8), 256, 0, st>>>(A, keep, j2, v2, vb);
+  count_launch();
+  k_compact_offsets<<<grid_for(A.nslots + 1, 256, 8), 256, 0, st>>>(A, keep, p2);
+}
+
 // ---------------------------------------------------- B segment index
 // One warp per B row.  Rows longer than min_len take the next table row and
 // record, for every segment g = 0..nseg, the offset of their first entry with

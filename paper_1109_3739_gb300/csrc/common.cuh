@@ -159,6 +159,11 @@ __device__ __forceinline__ int warp_max(int v) {
   for (int d = 16; d >= 1; d >>= 1) v = max(v, __shfl_xor_sync(FULL, v, d));
   return v;
 }
+__device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) v = max(v, __shfl_xor_sync(FULL, v, d));
+  return v;
+}
 
 // Exclusive scan of a[0..n) in shared memory by a whole group; returns the
 // total.  tmp needs 33 ints (CTA groups only).

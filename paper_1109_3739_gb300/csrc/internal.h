@@ -114,6 +114,14 @@ template <class K> inline void set_smem_attr(K kernel, size_t bytes) {
 // min(f, n) over the rows of the symbolic heavy bin (their list pool bound)
 void launch_flops(const RowSet &A, const RightOp &B, int64_t *f, int *key_cnt, unsigned long long *stats,
                   const BinCfg &bins, cudaStream_t st);
+// per-entry product counts (s over A's entries, zeros: entries with an
+// empty B row), the row counts and keys from their inclusive scan S, and the
+// copy of A without the zero entries (p2: nslots+1 offsets from 0)
+void launch_entry_flops(const RowSet &A, const RightOp &B, int64_t *s, unsigned long long *zeros, cudaStream_t st);
+void launch_row_flops(const RowSet &A, const int64_t *S, int64_t *f, int *key_cnt, unsigned long long *stats,
+                      const BinCfg &bins, int64_t bn, cudaStream_t st);
+void launch_compact_a(const RowSet &A, const int64_t *S, int64_t *keep, int64_t *scan_tmp, int32_t *j2, void *v2,
+                      int vb, int64_t *p2, cudaStream_t st);
 void launch_key_offsets(const int *key_cnt, int *key_off, int *key_cur, cudaStream_t st);
 // rows with more than cap_large products get a column-segment histogram slot
 void launch_scatter_sym(const RowSet &A, const int64_t *f, int *key_cur, int *list, int32_t *hslot,
@@ -201,15 +209,18 @@ void launch_mark_positions(const int32_t *X, int64_t n, int64_t bound, int32_t *
 void launch_fill_i32(int32_t *a, int64_t n, int32_t v, cudaStream_t st);
 
 // sparse.cu: sparse(i, j, v, m, n) by a stable radix sort of (row, column)
-// keys.  Tiles of sp_tiles(nnz); digit tables of 256 * tiles entries.
+// keys.  Tiles of sp_tiles(nnz); look-back status of 256 words per tile.
 int64_t sp_tiles(int64_t nnz);
 int sp_radix_bits();
 int64_t sp_long_capacity(int64_t nnz);  // runs longer than the emit kernel folds alone
-void launch_sp_hist(bool first, const uint64_t *K, const int32_t *I, const int32_t *J, int64_t nnz, int nbj,
-                    int64_t m, int64_t n, int shift, int64_t *cnt, int64_t ntiles, int *flag, cudaStream_t st);
-void launch_sp_scatter(bool first, int vb, const uint64_t *Kin, const int32_t *I, const int32_t *J, const void *Vin,
-                       int64_t nnz, int nbj, int64_t m, int64_t n, int shift, const int64_t *cnt_incl,
-                       int64_t ntiles, uint64_t *Kout, void *Vout, int *flag, cudaStream_t st);
+int sp_max_passes();
+// flag bit 1: an index out of range; bit 2: a look-back wait expired
+void launch_sp_allhist(const int32_t *I, const int32_t *J, int64_t nnz, int nbj, int64_t m, int64_t n, int passes,
+                       unsigned long long *ghist, int *flag, cudaStream_t st);
+void launch_sp_pass(int vb, const uint64_t *Kin, const int32_t *I, const int32_t *J, const void *Vin, int64_t nnz,
+                    int nbj, int64_t m, int64_t n, int pass, const unsigned long long *ghist,
+                    unsigned long long *status, int *ticket, int64_t ntiles, uint64_t *Kout, void *Vout, int *flag,
+                    cudaStream_t st);
 void launch_sp_heads(const uint64_t *K, int64_t nnz, int64_t *theads, int64_t ntiles, cudaStream_t st);
 // op: 0 (+) f64, 1 (+) f32, 2 (+) i64, 3 min f32, 4 min i32, 5 structure only
 void launch_sp_emit(int op, const uint64_t *K, const void *V, int64_t nnz, int nbj, const int64_t *theads_incl,

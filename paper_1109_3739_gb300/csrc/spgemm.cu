@@ -242,6 +242,7 @@ struct SmallBlock {  // device counters, read back in one copy
   int bci_cnt;               // B segment index rows handed out
   int pad2;
   long long nnz;
+  unsigned long long zeros;  // A entries whose B row is empty
   long long dbg[2];  // guarded builds: first failed check (code, index)
 };
 
@@ -417,13 +418,27 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
   if (!hb) return HS_ECUDA;
   CK(cudaMemsetAsync(sb, 0, sizeof(SmallBlock), st));
 
+  // product counts per A entry and their scan: every row's count without a
+  // warp walking the row (optional scratch; without it, one warp per row)
+  int64_t *es = (int64_t *)mem.raw(sizeof(int64_t) * (size_t)A->nnz);
+  int64_t *es_tmp = es ? (int64_t *)mem.raw(sizeof(int64_t) * (size_t)scan_tmp_elems(A->nnz)) : nullptr;
+  if (es) mem.scratch.push_back({es, sizeof(int64_t) * (size_t)A->nnz});
+  if (es_tmp) mem.scratch.push_back({es_tmp, sizeof(int64_t) * (size_t)scan_tmp_elems(A->nnz)});
+  mem.failed = false;
+  const bool flat = es && es_tmp;
   {
     PhaseTimer t("analysis", st);
     if (flags & HS_FLAG_VALIDATE) {
       launch_validate(A->ptr, A->idx, nslots, A->n, &sb->valflag, st);
       launch_validate(B->ptr, B->idx, B->m, B->n, &sb->valflag, st);
     }
-    launch_flops(rs, rb, f, sb->key_cnt, sb->stats, bins, st);
+    if (flat) {
+      launch_entry_flops(rs, rb, es, &sb->zeros, st);
+      launch_scan_i64(es, A->nnz, es_tmp, st);
+      launch_row_flops(rs, es, f, sb->key_cnt, sb->stats, bins, B->n, st);
+    } else {
+      launch_flops(rs, rb, f, sb->key_cnt, sb->stats, bins, st);
+    }
     launch_key_offsets(sb->key_cnt, sb->key_off, sb->key_cur, st);
     launch_scatter_sym(rs, f, sb->key_cur, list, hslot, &sb->nhist, bins, st);
   }
@@ -438,6 +453,31 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
   memcpy(key_off, hb->key_off, sizeof(key_off));
   const int nhist = hb->nhist;
   const int nseg = (int)((n + SEG_W - 1) / SEG_W);
+
+  // A entries whose B row is empty make no products.  When they are most of
+  // a large A (a very sparse B, as in the tall-skinny products of Section 4),
+  // the passes below read a copy of A without them: rows keep their product
+  // counts, bins and results, and a long row of A with few products no longer
+  // costs a walk over all its entries.  Not for plans, whose execute reads A's
+  // values in place.
+  if (flat && !plan && A->nnz >= (1 << 20) && hb->zeros * 2 > (unsigned long long)A->nnz) {
+    const int64_t kept = A->nnz - (int64_t)hb->zeros;
+    const int va = A->val ? vbytes_of(A->dtype) : 0;
+    int64_t *keep = mem.tmp<int64_t>((size_t)A->nnz);
+    int32_t *j2 = mem.tmp<int32_t>((size_t)(kept > 0 ? kept : 1));
+    void *v2 = va ? (void *)mem.tmp<char>((size_t)va * (size_t)(kept > 0 ? kept : 1)) : nullptr;
+    int64_t *p2 = mem.tmp<int64_t>((size_t)nslots + 1);
+    if (!mem.failed) {
+      PhaseTimer t("compact_a", st);
+      launch_compact_a(rs, es, keep, es_tmp, j2, v2, va, p2, st);
+      rs.p = p2;
+      rs.j = j2;
+      rs.v = v2;
+      rs.nnz = kept;
+      if (int e = phase_check("compact_a", st, sb->dbg)) return e;
+    }
+    mem.failed = false;
+  }
 
   uint32_t *hist = nullptr;
   if (nhist > 0) {
@@ -724,17 +764,19 @@ static int sparse_impl(const int32_t *I, const int32_t *J, const void *V, int64_
   const int rb = sp_radix_bits();
   int passes = (nbi + nbj + rb - 1) / rb;
   if (passes < 1) passes = 1;
+  if (passes > sp_max_passes()) return HS_EINTERNAL;
   const int64_t tiles = sp_tiles(nnz);
-  const int64_t table = tiles << rb;
   const int64_t longcap = sp_long_capacity(nnz);
-  int64_t scan_n = table > m + 1 ? table : m + 1;
+  const int64_t scan_n = tiles > m + 1 ? tiles : m + 1;
   uint64_t *kbuf[2] = {mem.tmp<uint64_t>((size_t)nnz), mem.tmp<uint64_t>((size_t)nnz)};
   void *vbuf[2] = {nullptr, nullptr};
   if (vb) {
     vbuf[0] = mem.tmp<char>((size_t)nnz * vb);
     vbuf[1] = mem.tmp<char>((size_t)nnz * vb);
   }
-  int64_t *cnt = mem.tmp<int64_t>((size_t)table);
+  unsigned long long *status = mem.tmp<unsigned long long>((size_t)(tiles << rb));
+  unsigned long long *ghist = mem.tmp<unsigned long long>((size_t)passes << rb);
+  int *ticket = mem.tmp<int>((size_t)passes);
   int64_t *theads = mem.tmp<int64_t>((size_t)tiles);
   int64_t *scan_tmp = mem.tmp<int64_t>((size_t)scan_tmp_elems(scan_n));
   int64_t *longlist = vb ? mem.tmp<int64_t>((size_t)(2 * longcap)) : nullptr;
@@ -742,18 +784,20 @@ static int sparse_impl(const int32_t *I, const int32_t *J, const void *V, int64_
   int64_t *host = (int64_t *)pinned(16);
   if (mem.failed || !host) return HS_ENOMEM;
   CK(cudaMemsetAsync(flags, 0, 8, st));
+  CK(cudaMemsetAsync(status, 0, sizeof(unsigned long long) * (size_t)(tiles << rb), st));
+  CK(cudaMemsetAsync(ghist, 0, sizeof(unsigned long long) * ((size_t)passes << rb), st));
+  CK(cudaMemsetAsync(ticket, 0, sizeof(int) * (size_t)passes, st));
   int cur = 0;
   {
     PhaseTimer t("sparse_sort", st);
+    launch_sp_allhist(I, J, nnz, nbj, m, n, passes, ghist, flags, st);
     for (int p = 0; p < passes; ++p) {
       const bool first = p == 0;
       const uint64_t *kin = first ? nullptr : kbuf[cur];
       const void *vin = first ? V : vbuf[cur];
       const int out = first ? 0 : cur ^ 1;
-      launch_sp_hist(first, kin, I, J, nnz, nbj, m, n, p * rb, cnt, tiles, flags, st);
-      launch_scan_i64(cnt, table, scan_tmp, st);
-      launch_sp_scatter(first, vb, kin, I, J, vin, nnz, nbj, m, n, p * rb, cnt, tiles, kbuf[out], vbuf[out],
-                        flags, st);
+      launch_sp_pass(vb, kin, I, J, vin, nnz, nbj, m, n, p, ghist + ((size_t)p << rb), status, ticket + p, tiles,
+                     kbuf[out], vbuf[out], flags, st);
       cur = out;
     }
     launch_sp_heads(kbuf[cur], nnz, theads, tiles, st);
@@ -763,7 +807,9 @@ static int sparse_impl(const int32_t *I, const int32_t *J, const void *V, int64_
   CK(cudaMemcpyAsync(host, theads + tiles - 1, 8, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(host + 1, flags, 4, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  if (*(int *)(host + 1)) return HS_EINVAL;
+  const int fl = *(int *)(host + 1);
+  if (fl & 1) return HS_EINVAL;
+  if (fl & 2) return HS_ETIMEDOUT;
   const int64_t U = host[0];
   C->nnz = U;
   C->idx = (int32_t *)outmem.raw(sizeof(int32_t) * (size_t)U);
