@@ -93,6 +93,119 @@ void launch_sort_short_rows(const int64_t *ptr, int32_t *j, int64_t rows, cudaSt
   }
 }
 
+// ----------------------------------------------------- SpRef by gathering
+// B = A(I, J) without forming R*A: the rows I[t] of A are laid end to end
+// (gathered entry g of output row t is entry A.p[I[t]] + g - G[t] of A,
+// G the scanned row lengths), every gathered entry (t, c, v) becomes one
+// tuple (t, p, v) for each p with J[p] == c (Q's row c), and the tuples are
+// sorted by (t, p) -- or, when J is strictly increasing, written in place,
+// already in order.
+
+// G[t + 1] = length of row I[t] (G[0] is zero)
+__global__ void k_gather_len(const int64_t *Ap, const int32_t *I, int64_t nI, int64_t *G) {
+  GRID_STRIDE(t, nI) G[t + 1] = Ap[I[t] + 1] - Ap[I[t]];
+}
+// inc[G[t]] += 1 for every row starting inside [0, total): after an
+// inclusive scan, inc[g] - 1 is the output row of gathered entry g
+__global__ void k_row_starts(const int64_t *G, int64_t nI, int64_t total, int64_t *inc) {
+  GRID_STRIDE(t, nI) {
+    const int64_t g = G[t];
+    if (g < total) atomicAdd(reinterpret_cast<unsigned long long *>(inc + g), 1ull);
+  }
+}
+__device__ __forceinline__ void gather_entry(const GatherArgs &a, int64_t g, int64_t &t, int64_t &q, int &c) {
+  t = a.row[g] - 1;
+  q = a.Ap[a.I[t]] + (g - a.G[t]);
+  c = a.Aj[q];
+}
+// W[g] = number of tuples entry g makes (|{p : J[p] == c}|)
+__global__ void k_gather_w(GatherArgs a, int64_t *W) {
+  GRID_STRIDE(g, a.total) {
+    int64_t t, q;
+    int c;
+    gather_entry(a, g, t, q, c);
+    W[g] = (c >= 0 && c < a.ncols) ? a.Qp[c + 1] - a.Qp[c] : 0;
+  }
+}
+__device__ __forceinline__ void copy_val(void *dst, int64_t at, const void *src, int64_t q, int vb) {
+  if (vb == 8) reinterpret_cast<uint64_t *>(dst)[at] = reinterpret_cast<const uint64_t *>(src)[q];
+  else if (vb == 4) reinterpret_cast<uint32_t *>(dst)[at] = reinterpret_cast<const uint32_t *>(src)[q];
+}
+// the tuples, entry g's at [W[g-1], W[g]) of the scanned counts
+__global__ void k_gather_fill(GatherArgs a, const int64_t *W, int32_t *ti, int32_t *pj, void *tv) {
+  GRID_STRIDE(g, a.total) {
+    int64_t t, q;
+    int c;
+    gather_entry(a, g, t, q, c);
+    int64_t at = g > 0 ? W[g - 1] : 0;
+    if (at == W[g]) continue;  // no tuple (and c may be any id)
+    for (int64_t k = a.Qp[c]; k < a.Qp[c + 1]; ++k, ++at) {
+      ti[at] = (int32_t)t;
+      pj[at] = a.Qj[k];
+      copy_val(tv, at, a.Av, q, a.vb);
+    }
+  }
+}
+// J strictly increasing: each entry makes at most one tuple and a row's
+// tuples come out in increasing p, so they are B's entries as they stand
+__global__ void k_gather_direct(GatherArgs a, const int64_t *W, int32_t *Bj, void *Bv) {
+  GRID_STRIDE(g, a.total) {
+    const int64_t before = g > 0 ? W[g - 1] : 0;
+    if (W[g] == before) continue;
+    int64_t t, q;
+    int c;
+    gather_entry(a, g, t, q, c);
+    Bj[before] = a.Qj[a.Qp[c]];
+    copy_val(Bv, before, a.Av, q, a.vb);
+  }
+}
+// B's offsets from the scanned tuple counts: Bp[t] = W[G[t] - 1]
+__global__ void k_gather_offsets(const int64_t *G, int64_t nI, const int64_t *W, int64_t *Bp) {
+  GRID_STRIDE(t, nI + 1) {
+    const int64_t g = G[t];
+    Bp[t] = g > 0 ? W[g - 1] : 0;
+  }
+}
+// flag bit 4: J not strictly increasing
+__global__ void k_check_increasing(const int32_t *X, int64_t n, int *flag) {
+  GRID_STRIDE(i, n - 1) if (X[i] >= X[i + 1]) atomicOr(flag, 4);
+}
+
+void launch_gather_len(const int64_t *Ap, const int32_t *I, int64_t nI, int64_t *G, cudaStream_t st) {
+  if (nI <= 0) return;
+  count_launch();
+  k_gather_len<<<grid1(nI), 256, 0, st>>>(Ap, I, nI, G);
+}
+void launch_row_starts(const int64_t *G, int64_t nI, int64_t total, int64_t *inc, cudaStream_t st) {
+  if (nI <= 0 || total <= 0) return;
+  count_launch();
+  k_row_starts<<<grid1(nI), 256, 0, st>>>(G, nI, total, inc);
+}
+void launch_gather_w(const GatherArgs &a, int64_t *W, cudaStream_t st) {
+  if (a.total <= 0) return;
+  count_launch();
+  k_gather_w<<<grid1(a.total), 256, 0, st>>>(a, W);
+}
+void launch_gather_fill(const GatherArgs &a, const int64_t *W, int32_t *ti, int32_t *pj, void *tv, cudaStream_t st) {
+  if (a.total <= 0) return;
+  count_launch();
+  k_gather_fill<<<grid1(a.total), 256, 0, st>>>(a, W, ti, pj, tv);
+}
+void launch_gather_direct(const GatherArgs &a, const int64_t *W, int32_t *Bj, void *Bv, cudaStream_t st) {
+  if (a.total <= 0) return;
+  count_launch();
+  k_gather_direct<<<grid1(a.total), 256, 0, st>>>(a, W, Bj, Bv);
+}
+void launch_gather_offsets(const int64_t *G, int64_t nI, const int64_t *W, int64_t *Bp, cudaStream_t st) {
+  count_launch();
+  k_gather_offsets<<<grid1(nI + 1), 256, 0, st>>>(G, nI, W, Bp);
+}
+void launch_check_increasing(const int32_t *X, int64_t n, int *flag, cudaStream_t st) {
+  if (n <= 1) return;
+  count_launch();
+  k_check_increasing<<<grid1(n - 1), 256, 0, st>>>(X, n, flag);
+}
+
 // flag bit 1: an index outside [0, bound)
 __global__ void k_check_range(const int32_t *X, int64_t n, int64_t bound, int *flag) {
   GRID_STRIDE(i, n) {
@@ -168,10 +281,6 @@ void launch_iota_i64(int64_t *p, int64_t n, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------ SpAsgn merge
-__device__ __forceinline__ void copy_val(void *dst, int64_t di, const void *src, int64_t si, int vb) {
-  if (vb == 8) reinterpret_cast<unsigned long long *>(dst)[di] = reinterpret_cast<const unsigned long long *>(src)[si];
-  else if (vb == 4) reinterpret_cast<uint32_t *>(dst)[di] = reinterpret_cast<const uint32_t *>(src)[si];
-}
 
 // extend-add collision: x (from A) (+) y (from B) in the semiring's add
 __device__ void combine_val(const AsgnArgs &a, int64_t di, int64_t ai, int64_t xi) {

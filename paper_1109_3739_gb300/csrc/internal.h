@@ -207,6 +207,27 @@ void launch_check_range(const int32_t *X, int64_t n, int64_t bound, int *flag, c
 // pos[X[i]] = i for in-range X[i] (bit 1 of flag: out of range; bit 2: repeated)
 void launch_mark_positions(const int32_t *X, int64_t n, int64_t bound, int32_t *pos, int *flag, cudaStream_t st);
 void launch_fill_i32(int32_t *a, int64_t n, int32_t v, cudaStream_t st);
+// SpRef by gathering the selected rows (index.cu)
+struct GatherArgs {
+  const int64_t *Ap;
+  const int32_t *Aj;
+  const void *Av;
+  int vb;
+  const int32_t *I;
+  const int64_t *G;    // nI + 1 gathered offsets
+  const int64_t *row;  // scanned row starts: row of g = row[g] - 1
+  const int64_t *Qp;   // n + 1
+  const int32_t *Qj;
+  int64_t total;       // gathered entries
+  int64_t ncols;       // columns of A: a column id outside [0, ncols) makes no tuple
+};
+void launch_gather_len(const int64_t *Ap, const int32_t *I, int64_t nI, int64_t *G, cudaStream_t st);
+void launch_row_starts(const int64_t *G, int64_t nI, int64_t total, int64_t *inc, cudaStream_t st);
+void launch_gather_w(const GatherArgs &a, int64_t *W, cudaStream_t st);
+void launch_gather_fill(const GatherArgs &a, const int64_t *W, int32_t *ti, int32_t *pj, void *tv, cudaStream_t st);
+void launch_gather_direct(const GatherArgs &a, const int64_t *W, int32_t *Bj, void *Bv, cudaStream_t st);
+void launch_gather_offsets(const int64_t *G, int64_t nI, const int64_t *W, int64_t *Bp, cudaStream_t st);
+void launch_check_increasing(const int32_t *X, int64_t n, int *flag, cudaStream_t st);
 
 // sparse.cu: sparse(i, j, v, m, n) by a stable radix sort of (row, column)
 // keys.  Tiles of sp_tiles(nnz); look-back status of 256 words per tile.

@@ -675,54 +675,132 @@ template <class F> static int with_output(hs_mat *C, Mem &outmem, F &&fn) {
   return e;
 }
 
+static int sparse_impl(const int32_t *I, const int32_t *J, const void *V, int64_t nnz, int64_t m, int64_t n,
+                       int dtype, int sr, hs_mat *C, Mem &mem, Mem &outmem, uint32_t flags);
+
+// B = A(I, J) (Section 3.1's SpRef), the triple product R*A*Q evaluated
+// without forming R*A: the rows I[t] are gathered end to end, each gathered
+// entry (t, c, v) yields (t, p, v) for every p with J[p] == c (Q's row c),
+// and the tuples are ordered by (t, p) with the radix sort of sparse(); when
+// J is strictly increasing they are in order already and are written out
+// directly.  Four host synchronisations (three with a strictly increasing J).
 static int spref_impl(const hs_mat *A, const int32_t *I, int64_t nI, const int32_t *J, int64_t nJ, hs_mat *Bout,
                       Mem &mem, Mem &outmem, uint32_t flags) {
   cudaStream_t st = mem.st;
   if (!A || !Bout || A->fmt != HS_CSR || nI < 0 || nJ < 0) return HS_EINVAL;
   if ((nI > 0 && !I) || (nJ > 0 && !J)) return HS_EINVAL;
   if (nI > 0x7fffffffLL || nJ > 0x7fffffffLL) return HS_EUNSUPPORTED;
-  // index ranges are always checked: they address A's rows and columns
+  if (!dtype_ok(A->dtype) || (A->m > 0 && !A->ptr)) return HS_EINVAL;
+  if (A->dtype != HS_BOOL && A->nnz > 0 && !A->val) return HS_EINVAL;
+  const int vb = A->dtype == HS_BOOL ? 0 : vbytes_of(A->dtype);
+  const int64_t n = A->n;
   int *flag = mem.tmp<int>(2);
-  int *hflag = (int *)pinned(8);
-  if (!flag || !hflag) return HS_ENOMEM;
+  int64_t *hbuf = (int64_t *)pinned(32);
+  int64_t *Qp = mem.tmp<int64_t>(n + 1);
+  int64_t *Qcur = mem.tmp<int64_t>(n + 1);
+  int32_t *Qj = mem.tmp<int32_t>(nJ > 0 ? nJ : 1);
+  int64_t *G = mem.tmp<int64_t>(nI + 1);
+  int64_t *scan_tmp = mem.tmp<int64_t>(scan_tmp_elems((n + 1) > (nI + 1) ? (n + 1) : (nI + 1)));
+  if (mem.failed || !hbuf) return HS_ENOMEM;
+  // index ranges are always checked, and before any kernel uses I or J as
+  // an address: they index A's rows, Q's rows and the gathered offsets
   CK(cudaMemsetAsync(flag, 0, 8, st));
   launch_check_range(I, nI, A->m, flag, st);
-  launch_check_range(J, nJ, A->n, flag, st);
-  CK(cudaMemcpyAsync(hflag, flag, 8, cudaMemcpyDeviceToHost, st));
+  launch_check_range(J, nJ, n, flag, st);
+  launch_check_increasing(J, nJ, flag, st);
+  if (flags & HS_FLAG_VALIDATE) launch_validate(A->ptr, A->idx, A->m, A->n, flag + 1, st);
+  CK(cudaMemcpyAsync(hbuf, flag, 8, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  if (hflag[0]) return HS_EINVAL;
-
-  // R = sparse(1:len(I), I, 1, len(I), m): row t holds column I[t]
-  int64_t *Rp = mem.tmp<int64_t>(nI + 1);
-  // Q = sparse(J, 1:len(J), 1, n, len(J)): row k holds every p with J[p] == k
-  int64_t *Qp = mem.tmp<int64_t>(A->n + 1);
-  int64_t *Qcur = mem.tmp<int64_t>(A->n + 1);
-  int32_t *Qj = mem.tmp<int32_t>(nJ > 0 ? nJ : 1);
-  int64_t *scan_tmp = mem.tmp<int64_t>(scan_tmp_elems(A->n + 1));
-  if (mem.failed) return HS_ENOMEM;
+  const int fl = ((int *)hbuf)[0], vf = ((int *)hbuf)[1];
+  if (fl & 1) return HS_EINVAL;
+  if (vf & 5) return HS_EINVAL;
+  if (vf & 2) return HS_ENONCANON;
+  const bool increasing = !(fl & 4);
   {
     PhaseTimer t("spref_build", st);
-    launch_iota_i64(Rp, nI + 1, st);
-    CK(cudaMemsetAsync(Qp, 0, sizeof(int64_t) * (size_t)(A->n + 1), st));
+    // Q = sparse(J, 1:len(J), 1, n, len(J)): row k holds every p with J[p] == k, increasing
+    CK(cudaMemsetAsync(Qp, 0, sizeof(int64_t) * (size_t)(n + 1), st));
     launch_build_Q_count(J, nJ, Qp, st);
-    launch_scan_i64(Qp, A->n + 1, scan_tmp, st);
-    CK(cudaMemcpyAsync(Qcur, Qp, sizeof(int64_t) * (size_t)(A->n + 1), cudaMemcpyDeviceToDevice, st));
+    launch_scan_i64(Qp, n + 1, scan_tmp, st);
+    CK(cudaMemcpyAsync(Qcur, Qp, sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyDeviceToDevice, st));
     launch_build_Q_fill(J, nJ, Qcur, Qj, st);
-    launch_sort_short_rows(Qp, Qj, A->n, st);
+    launch_sort_short_rows(Qp, Qj, n, st);
+  }
+  {
+    PhaseTimer t("spref_gather", st);
+    CK(cudaMemsetAsync(G, 0, sizeof(int64_t) * (size_t)(nI + 1), st));
+    launch_gather_len(A->ptr, I, nI, G, st);
+    launch_scan_i64(G, nI + 1, scan_tmp, st);
+  }
+  CK(cudaMemcpyAsync(hbuf, G + nI, 8, cudaMemcpyDeviceToHost, st));
+  if (int e = check_launch()) return e;
+  CK(cudaStreamSynchronize(st));
+  const int64_t total = hbuf[0];
+
+  auto empty_out = [&]() {
+    memset(Bout, 0, sizeof(*Bout));
+    Bout->fmt = HS_CSR;
+    Bout->dtype = A->dtype;
+    Bout->m = nI;
+    Bout->n = nJ;
+    Bout->ptr = (int64_t *)outmem.raw(sizeof(int64_t) * (size_t)(nI + 1));
+    Bout->idx = (int32_t *)outmem.raw(4);
+    Bout->val = vb ? outmem.raw((size_t)vb) : nullptr;
+    if (!Bout->ptr || !Bout->idx || (vb && !Bout->val)) return HS_ENOMEM;
+    CK(cudaMemsetAsync(Bout->ptr, 0, sizeof(int64_t) * (size_t)(nI + 1), st));
+    return check_launch();
+  };
+  if (total == 0 || nJ == 0) return empty_out();
+
+  int64_t *inc = mem.tmp<int64_t>((size_t)total);
+  int64_t *W = mem.tmp<int64_t>((size_t)total);
+  int64_t *scan_g = mem.tmp<int64_t>(scan_tmp_elems(total));
+  if (mem.failed) return HS_ENOMEM;
+  GatherArgs ga{A->ptr, A->idx, A->val, vb, I, G, inc, Qp, Qj, total, n};
+  {
+    PhaseTimer t("spref_gather", st);
+    CK(cudaMemsetAsync(inc, 0, sizeof(int64_t) * (size_t)total, st));
+    launch_row_starts(G, nI, total, inc, st);
+    launch_scan_i64(inc, total, scan_g, st);
+    launch_gather_w(ga, W, st);
+    launch_scan_i64(W, total, scan_g, st);
+  }
+  CK(cudaMemcpyAsync(hbuf, W + total - 1, 8, cudaMemcpyDeviceToHost, st));
+  if (int e = check_launch()) return e;
+  CK(cudaStreamSynchronize(st));
+  const int64_t ntup = hbuf[0];
+  if (ntup == 0) return empty_out();
+
+  if (increasing) {
+    memset(Bout, 0, sizeof(*Bout));
+    Bout->fmt = HS_CSR;
+    Bout->dtype = A->dtype;
+    Bout->m = nI;
+    Bout->n = nJ;
+    Bout->nnz = ntup;
+    Bout->ptr = (int64_t *)outmem.raw(sizeof(int64_t) * (size_t)(nI + 1));
+    Bout->idx = (int32_t *)outmem.raw(sizeof(int32_t) * (size_t)ntup);
+    Bout->val = vb ? outmem.raw((size_t)vb * (size_t)ntup) : nullptr;
+    if (!Bout->ptr || !Bout->idx || (vb && !Bout->val)) return HS_ENOMEM;
+    PhaseTimer t("spref_emit", st);
+    launch_gather_offsets(G, nI, W, Bout->ptr, st);
+    launch_gather_direct(ga, W, Bout->idx, Bout->val, st);
+    return check_launch();
+  }
+  if (ntup > 0x7fffffffLL) return HS_EUNSUPPORTED;
+  int32_t *ti = mem.tmp<int32_t>((size_t)ntup);
+  int32_t *pj = mem.tmp<int32_t>((size_t)ntup);
+  void *tv = vb ? (void *)mem.tmp<char>((size_t)vb * (size_t)ntup) : nullptr;
+  if (mem.failed) return HS_ENOMEM;
+  {
+    PhaseTimer t("spref_gather", st);
+    launch_gather_fill(ga, W, ti, pj, tv, st);
   }
   if (int e = check_launch()) return e;
-  hs_mat R{HS_CSR, HS_BOOL, nI, A->m, nI, 0, Rp, const_cast<int32_t *>(I), nullptr, nullptr};
-  hs_mat Q{HS_CSR, HS_BOOL, A->n, nJ, nJ, 0, Qp, Qj, nullptr, nullptr};
-  hs_mat RA;
-  memset(&RA, 0, sizeof(RA));
-  int e = spgemm_impl(HS_SELECT2ND, &R, A, &RA, mem, mem, flags & ~HS_FLAG_VALIDATE);
-  if (e) {
-    free_mat(&RA, mem);
-    return e;
-  }
-  e = spgemm_impl(HS_SELECT1ST, &RA, &Q, Bout, mem, outmem, flags & ~HS_FLAG_VALIDATE);
-  free_mat(&RA, mem);
-  return e;
+  // every (t, p) occurs once, so the combining operation never acts: values
+  // are copied bit for bit whatever the operation
+  const int sr = A->dtype == HS_BOOL ? HS_OR_AND : A->dtype == HS_I32 ? HS_MIN_PLUS : HS_PLUS_TIMES;
+  return sparse_impl(ti, pj, tv, ntup, nI, nJ, A->dtype, sr, Bout, mem, outmem, flags);
 }
 
 // C = sparse(i, j, v, m, n) (Section 2's constructor).  Every tuple is the
