@@ -67,8 +67,8 @@ def peaks():
 # that write its inputs (bins, lists, segment index) still hash to the value
 # they had when it was taken; after any change there the field is null until
 # it is measured again.
-MEASURED_TRAFFIC = {"kernel": "numeric_heavy", "scale": 20, "bytes": 33.16e9 + 24.59e9,
-                    "csrc_sha256_16": "7d1ecc48650bf4fc"}
+MEASURED_TRAFFIC = {"kernel": "numeric_heavy", "scale": 20, "bytes": 32.72e9 + 24.57e9,
+                    "csrc_sha256_16": "6ff06ccecf8861a9"}
 KERNEL_SOURCES = ("analysis.cu", "common.cuh", "internal.h", "numeric.cuh", "numeric_pt.cu", "symbolic.cu")
 
 
@@ -665,6 +665,7 @@ def main():
         dist.barrier()
     value = whole_job_rate(flops, args.steps, world, total_ms)
 
+
     # ---- roofline of the dominant kernel (largest total time among the library's kernel phases)
     hbm, peak_kind = peaks()
     kernel_phases = {k: v for k, v in prof.items() if k.startswith(("numeric_", "symbolic_"))}
@@ -754,6 +755,24 @@ def main():
         rate, desc, _ = oracle_sample(A, f, args.cpu_seconds, cores)
         cpu = {"value": rate, "unit": "mults/s", "cores": cores, "kind": "oracle", "sample": desc}
 
+    # the same product with rows left in any column order (the hash bins skip
+    # their sort), reported beside the canonical one; one untimed warm-up.  Timed
+    # last: the outputs it allocates stay in torch's cache
+    uts = []
+    for i in range(1 + max(3, args.steps // 2)):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        C = h.spgemm("plus_times", dA, dA, stream=stream, sorted_rows=False)
+        e1.record(stream)
+        e1.synchronize()
+        if i > 0:
+            uts.append(e0.elapsed_time(e1))
+        C = None
+    unsorted = {"ms_per_step": statistics.median(uts), "value": flops / (statistics.median(uts) / 1000.0),
+                "steps": len(uts), "what": "rows in any column order (HS_FLAG_UNSORTED), same product"}
+
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": "mults/s", "n_gpus": world, "steps": args.steps,
@@ -767,6 +786,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
             "gpu_launches": launches,
             "tuning": tuning,
+            "unsorted_output": unsorted,
             "phases_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         }), flush=True)
     if dist:

@@ -106,6 +106,17 @@ typedef struct hs_allocator {
 #define HS_FLAG_VALIDATE 1u      /* check canonical inputs and index ranges */
 #define HS_FLAG_STAGE_ON_DEVICE 2u /* hs_spgemm_to_host: compute C in device memory and
                                       copy it, even into host memory the GPU maps */
+#define HS_FLAG_UNSORTED 4u    /* hs_spgemm, hs_spgemm_batched, hs_spgemm_to_host,
+                                  hs_plan_create: rows of C may
+                                  come out in any column order (the hash bins skip their
+                                  sort); such a C is not canonical and must not be passed
+                                  where a canonical operand is expected */
+#define HS_FLAG_PRUNE_ZEROS 8u /* hs_spgemm and hs_spgemm_batched with HS_PLUS_TIMES: remove
+                                  the entries of C whose
+                                  sum is exactly zero (+0 or -0) by one compaction of C (one
+                                  more host synchronisation; C's arrays are reallocated, so
+                                  two copies of C are live for a moment); other semirings and
+                                  entry points ignore it */
 
 /* C = A*B over `semiring` (Section 1; Algorithm 1 and Section 2.1).
  * A: m x k, CSR or DCSR.  B: k x n, CSR.  C: m x n CSR, filled in by the

@@ -190,15 +190,36 @@ __global__ void k_compact_offsets(RowSet A, const int64_t *K, int64_t *p2) {
     p2[r] = x > 0 ? K[x - 1] : 0;
   }
 }
+void launch_compact_by_keep(const RowSet &A, const int64_t *K, int32_t *j2, void *v2, int vb, int64_t *p2,
+                            cudaStream_t st) {
+  count_launch();
+  k_compact_entries<<<grid_for(A.nnz, 256, 8), 256, 0, st>>>(A, K, j2, v2, vb);
+  count_launch();
+  k_compact_offsets<<<grid_for(A.nslots + 1, 256, 8), 256, 0, st>>>(A, K, p2);
+}
 void launch_compact_a(const RowSet &A, const int64_t *S, int64_t *keep, int64_t *scan_tmp, int32_t *j2, void *v2,
                       int vb, int64_t *p2, cudaStream_t st) {
   count_launch();
   k_keep_flags<<<grid_for(A.nnz, 256, 8), 256, 0, st>>>(A, S, keep);
   launch_scan_i64(keep, A.nnz, scan_tmp, st);
+  launch_compact_by_keep(A, keep, j2, v2, vb, p2, st);
+}
+
+// explicit zeros (value == 0; for floats +0 and -0 alike)
+template <typename T> __global__ void k_keep_nonzero(const T *v, int64_t n, int64_t *keep) {
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
+    keep[x] = v[x] != T(0);
+}
+void launch_keep_nonzero(const void *v, int dtype, int64_t n, int64_t *keep, cudaStream_t st) {
+  if (n <= 0) return;
   count_launch();
-  k_compact_entries<<<grid_for(A.nnz, 256, 8), 256, 0, st>>>(A, keep, j2, v2, vb);
-  count_launch();
-  k_compact_offsets<<<grid_for(A.nslots + 1, 256, 8), 256, 0, st>>>(A, keep, p2);
+  const int g = grid_for(n, 256, 8);
+  switch (dtype) {
+    case 0: k_keep_nonzero<<<g, 256, 0, st>>>(reinterpret_cast<const double *>(v), n, keep); break;
+    case 1: k_keep_nonzero<<<g, 256, 0, st>>>(reinterpret_cast<const float *>(v), n, keep); break;
+    case 2: k_keep_nonzero<<<g, 256, 0, st>>>(reinterpret_cast<const int32_t *>(v), n, keep); break;
+    default: k_keep_nonzero<<<g, 256, 0, st>>>(reinterpret_cast<const int64_t *>(v), n, keep); break;
+  }
 }
 
 // ---------------------------------------------------- B segment index

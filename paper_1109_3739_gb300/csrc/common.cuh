@@ -609,7 +609,7 @@ __host__ __device__ __forceinline__ size_t emit_work_bytes(int c, int vbytes) {
 template <class G, typename T, bool HAS_VAL>
 __device__ void group_sort_emit(const int *keys, const T *vals, int slots, int c, int *ck, T *cv,
                                 void *work, int *wtmp, EmitScratch *es, int32_t *out_j, T *out_v,
-                                int *err, int cap, long long *dbg) {
+                                int *err, int cap, long long *dbg, bool unsorted = false) {
   constexpr int EU = 4;  // entries per thread per step: their shared-memory chains overlap
   const int gs = G::size(), r = G::rank(), lane = lane_id();
   if (!HS_G(dbg, c >= 0 && c <= cap, 20, c)) {
@@ -663,6 +663,13 @@ __device__ void group_sort_emit(const int *keys, const T *vals, int slots, int c
     return;
   }
   if (c == 0) return;
+  if (unsorted) {  // the caller takes the row in table order
+    for (int e = r; e < c; e += gs) {
+      __stcs(out_j + e, ck[e]);
+      if constexpr (HAS_VAL) __stcs(out_v + e, cv[e]);
+    }
+    return;
+  }
   // (2) buckets
   const int nb = emit_buckets(c);
   int *bcnt = reinterpret_cast<int *>(work);

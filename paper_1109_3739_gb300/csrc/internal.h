@@ -122,6 +122,11 @@ void launch_row_flops(const RowSet &A, const int64_t *S, int64_t *f, int *key_cn
                       const BinCfg &bins, int64_t bn, cudaStream_t st);
 void launch_compact_a(const RowSet &A, const int64_t *S, int64_t *keep, int64_t *scan_tmp, int32_t *j2, void *v2,
                       int vb, int64_t *p2, cudaStream_t st);
+// entries of a CSR whose value is not zero (dtype F64, F32, I32 or I64):
+// keep flags, then (after their inclusive scan) the compacted copy
+void launch_keep_nonzero(const void *v, int dtype, int64_t n, int64_t *keep, cudaStream_t st);
+void launch_compact_by_keep(const RowSet &A, const int64_t *K, int32_t *j2, void *v2, int vb, int64_t *p2,
+                            cudaStream_t st);
 void launch_key_offsets(const int *key_cnt, int *key_off, int *key_cur, cudaStream_t st);
 // rows with more than cap_large products get a column-segment histogram slot
 void launch_scatter_sym(const RowSet &A, const int64_t *f, int *key_cur, int *list, int32_t *hslot,
@@ -188,6 +193,7 @@ struct NumArgs {
   const int64_t *loff;    // per row slot: its list (-1 none)
   const int32_t *bci_id;  // per B row: its row of the segment index (-1 none), or null
   const int32_t *bci;     // segment index: nseg+1 offsets per indexed B row
+  int unsorted;           // hash bins write their entries in table order (no sort)
 };
 // kind: 0 tiny, 1 warp_s, 2 warp, 3 mid_s, 4 mid, 5 large_s, 6 large, 7 heavy
 // (bin key KEY_TINY + kind; heavy takes every key from KEY_HEAVY on).

@@ -144,7 +144,8 @@ __global__ void __launch_bounds__(NWARP_WPB * 32, 4) k_num_warp(NumArgs a) {
                       [&](int col, T v, int) { hash_insert_val<SR>(keys, vals, mask, col, v, a.err); });
     __syncwarp();
     group_sort_emit<WarpGroup, T, SR::has_val>(keys, vals, slots, c, ck, cv, base, nullptr, es, a.Cj + cb,
-                                               SR::has_val ? Cv + cb : nullptr, a.err, NWARP_CAP, a.A.dbg);
+                                               SR::has_val ? Cv + cb : nullptr, a.err, NWARP_CAP, a.A.dbg,
+                                               a.unsorted);
     __syncwarp();
   }
 }
@@ -222,7 +223,8 @@ __global__ void __launch_bounds__(NT, 1) k_num_cta(NumArgs a) {
       }
     } else {
       group_sort_emit<CtaGroup, T, SR::has_val>(keys, vals, slots, c, ck, cv, smem_raw, tl.wtmp, &tl.es,
-                                                a.Cj + cb, SR::has_val ? Cv + cb : nullptr, a.err, CAP, a.A.dbg);
+                                                a.Cj + cb, SR::has_val ? Cv + cb : nullptr, a.err, CAP, a.A.dbg,
+                                                a.unsorted);
     }
     __syncthreads();
   }

@@ -623,6 +623,7 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
   }
   NumArgs na{rs, rb,   f,    nullptr, 0,    Cp,    C->idx, C->val, hslot,
              hist, nseg, &sb->dyn[1], &sb->err, gcur, gend, glist, loff, bci_id, bci};
+  na.unsorted = (flags & HS_FLAG_UNSORTED) ? 1 : 0;
   const char *names[NUM_KINDS] = {"numeric_tiny", "numeric_warp_s", "numeric_warp",  "numeric_mid_s",
                                   "numeric_mid",  "numeric_large_s", "numeric_large", "numeric_heavy"};
   static_assert(KEY_TINY + NUM_KINDS - 1 == KEY_HEAVY, "one key per numeric kind before the heavy keys");
@@ -654,6 +655,46 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
       snprintf(t_detail, sizeof(t_detail), "device consistency check %d", hb->err);
       return HS_EINTERNAL;
     }
+  }
+  // explicit zeros on request: entries whose (+,x) sum is exactly zero are
+  // removed by one compaction of C (the symbolic pass counts structure only,
+  // so this cannot happen earlier)
+  if ((flags & HS_FLAG_PRUNE_ZEROS) && sr == HS_PLUS_TIMES && !plan && !place && nnz > 0) {
+    int64_t *keep = mem.tmp<int64_t>((size_t)nnz);
+    int64_t *ktmp = mem.tmp<int64_t>((size_t)scan_tmp_elems(nnz));
+    if (mem.failed) return HS_ENOMEM;
+    {
+      PhaseTimer t("prune_zeros", st);
+      launch_keep_nonzero(C->val, out_dt, nnz, keep, st);
+      launch_scan_i64(keep, nnz, ktmp, st);
+    }
+    CK(cudaMemcpyAsync(&hb->nnz, keep + nnz - 1, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const int64_t kept = hb->nnz;
+    if (kept < nnz) {
+      int64_t *p2 = (int64_t *)outmem.raw(sizeof(int64_t) * (size_t)(m + 1));
+      int32_t *j2 = (int32_t *)outmem.raw(sizeof(int32_t) * (size_t)(kept > 0 ? kept : 1));
+      void *v2 = outmem.raw((size_t)vb * (size_t)(kept > 0 ? kept : 1));
+      if (!p2 || !j2 || !v2) {
+        if (p2) outmem.release(p2, sizeof(int64_t) * (size_t)(m + 1));
+        if (j2) outmem.release(j2, sizeof(int32_t) * (size_t)(kept > 0 ? kept : 1));
+        if (v2) outmem.release(v2, (size_t)vb * (size_t)(kept > 0 ? kept : 1));
+        return HS_ENOMEM;
+      }
+      const RowSet cs{Cp, C->idx, C->val, nullptr, m, nnz, m, sb->dbg};
+      {
+        PhaseTimer t("prune_zeros", st);
+        launch_compact_by_keep(cs, keep, j2, v2, vb, p2, st);
+      }
+      outmem.release(C->ptr, sizeof(int64_t) * (size_t)(m + 1));
+      outmem.release(C->idx, sizeof(int32_t) * (size_t)nnz);
+      outmem.release(C->val, (size_t)vb * (size_t)nnz);
+      C->ptr = p2;
+      C->idx = j2;
+      C->val = v2;
+      C->nnz = kept;
+    }
+    if (int e = check_launch()) return e;
   }
   if (plan) {  // the plan takes over every scratch buffer
     plan->c_nnz = nnz;
@@ -946,8 +987,10 @@ static int spasgn_impl(const hs_mat *A, const int32_t *I, int64_t nI, const int3
   hs_mat RB, X;
   memset(&RB, 0, sizeof(RB));
   memset(&X, 0, sizeof(X));
-  int e = spgemm_impl(HS_SELECT2ND, &R, B, &RB, mem, mem, flags & ~HS_FLAG_VALIDATE);
-  if (!e) e = spgemm_impl(HS_SELECT1ST, &RB, &Q, &X, mem, mem, flags & ~HS_FLAG_VALIDATE);
+  // the products feed the merge, which needs canonical rows
+  const uint32_t pf = flags & ~(HS_FLAG_VALIDATE | HS_FLAG_UNSORTED | HS_FLAG_PRUNE_ZEROS);
+  int e = spgemm_impl(HS_SELECT2ND, &R, B, &RB, mem, mem, pf);
+  if (!e) e = spgemm_impl(HS_SELECT1ST, &RB, &Q, &X, mem, mem, pf);
   free_mat(&RB, mem);
   if (e) {
     free_mat(&X, mem);
@@ -1155,7 +1198,8 @@ int hs_spgemm_to_host(int semiring, const hs_mat *A, const hs_mat *B, int64_t nb
     memset(&Cb, 0, sizeof(Cb));
     Mem mem{nullptr, st, pool};
     Mem out{nullptr, st, pool};
-    status = with_output(&Cb, out, [&] { return spgemm_impl(semiring, &Ab, B, &Cb, mem, out, flags); });
+    status = with_output(&Cb, out,
+                         [&] { return spgemm_impl(semiring, &Ab, B, &Cb, mem, out, flags & ~HS_FLAG_PRUNE_ZEROS); });
     if (status != HS_OK) break;
     const int64_t rows = r1 - r0;
     if (base + Cb.nnz <= capacity) {

@@ -244,13 +244,18 @@ def _device_of(A: DeviceCSR):
 
 
 # -------------------------------------------------------------- operations
-def spgemm(semiring: str, A: DeviceCSR, B: DeviceCSR, validate: bool = False, stream=None) -> DeviceCSR:
-    """C = A*B over `semiring` (hs_spgemm)."""
+def spgemm(semiring: str, A: DeviceCSR, B: DeviceCSR, validate: bool = False, stream=None,
+           sorted_rows: bool = True, prune_zeros: bool = False) -> DeviceCSR:
+    """C = A*B over `semiring` (hs_spgemm).  sorted_rows=False lets rows come out
+    in any column order (HS_FLAG_UNSORTED); prune_zeros removes entries whose
+    (+,x) sum is exactly zero (HS_FLAG_PRUNE_ZEROS)."""
     L = _lib()
     al = _TorchAlloc(_device_of(A))
     a, b, c = A.desc(), B.desc(), hs_mat()
+    fl = ((FLAG_VALIDATE if validate else 0) | (0 if sorted_rows else FLAG_UNSORTED)
+          | (FLAG_PRUNE_ZEROS if prune_zeros else 0))
     st = L.hs_spgemm(SEMIRING[semiring], ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
-                     ctypes.byref(al.struct), _stream_ptr(stream), FLAG_VALIDATE if validate else 0)
+                     ctypes.byref(al.struct), _stream_ptr(stream), fl)
     if st != 0:
         raise HsError(st, "hs_spgemm")
     return _adopt_output(al, c)
@@ -280,6 +285,8 @@ def spgemm_batched(semiring: str, As: list, Bs: list, validate: bool = False, st
 
 
 FLAG_STAGE_ON_DEVICE = 2
+FLAG_UNSORTED = 4
+FLAG_PRUNE_ZEROS = 8
 
 
 def spgemm_to_host(semiring: str, A: DeviceCSR, B: DeviceCSR, rowptr, col, val, blocks: int = 8,
