@@ -38,26 +38,44 @@ void launch_fill_i32(int32_t *a, int64_t n, int32_t v, cudaStream_t st) {
   }
 }
 
-// R of SpRef: offsets 0..nI (the column ids are I itself)
-void launch_build_R(const int32_t *, int64_t nI, int64_t *Rp, int32_t *, cudaStream_t st) {
-  count_launch();
-  k_iota_i64<<<grid1(nI + 1), 256, 0, st>>>(Rp, nI + 1);
-}
-
-// Q of SpRef: counts per row k go to Qp[k+1]
-__global__ void k_count_idx(const int32_t *X, int64_t n, int64_t *cnt) {
-  GRID_STRIDE(i, n) atomicAdd(reinterpret_cast<unsigned long long *>(cnt + X[i] + 1), 1ull);
-}
-void launch_build_Q_count(const int32_t *J, int64_t nJ, int64_t *Qp_counts, cudaStream_t st) {
-  if (nJ > 0) {
+__global__ void k_iota_i32(int32_t *p, int64_t n) { GRID_STRIDE(i, n) p[i] = (int32_t)i; }
+void launch_iota_i32(int32_t *p, int64_t n, cudaStream_t st) {
+  if (n > 0) {
     count_launch();
-    k_count_idx<<<grid1(nJ), 256, 0, st>>>(J, nJ, Qp_counts);
+    k_iota_i32<<<grid1(n), 256, 0, st>>>(p, n);
   }
 }
 
+// Q of SpRef: counts per row k go to Qp[k+1]; indices outside [0, bound)
+// are skipped (the host reports them), so this may run before the range check
+__global__ void k_count_idx(const int32_t *X, int64_t n, int64_t bound, int64_t *cnt) {
+  GRID_STRIDE(i, n) {
+    const int32_t x = X[i];
+    if (x >= 0 && x < bound) atomicAdd(reinterpret_cast<unsigned long long *>(cnt + x + 1), 1ull);
+  }
+}
+void launch_build_Q_count(const int32_t *J, int64_t nJ, int64_t bound, int64_t *Qp_counts, cudaStream_t st) {
+  if (nJ > 0) {
+    count_launch();
+    k_count_idx<<<grid1(nJ), 256, 0, st>>>(J, nJ, bound, Qp_counts);
+  }
+}
+// the largest of n counts, into *out (zeroed by the caller)
+__global__ void k_max_count(const int64_t *cnt, int64_t n, unsigned long long *out) {
+  unsigned long long mx = 0;
+  GRID_STRIDE(i, n) mx = max(mx, (unsigned long long)cnt[i]);
+  mx = warp_max(mx);
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
+}
+void launch_max_count(const int64_t *cnt, int64_t n, unsigned long long *out, cudaStream_t st) {
+  if (n <= 0) return;
+  count_launch();
+  k_max_count<<<grid1(n), 256, 0, st>>>(cnt, n, out);
+}
+
 // Q of SpRef: cur holds the row offsets on entry and is advanced by atomics;
-// rows are then put in increasing order of p by an insertion sort (rows of Q
-// hold one entry per repetition of k in J, usually one)
+// rows are then put in increasing order of p by an insertion sort, used only
+// when no row holds more than 32 entries (one per repetition of k in J)
 __global__ void k_fill_idx(const int32_t *X, int64_t n, int64_t *cur, int32_t *out) {
   GRID_STRIDE(i, n) {
     const unsigned long long at = atomicAdd(reinterpret_cast<unsigned long long *>(cur + X[i]), 1ull);

@@ -205,8 +205,9 @@ bool launch_numeric_oa(int kind, const NumArgs &a, cudaStream_t st);
 bool launch_numeric_sel(int second, int vbytes, int kind, const NumArgs &a, cudaStream_t st);
 
 // index.cu: selection matrices and the SpAsgn merge
-void launch_build_R(const int32_t *I, int64_t nI, int64_t *Rp, int32_t *Rj, cudaStream_t st);
-void launch_build_Q_count(const int32_t *J, int64_t nJ, int64_t *Qp_counts, cudaStream_t st);
+void launch_build_Q_count(const int32_t *J, int64_t nJ, int64_t bound, int64_t *Qp_counts, cudaStream_t st);
+void launch_max_count(const int64_t *cnt, int64_t n, unsigned long long *out, cudaStream_t st);
+void launch_iota_i32(int32_t *p, int64_t n, cudaStream_t st);
 void launch_build_Q_fill(const int32_t *J, int64_t nJ, int64_t *Qcur, int32_t *Qj, cudaStream_t st);
 void launch_sort_short_rows(const int64_t *ptr, int32_t *j, int64_t rows, cudaStream_t st);
 void launch_check_range(const int32_t *X, int64_t n, int64_t bound, int *flag, cudaStream_t st);

@@ -736,6 +736,7 @@ static int spref_impl(const hs_mat *A, const int32_t *I, int64_t nI, const int32
   const int vb = A->dtype == HS_BOOL ? 0 : vbytes_of(A->dtype);
   const int64_t n = A->n;
   int *flag = mem.tmp<int>(2);
+  unsigned long long *qmax = mem.tmp<unsigned long long>(1);
   int64_t *hbuf = (int64_t *)pinned(32);
   int64_t *Qp = mem.tmp<int64_t>(n + 1);
   int64_t *Qcur = mem.tmp<int64_t>(n + 1);
@@ -744,28 +745,48 @@ static int spref_impl(const hs_mat *A, const int32_t *I, int64_t nI, const int32
   int64_t *scan_tmp = mem.tmp<int64_t>(scan_tmp_elems((n + 1) > (nI + 1) ? (n + 1) : (nI + 1)));
   if (mem.failed || !hbuf) return HS_ENOMEM;
   // index ranges are always checked, and before any kernel uses I or J as
-  // an address: they index A's rows, Q's rows and the gathered offsets
+  // an address: they index A's rows, Q's rows and the gathered offsets (the
+  // row counts of Q skip out-of-range ids, so they run alongside)
   CK(cudaMemsetAsync(flag, 0, 8, st));
+  CK(cudaMemsetAsync(qmax, 0, 8, st));
+  CK(cudaMemsetAsync(Qp, 0, sizeof(int64_t) * (size_t)(n + 1), st));
   launch_check_range(I, nI, A->m, flag, st);
   launch_check_range(J, nJ, n, flag, st);
   launch_check_increasing(J, nJ, flag, st);
   if (flags & HS_FLAG_VALIDATE) launch_validate(A->ptr, A->idx, A->m, A->n, flag + 1, st);
+  launch_build_Q_count(J, nJ, n, Qp, st);
+  launch_max_count(Qp, n + 1, qmax, st);
   CK(cudaMemcpyAsync(hbuf, flag, 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hbuf + 1, qmax, 8, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const int fl = ((int *)hbuf)[0], vf = ((int *)hbuf)[1];
   if (fl & 1) return HS_EINVAL;
   if (vf & 5) return HS_EINVAL;
   if (vf & 2) return HS_ENONCANON;
   const bool increasing = !(fl & 4);
-  {
+  const int64_t qrow_max = hbuf[1];
+  // Q = sparse(J, 1:len(J), 1, n, len(J)): row k holds every p with J[p] == k,
+  // increasing.  Short rows (at most 32 repetitions of an index): counted,
+  // filled by atomics and sorted in place; otherwise built by the stable
+  // radix sort of sparse() itself
+  struct QGuard {
+    hs_mat q{};
+    Mem &m;
+    ~QGuard() { free_mat(&q, m); }
+  } qg{hs_mat{}, mem};
+  if (qrow_max <= 32) {
     PhaseTimer t("spref_build", st);
-    // Q = sparse(J, 1:len(J), 1, n, len(J)): row k holds every p with J[p] == k, increasing
-    CK(cudaMemsetAsync(Qp, 0, sizeof(int64_t) * (size_t)(n + 1), st));
-    launch_build_Q_count(J, nJ, Qp, st);
     launch_scan_i64(Qp, n + 1, scan_tmp, st);
     CK(cudaMemcpyAsync(Qcur, Qp, sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyDeviceToDevice, st));
     launch_build_Q_fill(J, nJ, Qcur, Qj, st);
     launch_sort_short_rows(Qp, Qj, n, st);
+  } else {
+    int32_t *pidx = mem.tmp<int32_t>((size_t)nJ);
+    if (!pidx) return HS_ENOMEM;
+    launch_iota_i32(pidx, nJ, st);
+    if (int e = sparse_impl(J, pidx, nullptr, nJ, n, nJ, HS_BOOL, HS_OR_AND, &qg.q, mem, mem, 0)) return e;
+    Qp = qg.q.ptr;
+    Qj = qg.q.idx;
   }
   {
     PhaseTimer t("spref_gather", st);

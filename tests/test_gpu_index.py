@@ -43,6 +43,19 @@ def test_spref_small(dt):
         assert_bitexact(got, oracle.spref(A, Iv, Jv), f"spref {dt} {len(Iv)}x{len(Jv)}")
 
 
+@pytest.mark.parametrize("reps", [32, 33, 5000])
+def test_spref_repeated_columns(reps):
+    """J repeats one column reps times (Q's row for it holds reps entries):
+    up to 32 the short-row build, beyond it Q = sparse(J, 1:len(J), 1) by the
+    stable sort; both against the oracle."""
+    A = I.er_matrix(400, 300, 5, seed=35, dtype="f32", kind="signed")
+    Jv = np.concatenate([np.full(reps, 7, np.int32), I.random_sequence(300, 200, 36)])
+    Jv = Jv[np.argsort(I.draws(37, 1, 0, len(Jv)), kind="stable")].astype(np.int32)  # interleave
+    Iv = I.random_sequence(400, 150, 38)
+    got = H().spref(dev(A), Iv, Jv).to_host()
+    assert_bitexact(got, oracle.spref(A, Iv, Jv), f"spref J with {reps} repeats")
+
+
 def test_spref_rejects_out_of_range():
     h = H()
     A = I.er_matrix(50, 40, 3, seed=32, dtype="f64")
