@@ -375,7 +375,7 @@ def run_spref(args):
     """The paper's two SpRef experiments on the R-MAT matrix of scale --scale
     (edge factor 8, f32): E1 the random symmetric permutation B = A(p, p);
     E2 ten induced subgraphs A(r_i, r_i), r_1..r_10 the chunks of a random
-    permutation, extracted one after another.  value: entries of B produced
+    permutation, extracted in sequence.  value: entries of B produced
     per second in E1."""
     import torch
 

@@ -1,7 +1,7 @@
 """Tall-skinny products C = A*B of Section 4's last experiment on the GPU
 against the CPU oracle: A an R-MAT matrix with 8 nonzeros per column, B an
 n x k Erdos-Renyi matrix with d2 nonzeros per column, n/k = 8192 (the paper's
-aspect ratio), d2 from 1 to 10^5 in powers of ten.  The product stands for one
+aspect ratio), d2 = 1, 10, 100, ..., 10^5.  The product stands for one
 level of a multi-source breadth-first search; its rows range from empty
 (d2 = 1: B has k nonzeros in all) to a few hundred products each.
 """
