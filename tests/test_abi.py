@@ -21,7 +21,7 @@ def declared_functions():
 
 def test_header_declares_the_operations():
     names = declared_functions()
-    for must in ("hs_spgemm", "hs_spref", "hs_spasgn", "hs_mat_free", "hs_strerror"):
+    for must in ("hs_spgemm", "hs_spref", "hs_spasgn", "hs_sparse", "hs_mat_free", "hs_strerror"):
         assert must in names
 
 
@@ -60,3 +60,32 @@ def test_tuning_round_trip_without_gpu():
     assert d2["mid_s_max"] == 512 and d2["sym_heavy_from"] == 6144 and d2["warp_s_max"] == 128
     H.set_tuning(None)
     assert H.get_tuning() == d
+
+
+def test_sparse_argument_checks_without_gpu():
+    """hs_sparse rejects bad requests before any CUDA call (no GPU needed)."""
+    from paper_1109_3739_gb300 import hspgemm as H
+    L = H.library()
+    L.hs_sparse.restype = ctypes.c_int
+    vp, i64, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    L.hs_sparse.argtypes = [vp, vp, vp, i64, i64, i64, ci, ci, ctypes.POINTER(H.hs_mat), vp, vp, ctypes.c_uint32]
+    c = H.hs_mat()
+    dummy = ctypes.c_int32(0)
+    p = ctypes.addressof(dummy)  # never dereferenced: every call below fails its checks first
+    PT, MP, OR, SEL = H.SEMIRING["plus_times"], H.SEMIRING["min_plus"], H.SEMIRING["or_and"], H.SEMIRING["select2nd"]
+    F64, F32, I32, I64, BOOL = (H.DTYPE[k] for k in ("f64", "f32", "i32", "i64", "bool"))
+    cases = [
+        ((p, p, p, -1, 4, 4, F64, PT), -1),        # negative count
+        ((p, p, p, 1, 4, 4, F64, SEL), -1),        # selector semirings combine nothing
+        ((p, p, p, 1, 4, 4, I32, PT), -1),         # no int32 sum
+        ((p, p, p, 1, 4, 4, F64, MP), -1),         # no f64 min
+        ((p, p, p, 1, 4, 4, F32, OR), -1),         # or needs bool
+        ((None, p, p, 1, 4, 4, F64, PT), -1),      # missing i
+        ((p, p, None, 1, 4, 4, I64, PT), -1),      # missing values
+        ((p, p, p, 1 << 31, 4, 4, F64, PT), -7),   # more tuples than int32 ids
+        ((p, p, p, 1, 4, 1 << 31, BOOL, OR), -7),  # more columns than int32 ids
+    ]
+    for args, want in cases:
+        got = L.hs_sparse(*args, ctypes.byref(c), None, None, 0)
+        assert got == want, (args, got)
+        assert not c.ptr and not c.idx and not c.val  # nothing left allocated
