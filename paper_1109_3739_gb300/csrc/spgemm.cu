@@ -936,6 +936,7 @@ static int sparse_impl(const int32_t *I, const int32_t *J, const void *V, int64_
       const uint64_t *kin = first ? nullptr : kbuf[cur];
       const void *vin = first ? V : vbuf[cur];
       const int out = first ? 0 : cur ^ 1;
+      PhaseTimer tp("sparse_pass", st);
       launch_sp_pass(vb, kin, I, J, vin, nnz, nbj, m, n, p, ghist + ((size_t)p << rb), status, ticket + p, tiles,
                      kbuf[out], vbuf[out], flags, st);
       cur = out;
