@@ -134,10 +134,16 @@ int hs_spgemm(int semiring, const hs_mat *A, const hs_mat *B, hs_mat *C,
 /* B = A(I,J) (Section 3; SpRef listing of Section 3.1): B is len(I) x len(J),
  * row t of B is row I[t] of A and column p of B is column J[p] of A.  I and J
  * are int32 device arrays, any order, duplicates allowed (they repeat
- * rows/columns).  Computed as (R*A)*Q with R = sparse(1:len(I), I, 1) and
- * Q = sparse(J, 1:len(J), 1) through hs_spgemm with the selector semirings,
- * so values are copied bit for bit.  Errors: HS_EINVAL (index out of range
- * with HS_FLAG_VALIDATE, bad shapes), HS_ENOMEM, HS_ECUDA. */
+ * rows/columns).  This is the product R*A*Q with R = sparse(1:len(I), I, 1)
+ * and Q = sparse(J, 1:len(J), 1), evaluated without forming R*A: the rows
+ * I[t] are gathered, each entry (I[t], c) becomes (t, p) for every p with
+ * J[p] == c, and the entries are ordered by a stable radix sort (none when J
+ * is strictly increasing).  Values are copied bit for bit.  Index ranges are
+ * always checked; with HS_FLAG_VALIDATE, A is checked to be canonical too.
+ * At most 2^31-1 entries of B unless J is strictly increasing; three or four
+ * host synchronisations with `stream`.  Errors: HS_EINVAL (an index out of
+ * range, bad shapes, NULL pointers), HS_ENONCANON (with HS_FLAG_VALIDATE),
+ * HS_EUNSUPPORTED, HS_ENOMEM, HS_ECUDA. */
 int hs_spref(const hs_mat *A, const int32_t *I, int64_t nI, const int32_t *J, int64_t nJ,
              hs_mat *B, const hs_allocator *al, void *stream, uint32_t flags);
 
