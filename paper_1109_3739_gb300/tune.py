@@ -51,8 +51,9 @@ def tune(run, trials: int = 3, candidates: dict | None = None, stream=None):
     best_ms = time_ms(run, trials, stream)
     log = [(dict(best), best_ms)]
     for knob, values in cands.items():
+        start = best[knob]  # timed already, with the same other knobs: best_ms
         for v in values:
-            if v == best[knob]:
+            if v == start:
                 continue
             trial = dict(best, **{knob: v})
             h.set_tuning(trial)

@@ -1,0 +1,49 @@
+"""The autotuner's search logic on the CPU: the timing is replaced by a cost
+function of the thresholds currently set (hs_get_tuning needs no GPU)."""
+from __future__ import annotations
+
+
+def test_coordinate_descent_picks_each_knobs_best(monkeypatch):
+    from paper_1109_3739_gb300 import hspgemm as h
+    from paper_1109_3739_gb300 import tune
+
+    # a separable cost: the best value of each knob is known
+    want = {"warp_s_max": 64, "mid_s_max": 768, "large_s_max": 4096, "sym_mid_s_max": 512,
+            "sym_heavy_from": 6144}
+
+    def fake_time(run, trials, stream=None):
+        t = h.get_tuning()
+        return 10.0 + sum(abs(t[k] - v) / 1000.0 for k, v in want.items())
+
+    monkeypatch.setattr(tune, "time_ms", fake_time)
+    try:
+        best, log = tune.tune(lambda: None, trials=1)
+        assert best == want
+        assert h.get_tuning() == want            # left set
+        assert log[0][0] == {"warp_s_max": 128, "mid_s_max": 1024, "large_s_max": 4096,
+                             "sym_mid_s_max": 1024, "sym_heavy_from": 0}  # the defaults first
+        # one timing for the defaults, then every other candidate once
+        n_other = sum(len(v) - 1 for v in tune.CANDIDATES.values())
+        assert len(log) == 1 + n_other
+    finally:
+        h.set_tuning(None)
+
+
+def test_tuning_keeps_the_defaults_when_nothing_is_faster(monkeypatch):
+    from paper_1109_3739_gb300 import hspgemm as h
+    from paper_1109_3739_gb300 import tune
+    defaults = None
+
+    def fake_time(run, trials, stream=None):
+        nonlocal defaults
+        t = h.get_tuning()
+        if defaults is None:
+            defaults = dict(t)
+        return 1.0 if t == defaults else 2.0
+
+    monkeypatch.setattr(tune, "time_ms", fake_time)
+    try:
+        best, _ = tune.tune(lambda: None, trials=1)
+        assert best == defaults and h.get_tuning() == defaults
+    finally:
+        h.set_tuning(None)
