@@ -115,3 +115,14 @@ def test_sparse_empty_and_errors():
         oracle.sparse([0], [0], np.ones(1, np.int32), 1, 1, "plus_times")  # no i32 sum
     with pytest.raises(oracle.OracleError):
         oracle.sparse([0], [0], np.ones(1), 1, 1, "select2nd")
+
+
+def test_sparse_of_the_rmat_edge_list_is_the_rmat_matrix():
+    """The edge list the sparse() workload starts from and the matrix the
+    SpGEMM workload multiplies describe one graph: the oracle's or-combined
+    construction has exactly rmat_matrix's structure."""
+    i, j, _ = I.rmat_tuples(12, 8, seed=2, dtype="f32")
+    C = oracle.sparse(i, j, None, 1 << 12, 1 << 12, "or_and", dtype="bool")
+    R = I.rmat_matrix(12, 8, seed=2, dtype="f32")
+    np.testing.assert_array_equal(C.rowptr, R.rowptr)
+    np.testing.assert_array_equal(C.col, R.col)
