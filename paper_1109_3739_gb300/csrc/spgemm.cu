@@ -173,7 +173,11 @@ static int vbytes_of(int dt) {
   }
 }
 
-// pinned staging for the small device->host reads
+// pinned staging for the small device->host reads: one 8 KB page-locked
+// buffer per thread, shared by every call on that thread.  A caller reads
+// what it copied there before it calls another operation's implementation
+// (SpAsgn runs two products, SpRef may build Q with sparse()), and copies
+// into it again afterwards.
 struct Pinned {
   void *p = nullptr;
   ~Pinned() {
