@@ -68,15 +68,21 @@ def spgemm(sr: str, A, B):
     return pat, val, bnd
 
 
-def sparse(i, j, v, m: int, n: int, sr: str = "plus_times"):
+def sparse(i, j, v, m: int, n: int, sr: str = "plus_times", with_bound: bool = False):
     """sparse(i, j, v, m, n) by a dictionary keyed on (row, column), tuples
-    folded in the order given.  Returns {(r, c): value} (True for bool)."""
+    folded in the order given.  Returns {(r, c): value} (True for bool).
+
+    With with_bound also returns {(r, c): sum of |v| over the position's
+    tuples}, added in tuple order in Python floats (0.0 for bool)."""
     out = {}
+    mag = {}
     for k in range(len(i)):
         key = (int(i[k]), int(j[k]))
         if not (0 <= key[0] < m and 0 <= key[1] < n):
             raise ValueError("index out of range")
         x = True if v is None else v[k].item()
+        ax = 0.0 if v is None else abs(float(x))
+        mag[key] = ax if key not in mag else mag[key] + ax
         if key not in out:
             out[key] = x
         elif sr == "plus_times":
@@ -87,4 +93,4 @@ def sparse(i, j, v, m: int, n: int, sr: str = "plus_times"):
             out[key] = True
         else:
             raise ValueError(sr)
-    return out
+    return (out, mag) if with_bound else out

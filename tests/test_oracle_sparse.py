@@ -38,10 +38,15 @@ def _from_dict(d, m, n, dtype):
 @pytest.mark.parametrize("m,n,nnz", [(7, 5, 60), (30, 40, 200), (1, 1, 9), (50, 3, 0)])
 def test_sparse_vs_dictionary(sr, dt, m, n, nnz):
     i, j, v = I.random_tuples(m, n, nnz, seed=m * 1000 + nnz, dtype=dt)
-    C = oracle.sparse(i, j, v, m, n, sr, dtype=dt)
-    R = _from_dict(brute.sparse(i, j, v, m, n, sr), m, n, dt)
+    C, bound = oracle.sparse(i, j, v, m, n, sr, dtype=dt, with_bound=True)
+    d, mag = brute.sparse(i, j, v, m, n, sr, with_bound=True)
+    R = _from_dict(d, m, n, dt)
     # the dictionary folds in tuple order in Python floats (double) and so does the oracle
     assert_bitexact(C, R, f"{sr} {dt}")
+    # the tolerance scale: per position, the sum of |v| over its tuples in
+    # tuple order (double); the dictionary's keys sorted are C's entries
+    ref_b = np.array([mag[key] for key in sorted(mag)], dtype=np.float64)
+    np.testing.assert_array_equal(bound, ref_b, err_msg=f"bound {sr} {dt}")
 
 
 def test_sparse_vs_scipy():

@@ -50,11 +50,19 @@ def test_brute_force(sr, dt):
             seed += 1
             A = rand_sparse(m, k, dens, seed, dt)
             B = rand_sparse(k, n, dens, seed + 5000, dt)
-            C = oracle.spgemm(sr, A, B)
-            pat, val, _ = brute.spgemm(sr, A, B)
+            C, bound = oracle.spgemm(sr, A, B, with_bound=True)
+            pat, val, bnd = brute.spgemm(sr, A, B)
             np.testing.assert_array_equal(C.rowptr, np.concatenate([[0], np.cumsum(pat.sum(1))]))
             rows, cols = np.nonzero(pat)
             np.testing.assert_array_equal(C.col, cols)
+            # the per-entry tolerance scale sum |a||b| of the floating-point
+            # parity tests: same products, same ascending-k order of additions
+            # in double, so equal; the exact semirings carry no scale
+            if sr == "plus_times" and dt in ("f32", "f64"):
+                ref_b = np.array([bnd[i][j] for i, j in zip(rows, cols)], dtype=np.float64)
+                np.testing.assert_array_equal(bound, ref_b, err_msg=f"bound {dt} {m}x{k}x{n} d={dens}")
+            else:
+                assert not np.any(bound), f"{sr} {dt}: nonzero tolerance scale"
             if dt == "bool":
                 assert C.val is None
                 continue
