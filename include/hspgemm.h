@@ -305,7 +305,10 @@ int hs_batch_stack(int64_t count, const hs_mat *A, const hs_mat *B, hs_mat *SA, 
  *     16 bytes per row of A, plus 4 bytes per 4096 columns for every row with
  *     more than 4096 (8-byte values) or 8192 (other types) products and 8
  *     bytes per entry of A when such rows exist); nothing is written but
- *     C->ptr.
+ *     C->ptr, and C->nnz is 0.
+ *   - HS_EINVAL: besides the checks of hs_spgemm, a missing A->ptr or B->ptr
+ *     (operand with rows), A->idx or B->idx (operand with entries), C->ptr,
+ *     or C->idx / C->val with capacity > 0; found before any CUDA call.
  *   - HS_ECAPACITY: nnz(C) > capacity; C->ptr is complete and C->nnz holds
  *     the capacity needed, so the caller can provide larger arrays and call
  *     again.  C->idx and C->val are not touched.
@@ -340,6 +343,18 @@ int hs_version(void);
 /* Number of CUDA kernels this library has launched in this process (all
  * threads, all devices); differences around a region count its launches. */
 int64_t hs_launch_count(void);
+
+/* Failure-detection test hook (the paper has no counterpart; not part of any
+ * operation).  The next radix sort on this host thread (an hs_sparse call
+ * with at least one tuple, or an hs_spref that sorts) runs its passes with a
+ * look-back poll limit of
+ * `spin_limit` (at least 1) and with tile `withhold_tile` (0-based, tiles of
+ * 4096 tuples) never publishing its digit counts, so the bounded wait of a
+ * later tile runs out: the call then returns HS_ETIMEDOUT, every store of
+ * the pass stays inside its buffers (they are bounds-checked) and nothing is
+ * left allocated.  The setting is consumed by that one call.  Returns HS_OK,
+ * or HS_EINVAL for spin_limit < 1 or withhold_tile < 0. */
+int hs_test_lookback_expiry(int spin_limit, int64_t withhold_tile);
 
 /* Phase timing.  With hs_profile_enable(1) every later call records CUDA
  * events on its stream around each phase; hs_profile_read copies the

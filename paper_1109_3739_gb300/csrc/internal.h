@@ -242,13 +242,17 @@ int64_t sp_tiles(int64_t nnz);
 int sp_radix_bits();
 int64_t sp_long_capacity(int64_t nnz);  // runs longer than the emit kernel folds alone
 int sp_max_passes();
-// flag bit 1: an index out of range; bit 2: a look-back wait expired
+// flag bit 1: an index out of range; bit 2: a look-back wait expired.
+// spin_limit: polls of one look-back word before giving up (sp_spin_limit()
+// in production); withhold: a tile that never publishes its counts (-1: none;
+// failure-detection tests only)
+int sp_spin_limit();
 void launch_sp_allhist(const int32_t *I, const int32_t *J, int64_t nnz, int nbj, int64_t m, int64_t n, int passes,
                        unsigned long long *ghist, int *flag, cudaStream_t st);
 void launch_sp_pass(int vb, const uint64_t *Kin, const int32_t *I, const int32_t *J, const void *Vin, int64_t nnz,
                     int nbj, int64_t m, int64_t n, int pass, const unsigned long long *ghist,
                     unsigned long long *status, int *ticket, int64_t ntiles, uint64_t *Kout, void *Vout, int *flag,
-                    cudaStream_t st);
+                    int spin_limit, long long withhold, cudaStream_t st);
 void launch_sp_heads(const uint64_t *K, int64_t nnz, int64_t *theads, int64_t ntiles, cudaStream_t st);
 // op: 0 (+) f64, 1 (+) f32, 2 (+) i64, 3 min f32, 4 min i32, 5 structure only
 void launch_sp_emit(int op, const uint64_t *K, const void *V, int64_t nnz, int nbj, const int64_t *theads_incl,

@@ -154,6 +154,9 @@ static int spgemm_noalloc_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat 
   const int64_t nslots = A->fmt == HS_DCSR ? A->nzr : A->m;
   if (nslots < 0 || (A->fmt == HS_DCSR && nslots > 0 && !A->ids)) return HS_EINVAL;
   if (nslots > 0x7fffffffLL) return HS_EUNSUPPORTED;
+  // every input array a kernel will read must be there: checked before the first CUDA call
+  if ((nslots > 0 && !A->ptr) || (B->m > 0 && !B->ptr)) return HS_EINVAL;
+  if ((A->nnz > 0 && !A->idx) || (B->nnz > 0 && !B->idx)) return HS_EINVAL;
   if (!C->ptr || (capacity > 0 && (!C->idx || (vb && !C->val)))) return HS_EINVAL;
 
   C->fmt = HS_CSR;
@@ -238,7 +241,10 @@ static int spgemm_noalloc_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat 
   if (key_off[NKEYS] > key_off[KEY_HEAVY]) {
     gcur = ar.take<int32_t>((size_t)A->nnz);
     gend = ar.take<int32_t>((size_t)A->nnz);
-    if (ar.over) return HS_ESCRATCH;
+    if (ar.over) {
+      C->nnz = 0;  // C->ptr holds the row offsets, but no entry was written
+      return HS_ESCRATCH;
+    }
   }
   NumArgs na{rs,   rb,   f,    nullptr,     0,        Cp,   C->idx, C->val,  hslot,
              hist, nseg, &sb->dyn[1], &sb->err, gcur, gend, nullptr, nullptr, nullptr, nullptr};

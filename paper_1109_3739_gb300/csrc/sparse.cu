@@ -31,6 +31,7 @@ constexpr int SP_MAX_PASSES = 8;
 // pass), bits 0..31 the count
 constexpr unsigned long long SP_INCL = 1ull << 63, SP_AGG = 1ull << 62;
 constexpr int SP_SPIN_LIMIT = 1 << 18;  // polls of one status word before giving up (well under a second)
+int sp_spin_limit() { return SP_SPIN_LIMIT; }
 static_assert(SP_NT == SP_RADIX, "one thread per digit in the per-tile digit scan");
 
 template <bool FIRST>
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(SP_NT, 3) k_sp_onesweep(const uint64_t *Kin, c
                                                        const void *Vin, int64_t nnz, int nbj, int64_t m,
                                                        int64_t n, int pass, const unsigned long long *ghist,
                                                        unsigned long long *status, int *ticket, uint64_t *Kout,
-                                                       void *Vout, int *flag) {
+                                                       void *Vout, int *flag, int spin_limit, long long withhold) {
   using VT = typename SpVal<VB>::T;
   extern __shared__ __align__(16) unsigned char sp_smem[];
   uint64_t *skey = reinterpret_cast<uint64_t *>(sp_smem);
@@ -152,8 +153,13 @@ __global__ void __launch_bounds__(SP_NT, 3) k_sp_onesweep(const uint64_t *Kin, c
   }
   const unsigned long long tag = (unsigned long long)(pass + 1) << 32;
   unsigned long long *my = status + tile * SP_RADIX + d;
-  if (tile == 0) sp_st(my, SP_INCL | tag | (unsigned)tot);
-  else sp_st(my, SP_AGG | tag | (unsigned)tot);
+  // (a tile equal to `withhold` never publishes: the failure-detection
+  // tests use it so that the next tile's bounded wait runs out)
+  const bool publish = tile != withhold;
+  if (publish) {
+    if (tile == 0) sp_st(my, SP_INCL | tag | (unsigned)tot);
+    else sp_st(my, SP_AGG | tag | (unsigned)tot);
+  }
   // tile start of each digit (exclusive scan over the digits) and the digit's
   // start in the whole output (exclusive scan of this pass's totals)
   const int incl = warp_incl_scan(tot);
@@ -183,7 +189,7 @@ __global__ void __launch_bounds__(SP_NT, 3) k_sp_onesweep(const uint64_t *Kin, c
       for (;;) {
         x = sp_ld(q);
         if ((x & (0xffffull << 32)) == tag && (x & (SP_INCL | SP_AGG))) break;
-        if (++spin > SP_SPIN_LIMIT) {  // never expected: the host reports HS_ETIMEDOUT
+        if (++spin > spin_limit) {  // never expected: the host reports HS_ETIMEDOUT
           atomicOr(flag, 2);
           x = SP_INCL | tag;
           break;
@@ -193,7 +199,7 @@ __global__ void __launch_bounds__(SP_NT, 3) k_sp_onesweep(const uint64_t *Kin, c
       excl += (long long)(x & 0xffffffffull);
       if (x & SP_INCL) break;
     }
-    sp_st(my, SP_INCL | tag | (unsigned)(excl + tot));
+    if (publish) sp_st(my, SP_INCL | tag | (unsigned)(excl + tot));
   }
   goff[d] = gbefore + gincl - gh + excl;
   __syncthreads();
@@ -442,21 +448,24 @@ template <bool FIRST, int VB>
 static void sp_pass_one(const uint64_t *Kin, const int32_t *I, const int32_t *J, const void *Vin, int64_t nnz,
                         int nbj, int64_t m, int64_t n, int pass, const unsigned long long *ghist,
                         unsigned long long *status, int *ticket, int64_t ntiles, uint64_t *Kout, void *Vout,
-                        int *flag, cudaStream_t st) {
+                        int *flag, int spin_limit, long long withhold, cudaStream_t st) {
   constexpr size_t smem = sp_scatter_smem<VB>();
   set_smem_attr(k_sp_onesweep<FIRST, VB>, smem);
   count_launch();
   k_sp_onesweep<FIRST, VB><<<sp_grid(ntiles), SP_NT, smem, st>>>(Kin, I, J, Vin, nnz, nbj, m, n, pass, ghist,
-                                                                 status, ticket, Kout, Vout, flag);
+                                                                 status, ticket, Kout, Vout, flag, spin_limit,
+                                                                 withhold);
 }
 
 void launch_sp_pass(int vb, const uint64_t *Kin, const int32_t *I, const int32_t *J, const void *Vin, int64_t nnz,
                     int nbj, int64_t m, int64_t n, int pass, const unsigned long long *ghist,
                     unsigned long long *status, int *ticket, int64_t ntiles, uint64_t *Kout, void *Vout, int *flag,
-                    cudaStream_t st) {
+                    int spin_limit, long long withhold, cudaStream_t st) {
   if (ntiles <= 0) return;
-#define SP_PS(F, B) \
-  sp_pass_one<F, B>(Kin, I, J, Vin, nnz, nbj, m, n, pass, ghist, status, ticket, ntiles, Kout, Vout, flag, st)
+  if (spin_limit < 1) spin_limit = 1;
+#define SP_PS(F, B)                                                                                              \
+  sp_pass_one<F, B>(Kin, I, J, Vin, nnz, nbj, m, n, pass, ghist, status, ticket, ntiles, Kout, Vout, flag, \
+                    spin_limit, withhold, st)
   if (pass == 0) {
     if (vb == 8) SP_PS(true, 8);
     else if (vb == 4) SP_PS(true, 4);

@@ -378,6 +378,7 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
   const int64_t nslots = A->fmt == HS_DCSR ? A->nzr : A->m;
   if (nslots < 0 || (A->fmt == HS_DCSR && nslots > 0 && !A->ids)) return HS_EINVAL;
   if ((nslots > 0 && !A->ptr) || (B->m >= 0 && !B->ptr && B->m > 0)) return HS_EINVAL;
+  if ((A->nnz > 0 && !A->idx) || (B->nnz > 0 && !B->idx)) return HS_EINVAL;
   if (nslots > 0x7fffffffLL) return HS_EUNSUPPORTED;
 
   memset(C, 0, sizeof(*C));
@@ -878,6 +879,12 @@ static int spref_impl(const hs_mat *A, const int32_t *I, int64_t nI, const int32
 // was out of range.
 static int bits_of(int64_t x) { return x > 0 ? 64 - __builtin_clzll((unsigned long long)x) : 0; }
 
+// Failure-detection test setting for the next sparse() sort on this host
+// thread (hs_test_lookback_expiry): a short look-back poll limit and a tile
+// that never publishes its counts.  Consumed by one call.
+static thread_local int t_sp_spin = 0;             // 0: the production limit
+static thread_local long long t_sp_withhold = -1;  // -1: every tile publishes
+
 static int sparse_impl(const int32_t *I, const int32_t *J, const void *V, int64_t nnz, int64_t m, int64_t n,
                        int dtype, int sr, hs_mat *C, Mem &mem, Mem &outmem, uint32_t) {
   cudaStream_t st = mem.st;
@@ -932,6 +939,10 @@ static int sparse_impl(const int32_t *I, const int32_t *J, const void *V, int64_
   CK(cudaMemsetAsync(ghist, 0, sizeof(unsigned long long) * ((size_t)passes << rb), st));
   CK(cudaMemsetAsync(ticket, 0, sizeof(int) * (size_t)passes, st));
   int cur = 0;
+  const int spin = t_sp_spin > 0 ? t_sp_spin : sp_spin_limit();
+  const long long withhold = t_sp_withhold;
+  t_sp_spin = 0;
+  t_sp_withhold = -1;
   {
     PhaseTimer t("sparse_sort", st);
     launch_sp_allhist(I, J, nnz, nbj, m, n, passes, ghist, flags, st);
@@ -942,7 +953,7 @@ static int sparse_impl(const int32_t *I, const int32_t *J, const void *V, int64_
       const int out = first ? 0 : cur ^ 1;
       PhaseTimer tp("sparse_pass", st);
       launch_sp_pass(vb, kin, I, J, vin, nnz, nbj, m, n, p, ghist + ((size_t)p << rb), status, ticket + p, tiles,
-                     kbuf[out], vbuf[out], flags, st);
+                     kbuf[out], vbuf[out], flags, spin, withhold, st);
       cur = out;
     }
     launch_sp_heads(kbuf[cur], nnz, theads, tiles, st);
@@ -1345,6 +1356,13 @@ const char *hs_last_error_detail(void) { return t_detail; }
 int hs_version(void) { return 100; }
 
 int64_t hs_launch_count(void) { return (int64_t)launch_total(); }
+
+int hs_test_lookback_expiry(int spin_limit, int64_t withhold_tile) {
+  if (spin_limit < 1 || withhold_tile < 0) return HS_EINVAL;
+  t_sp_spin = spin_limit;
+  t_sp_withhold = (long long)withhold_tile;
+  return HS_OK;
+}
 
 void hs_profile_enable(int on) {
   std::lock_guard<std::mutex> g(g_prof.mu);

@@ -105,6 +105,8 @@ def _lib():
             L.hs_spgemm_to_host.argtypes = [ci, P(hs_mat), P(hs_mat), i64, vp, vp, vp, i64, P(ctypes.c_int64), vp, u32]
             L.hs_spgemm_to_host.restype = ci
             L.hs_trim_memory.restype = ci
+            L.hs_test_lookback_expiry.argtypes = [ci, i64]
+            L.hs_test_lookback_expiry.restype = ci
             L.hs_set_tuning.argtypes = [P(hs_tuning)]
             L.hs_set_tuning.restype = ci
             L.hs_get_tuning.argtypes = [P(hs_tuning)]

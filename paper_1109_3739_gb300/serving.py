@@ -9,14 +9,18 @@ update of a graph), admitted as they arrive and batched continuously.
   at a time, each on the version current when it starts.
 * Server admits requests as slots (worker streams) and memory (an estimate of
   each request's working set against a budget) free up.  A free slot takes
-  every admitted request that is waiting (up to max_batch): the SpRef
-  requests of that batch share one stacked R*A product (R stacks every
-  request's selection matrix) and one hs_spgemm_batched call for their (RA)*Q
-  steps; contractions and updates run as they are.  Slots run on their own
-  CUDA streams from their own host threads, so the GPU work of batches in
+  every admitted request that is waiting (up to max_batch) and runs them on
+  its stream: SpRef by the library's gather (hs_spref: the selected rows are
+  gathered and relabelled on the device, R and Q are never formed),
+  contractions as two products, updates one at a time.  Slots run on their
+  own CUDA streams from their own host threads, so the GPU work of batches in
   flight overlaps.
-* Every kernel runs in the library (hs_spgemm, hs_spgemm_batched, hs_spasgn);
-  this module only schedules, builds the small index arrays and measures.
+* A malformed request (unknown kind, vertex or label set out of range,
+  ragged edge arrays) is rejected at admission and never binds to a version;
+  a request cancelled before its batch starts is skipped; a request whose
+  library call fails is marked failed without sinking the rest of its batch.
+* Every kernel runs in the library (hs_spgemm, hs_spref, hs_spasgn); this
+  module only schedules, builds the small index arrays and measures.
 """
 from __future__ import annotations
 
@@ -47,6 +51,39 @@ class Request:
     batch: int = 0
     base_version: int = -1    # spasgn: the version it updated
     new_version: int = -1     # spasgn: the version it produced
+    status: str = "pending"   # "ok" | "rejected" | "cancelled" | "failed"
+    error: str = ""
+    cancelled: bool = False   # set by the client; honoured until the request's batch starts
+
+
+def malformed(r: Request, n: int | None, nlabels: int | None) -> str:
+    """Why a request cannot be served ("" if it can): checked on the host at
+    admission, before it binds to a graph version."""
+    if r.kind == "spref":
+        if r.I is None:
+            return "spref without a vertex list"
+        x = np.asarray(r.I)
+        if x.ndim != 1 or not np.issubdtype(x.dtype, np.integer):
+            return "spref vertex list is not a 1-D integer array"
+        if n is not None and len(x) and (int(x.min()) < 0 or int(x.max()) >= n):
+            return "spref vertex out of range"
+        return ""
+    if r.kind == "contract":
+        if nlabels is not None and not (0 <= r.labels_id < nlabels):
+            return "unknown label set"
+        return ""
+    if r.kind == "spasgn":
+        if r.edges is None or len(r.edges) != 3:
+            return "spasgn without (u, v, w) edge arrays"
+        u, v, w = (np.asarray(a) for a in r.edges)
+        if not (u.ndim == v.ndim == w.ndim == 1 and len(u) == len(v) == len(w)):
+            return "spasgn edge arrays differ in shape"
+        if not all(np.issubdtype(a.dtype, np.integer) for a in (u, v, w)):
+            return "spasgn edge arrays are not integer"
+        if n is not None and len(u) and (min(int(u.min()), int(v.min())) < 0 or max(int(u.max()), int(v.max())) >= n):
+            return "spasgn endpoint out of range"
+        return ""
+    return f"unknown request kind {r.kind!r}"
 
 
 @dataclasses.dataclass
@@ -188,64 +225,40 @@ class Executor:
             return self._S[lid]
 
     def run_batch(self, batch, stream, writer_lock):
-        import torch
-        sprefs = [r for r in batch if r.kind == "spref"]
-        others = [r for r in batch if r.kind != "spref"]
-        if sprefs:
-            self._spref_batch(sprefs, stream)
-        for r in others:
-            if r.kind == "contract":
-                ver = self.store.get(r.version)
-                S, ST = self.contraction_ops(r.labels_id)
-                SA = H.spgemm("plus_times", S, ver.A64, stream=stream)
-                out = H.spgemm("plus_times", SA, ST, stream=stream)
-                r.result = out if self.keep else None
-            else:
-                with writer_lock:  # updates apply one after another, each to the latest version
-                    ver = self.store.get(self.store.latest())
-                    r.base_version = ver.vid
-                    Iv, Jv, B = update_operands(r.edges)
-                    Bd = H.DeviceCSR.from_host(B, device=self.device)
-                    C = H.spasgn(ver.A32, Iv, Jv, Bd, stream=stream)
-                    stream.synchronize()
-                    r.result = C if self.keep else None
-                    r.new_version = self.store.install(C)
+        """Runs each request of the batch on `stream`; a request whose call
+        fails is marked failed and the others still run."""
+        for r in batch:
+            try:
+                self._run_one(r, stream, writer_lock)
+                r.status = "ok"
+            except Exception as e:  # the library's status, reported per request
+                r.status, r.error, r.result = "failed", str(e), None
         stream.synchronize()
 
-    def _spref_batch(self, reqs, stream):
-        """A(I_r, I_r) for every request r: one stacked R*A, then one batched (RA)*Q."""
-        import torch
-        groups = {}
-        for r in reqs:
-            groups.setdefault(r.version, []).append(r)
-        for vid, rs in groups.items():
-            A = self.store.get(vid).A32
-            n = A.n
-            Is = [np.asarray(r.I, np.int32) for r in rs]
-            total = sum(len(x) for x in Is)
-            # stacked R: row t selects vertex I[t] (one nonzero per row)
-            Rcol = torch.from_numpy(np.concatenate(Is)).to(self.device, non_blocking=False)
-            Rptr = torch.arange(total + 1, dtype=torch.int64, device=self.device)
-            R = H.DeviceCSR(total, A.m, Rptr, Rcol, None, "bool")
-            RA = H.spgemm("select2nd", R, A, stream=stream)
-            # Q_r = sparse(I_r, 1:|I_r|, 1, n, |I_r|): row k holds the position of k in I_r
-            rp = RA.rowptr.cpu().numpy()  # one read of the stacked offsets for the batch
-            lefts, Qs, off = [], [], 0
-            for x in Is:
-                a, b = int(rp[off]), int(rp[off + len(x)])
-                lefts.append(H.DeviceCSR(len(x), n, RA.rowptr[off:off + len(x) + 1] - a, RA.col[a:b],
-                                         None if RA.val is None else RA.val[a:b], RA.dtype))
-                order = np.argsort(x, kind="stable")
-                counts = np.zeros(n + 1, np.int64)
-                counts[x.astype(np.int64) + 1] = 1
-                qptr = np.cumsum(counts)
-                Qs.append(H.DeviceCSR(n, len(x), torch.from_numpy(qptr).to(self.device),
-                                      torch.from_numpy(order.astype(np.int32)).to(self.device), None, "bool"))
-                off += len(x)
-            C, offs = H.spgemm_batched("select1st", lefts, Qs, stream=stream)
-            for i, r in enumerate(rs):
-                # rows offs[i]..offs[i+1] of the stacked result are request r's A(I, I)
-                r.result = (C, int(offs[i]), int(offs[i + 1]), len(Is[i])) if self.keep else None
+    def _run_one(self, r, stream, writer_lock):
+        if r.kind == "spref":
+            # A(I, I) by the library's gather: I goes to the device once, the
+            # selected rows are gathered, relabelled through I's inverse and
+            # ordered there (hs_spref)
+            A = self.store.get(r.version).A32
+            out = H.spref(A, r.I, r.I, stream=stream)
+            r.result = out if self.keep else None
+        elif r.kind == "contract":
+            ver = self.store.get(r.version)
+            S, ST = self.contraction_ops(r.labels_id)
+            SA = H.spgemm("plus_times", S, ver.A64, stream=stream)
+            out = H.spgemm("plus_times", SA, ST, stream=stream)
+            r.result = out if self.keep else None
+        else:
+            with writer_lock:  # updates apply one after another, each to the latest version
+                ver = self.store.get(self.store.latest())
+                r.base_version = ver.vid
+                Iv, Jv, B = update_operands(r.edges)
+                Bd = H.DeviceCSR.from_host(B, device=self.device)
+                C = H.spasgn(ver.A32, Iv, Jv, Bd, stream=stream)
+                stream.synchronize()
+                r.result = C if self.keep else None
+                r.new_version = self.store.install(C)
 
 
 def estimate_bytes(r: Request, A) -> int:
@@ -291,12 +304,21 @@ class Server:
         def work(batch, nbytes):
             s = stream_pool.get()
             try:
+                # a request cancelled before its batch starts is skipped
+                live = []
+                for r in batch:
+                    if r.cancelled:
+                        r.status = "cancelled"
+                        r.t_done = time.perf_counter() - t0
+                    else:
+                        live.append(r)
                 with torch.cuda.stream(s):
-                    for r in batch:
+                    for r in live:
                         r.t_start = time.perf_counter() - t0
-                    self.ex.run_batch(batch, s, writer_lock)
+                    if live:
+                        self.ex.run_batch(live, s, writer_lock)
                     now = time.perf_counter() - t0
-                    for r in batch:
+                    for r in live:
                         r.t_done = now
             except Exception as e:  # surfaced by run()
                 errors.append(e)
@@ -315,12 +337,23 @@ class Server:
         threads = []
         i = 0
         A0 = self.store.get(0).A32
+        n_cols = getattr(A0, "n", None)
+        nlabels = len(self.ex.labels) if hasattr(self.ex, "labels") else None
         while i < len(pending) or not ready.empty():
-            # admit everything that has arrived
+            # admit everything that has arrived; malformed or already
+            # cancelled requests finish here, bound to no version
             now = time.perf_counter() - t0
             while i < len(pending) and (pending[i].arrival <= now or not realtime):
-                ready.put(pending[i])
+                r = pending[i]
                 i += 1
+                why = malformed(r, n_cols, nlabels)
+                if why or r.cancelled:
+                    r.status, r.error = ("rejected", why) if why else ("cancelled", "")
+                    r.t_admit = r.t_done = time.perf_counter() - t0
+                    with done_lock:
+                        done.append(r)
+                    continue
+                ready.put(r)
             if ready.empty():
                 time.sleep(max(0.0, min(0.002, pending[i].arrival - now)) if i < len(pending) else 0)
                 continue
@@ -379,8 +412,18 @@ def run_serial(store: GraphStore, executor: Executor, requests):
 
 
 def latency_summary(done, makespan):
-    out = {"requests": len(done), "makespan_s": makespan,
-           "req_per_s": len(done) / makespan if makespan else None}
+    """Latency percentiles and rate over the requests that were served (a
+    request that ran has status "ok"; pending means a scheduler without
+    statuses, as in the serial loop); rejected, cancelled and failed requests
+    are counted beside them."""
+    served = [r for r in done if r.status in ("ok", "pending")]
+    out = {"requests": len(served), "makespan_s": makespan,
+           "req_per_s": len(served) / makespan if makespan else None}
+    for st in ("rejected", "cancelled", "failed"):
+        k = sum(1 for r in done if r.status == st)
+        if k:
+            out[st] = k
+    done = served
     for kind in ("spref", "contract", "spasgn"):
         lat = np.array([r.t_done - r.arrival for r in done if r.kind == kind])
         if len(lat):

@@ -89,3 +89,40 @@ def test_sparse_argument_checks_without_gpu():
         got = L.hs_sparse(*args, ctypes.byref(c), None, None, 0)
         assert got == want, (args, got)
         assert not c.ptr and not c.idx and not c.val  # nothing left allocated
+
+
+def test_noalloc_argument_checks_without_gpu():
+    """hs_spgemm_noalloc rejects missing input arrays with HS_EINVAL before any
+    CUDA call (a null offset or column array would otherwise be read by its
+    first kernel), the same checks hs_spgemm makes."""
+    from paper_1109_3739_gb300 import hspgemm as H
+    L = H.library()
+    L.hs_spgemm_noalloc.restype = ctypes.c_int
+    L.hs_spgemm_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(H.hs_mat), ctypes.POINTER(H.hs_mat),
+                                    ctypes.POINTER(H.hs_mat), ctypes.c_int64, ctypes.c_void_p]
+    dummy = (ctypes.c_int64 * 8)()
+    p = ctypes.addressof(dummy)  # never dereferenced: every call below fails its checks first
+    PT, F32 = H.SEMIRING["plus_times"], H.DTYPE["f32"]
+
+    def mat(m, n, nnz, ptr=p, idx=p, val=p):
+        x = H.hs_mat()
+        x.fmt, x.dtype, x.m, x.n, x.nnz = 0, F32, m, n, nnz  # HS_CSR
+        x.ptr, x.idx, x.val = ptr, idx, val
+        return x
+
+    cases = [
+        (mat(4, 4, 3, ptr=None), mat(4, 4, 3)),   # A without offsets
+        (mat(4, 4, 3, idx=None), mat(4, 4, 3)),   # A without column ids
+        (mat(4, 4, 3), mat(4, 4, 3, ptr=None)),   # B without offsets
+        (mat(4, 4, 3), mat(4, 4, 3, idx=None)),   # B without column ids
+        (mat(4, 4, 3, val=None), mat(4, 4, 3)),   # (+,x) without values
+        (mat(4, 4, 3), mat(5, 4, 3)),             # inner dimensions differ
+    ]
+    for A, B in cases:
+        C = mat(0, 0, 0)
+        got = L.hs_spgemm_noalloc(PT, ctypes.byref(A), ctypes.byref(B), ctypes.byref(C), 16, None)
+        assert got == -1, got
+    # a missing C->ptr, and C->idx with a capacity
+    A, B = mat(4, 4, 3), mat(4, 4, 3)
+    for C in (mat(0, 0, 0, ptr=None), mat(0, 0, 0, idx=None)):
+        assert L.hs_spgemm_noalloc(PT, ctypes.byref(A), ctypes.byref(B), ctypes.byref(C), 16, None) == -1

@@ -35,6 +35,7 @@ def test_serving_mix_matches_alone_and_oracle():
     srv = S.Server(store, ex, slots=4, max_batch=8, mem_budget=1 << 30)
     done, makespan = srv.run(reqs)
     assert len(done) == len(reqs)
+    assert all(r.status == "ok" for r in done), [(r.rid, r.status, r.error) for r in done if r.status != "ok"]
     assert max(r.batch for r in done) < len(done)  # some batch held several requests
     starts = sorted((r.t_start, r.t_done) for r in done)
     overlap = any(starts[i + 1][0] < starts[i][1] for i in range(len(starts) - 1))

@@ -182,3 +182,78 @@ def test_latency_summary():
     assert out["spref"]["n"] == 2 and abs(out["spref"]["p50_ms"] - 15.0) < 1e-9
     assert abs(out["contract"]["p99_ms"] - 50.0) < 1e-9
     assert abs(out["all"]["p50_ms"] - 25.0) < 1e-9
+
+
+def test_malformed_requests_are_rejected_at_admission(no_cuda_streams):
+    store = FakeStore()
+    store.graph.A32.n = 100  # vertices 0..99
+    ex = FakeExecutor(store)
+    ex.labels = [None]       # one label set
+    reqs = _requests(30, seed=7)
+    bad = [
+        S.Request(100, "spref", 0.0, I=np.array([3, 100], np.int32)),          # vertex out of range
+        S.Request(101, "spref", 0.0, I=np.array([1.0, 2.0])),                   # not integer
+        S.Request(102, "contract", 0.0, labels_id=3),                           # unknown label set
+        S.Request(103, "spasgn", 0.0, edges=(np.zeros(3, np.int32), np.zeros(2, np.int32),
+                                             np.ones(3, np.int32))),            # ragged arrays
+        S.Request(104, "spasgn", 0.0, edges=(np.array([-1], np.int32), np.zeros(1, np.int32),
+                                             np.ones(1, np.int32))),            # endpoint out of range
+        S.Request(105, "pagerank", 0.0),                                        # unknown kind
+        S.Request(106, "spref", 0.0),                                           # no vertex list
+    ]
+    done, _ = S.Server(store, ex, slots=2, max_batch=4, mem_budget=1 << 40).run(reqs + bad, realtime=False)
+    assert sorted(r.rid for r in done) == sorted(r.rid for r in reqs + bad)
+    served = sorted(rid for b in ex.batches for rid in b)
+    assert served == sorted(r.rid for r in reqs)  # the good ones, once each; no bad one ran
+    for r in bad:
+        assert r.status == "rejected" and r.error, (r.rid, r.status, r.error)
+        assert r.version == -1                    # never bound to a graph version
+    out = S.latency_summary(done, 1.0)
+    assert out["rejected"] == len(bad) and out["requests"] == len(reqs)
+
+
+def test_cancelled_requests_are_skipped(no_cuda_streams):
+    store = FakeStore()
+    ex = FakeExecutor(store, sleep=0.05)
+    reqs = _requests(8, seed=9)
+    reqs[2].cancelled = True  # cancelled before it arrives
+    server = S.Server(store, ex, slots=1, max_batch=1, mem_budget=1 << 40)
+
+    def cancel_later():  # while request 0 runs, request 6 still waits for the one slot
+        time.sleep(0.02)
+        reqs[6].cancelled = True
+
+    th = threading.Thread(target=cancel_later)
+    th.start()
+    done, _ = server.run(reqs, realtime=False)
+    th.join()
+    served = [rid for b in ex.batches for rid in b]
+    assert 2 not in served and 6 not in served
+    assert sorted(served) == [r.rid for r in reqs if r.rid not in (2, 6)]
+    assert reqs[2].status == "cancelled" and reqs[6].status == "cancelled"
+    assert len(done) == len(reqs)
+    assert not ex.missing_versions
+
+
+def test_a_failing_request_does_not_sink_its_batch():
+    import torch
+
+    class Stream:
+        def synchronize(self):
+            pass
+
+    store = FakeStore()
+    ex = S.Executor(store, [np.zeros(4, np.int32)], device="cpu")
+    ran = []
+
+    def run_one(r, stream, writer_lock):
+        if r.rid == 1:
+            raise RuntimeError("hs_spref: HS_EINVAL")
+        ran.append(r.rid)
+
+    ex._run_one = run_one
+    batch = [S.Request(i, "spref", 0.0, I=np.arange(3, dtype=np.int32)) for i in range(4)]
+    ex.run_batch(batch, Stream(), threading.Lock())
+    assert ran == [0, 2, 3]
+    assert [r.status for r in batch] == ["ok", "failed", "ok", "ok"]
+    assert "HS_EINVAL" in batch[1].error and batch[1].result is None

@@ -30,6 +30,10 @@ def H():
 
 CASES = [
     ("plus_times", "f32", lambda: I.rmat_matrix(14, 8, seed=91, dtype="f32")),
+    # scale 16: rows with more products than the large tier, so the entry
+    # point's own heavy path (part bitmaps built from the products, segment
+    # ends found by search) runs
+    ("plus_times", "f32", lambda: I.rmat_matrix(16, 8, seed=96, dtype="f32")),
     ("plus_times", "f64", lambda: I.er_matrix(4096, 4096, 8, seed=1, dtype="f64")),
     ("plus_times", "i64", lambda: I.rmat_matrix(13, 8, seed=92, dtype="i64", kind="signed")),
     ("or_and", "bool", lambda: I.rmat_matrix(14, 8, seed=93, dtype="bool")),
@@ -37,7 +41,26 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("sr,dt,make", CASES, ids=[f"{c[0]}-{c[1]}" for c in CASES])
+def _raw_noalloc(h, sr, dA, capacity, out_dt):
+    """Output arrays allocated beforehand and a function making one bare call
+    of the C entry point into them: (rowptr, col, val, A's descriptor, C's
+    descriptor, call)."""
+    import ctypes
+    import torch
+    L = h.library()
+    tdt = {"f64": torch.float64, "f32": torch.float32, "i32": torch.int32, "i64": torch.int64}.get(out_dt)
+    rowptr = torch.empty(dA.m + 1, dtype=torch.int64, device=dA.rowptr.device)
+    col = torch.empty(max(capacity, 1), dtype=torch.int32, device=dA.rowptr.device)
+    val = None if tdt is None else torch.empty(max(capacity, 1), dtype=tdt, device=dA.rowptr.device)
+    a = dA.desc()
+    c = h.hs_mat(0, 0, 0, 0, 0, 0, rowptr.data_ptr(), col.data_ptr(), None,
+                 None if val is None else val.data_ptr())
+    return (rowptr, col, val, a, c,
+            lambda: L.hs_spgemm_noalloc(h.SEMIRING[sr], ctypes.byref(a), ctypes.byref(a), ctypes.byref(c),
+                                        int(capacity), None))
+
+
+@pytest.mark.parametrize("sr,dt,make", CASES, ids=[f"{c[0]}-{c[1]}-{i}" for i, c in enumerate(CASES)])
 def test_noalloc_matches_allocating_entry_point(sr, dt, make):
     import torch
     h = H()
@@ -45,24 +68,40 @@ def test_noalloc_matches_allocating_entry_point(sr, dt, make):
     dA = h.DeviceCSR.from_host(A)
     ref = h.spgemm(sr, dA, dA)
     ref_host = ref.to_host()
-    bound = None
-    if dt in ("f32", "f64"):
-        _, bound = oracle.spgemm(sr, A, A, with_bound=True)
-    free_before = None
+    nnz = ref.nnz
+    del ref
+    R, bound = oracle.spgemm(sr, A, A, with_bound=True)
+    out_dt = "bool" if sr == "or_and" else dt
+    rowptr, col, val, a, c, call_abi = _raw_noalloc(h, sr, dA, nnz, out_dt)
     for call in range(2):  # two calls in a row share the fixed scratch
-        C = h.spgemm_noalloc(sr, dA, dA, capacity=ref.nnz)
+        # hand back what the library's pool and torch's cache keep, so that
+        # any allocation inside the call would show as less free memory
+        h.trim_memory()
         torch.cuda.synchronize()
-        if call == 1:
-            # the second call allocates nothing: device free memory is unchanged
-            assert torch.cuda.mem_get_info()[0] == free_before
-        got = C.to_host()
-        if bound is not None:
-            assert_within(got, ref_host, bound, dt, f"noalloc call {call}")
+        torch.cuda.empty_cache()
+        free0 = torch.cuda.mem_get_info()[0]
+        st = call_abi()
+        torch.cuda.synchronize()
+        free1 = torch.cuda.mem_get_info()[0]
+        assert st == 0, h.HsError(st, "hs_spgemm_noalloc")
+        if call == 1:  # the first call may load kernel modules lazily
+            assert free1 == free0, f"device free memory changed by {free0 - free1} bytes"
+        got = h.DeviceCSR(c.m, c.n, rowptr, col[:c.nnz], None if val is None else val[:c.nnz],
+                          h.DTYPE_NAME[c.dtype]).to_host()
+        # against the allocating entry point: same structure, and the oracle
+        # decides the values (bit for bit for the exact semirings)
+        assert np.array_equal(got.rowptr, ref_host.rowptr) and np.array_equal(got.col, ref_host.col)
+        if dt in ("f32", "f64"):
+            assert_within(got, R, bound, dt, f"noalloc call {call}")
+            assert_within(ref_host, R, bound, dt, "hs_spgemm")
         else:
-            assert_bitexact(got, ref_host, f"noalloc call {call}")
-        del C, got
-        torch.cuda.synchronize()
-        free_before = torch.cuda.mem_get_info()[0]
+            assert_bitexact(got, R, f"noalloc call {call}")
+        # a stale value from the previous call must not survive: scribble
+        # over the outputs before the second call
+        col.fill_(-1)
+        if val is not None:
+            val.fill_(0)
+        rowptr.fill_(-1)
 
 
 def test_noalloc_capacity_and_scratch_limits():
