@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=2000)
     ap.add_argument("--requests", type=int, default=400)
     ap.add_argument("--rate", type=float, default=0.0, help="serving: arrivals per second (0: sweep)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="rmat: skip the other configurations' measurements (ER, (or,and), (min,+), Galerkin, "
+                         "SpRef, batched, serving) that the default line carries under 'configs'")
     return ap.parse_args()
 
 
@@ -112,11 +115,22 @@ def make_input(scale):
 
 
 def row_flops(A):
-    deg = np.diff(A.rowptr)
-    rows = np.repeat(np.arange(A.m), deg)
+    return row_flops_ab(A, A)
+
+
+def row_flops_ab(A, B):
+    """Products per row of A*B: sum over A(i,k) of nnz(B(k,:))."""
+    deg_b = np.diff(B.rowptr)
+    rows = np.repeat(np.arange(A.m), np.diff(A.rowptr))
     f = np.zeros(A.m, np.int64)
-    np.add.at(f, rows, deg[A.col])
+    np.add.at(f, rows, deg_b[A.col])
     return f
+
+
+def row_flops_ab_dev(dA, B):
+    """Total products of A*B with A on the device (its columns copied back)."""
+    deg_b = np.diff(B.rowptr)
+    return int(deg_b[dA.col.cpu().numpy()].sum())
 
 
 # ------------------------------------------------------------------ clocks
@@ -304,7 +318,7 @@ def run_batched(args):
     hbm, peak_kind = peaks()
     nnz_a = sum(a.nnz for a, _ in probs) + sum(b.nnz for _, b in probs)
     alg = nnz_a * 12 + sum(a.m + b.m + 2 for a, b in probs) * 8 + nnz_c * 12 + sum(a.m + 1 for a, _ in probs) * 8
-    print(json.dumps({
+    return {
         "metric": METRIC, "value": flops / (med_b / 1000.0), "unit": "mults/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": med_b, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -322,7 +336,7 @@ def run_batched(args):
         "gpu_launches": nb_launch,
         "tuning": tuning,
         "phases_ms_per_step": phases,
-    }), flush=True)
+    }
 
 
 # ------------------------------------------------------------------ serving
@@ -367,7 +381,7 @@ def run_serving(args):
         out["runs"].append({"rate": rate, **res})
     last = out["runs"][-1]
     out["value"] = last["batched"]["req_per_s"]
-    print(json.dumps(out), flush=True)
+    return out
 
 
 # -------------------------------------------------------------------- SpRef
@@ -592,15 +606,151 @@ def run_sparse(args):
     }), flush=True)
 
 
+# ------------------------------------------- the other configurations
+def time_device(fn, steps, warmup, flush, stream):
+    """Median CUDA-event milliseconds of fn() over `steps` runs after `warmup`
+    untimed ones, L2 flushed before each; also the library's kernel launches
+    per run and the last result."""
+    import torch
+
+    from paper_1109_3739_gb300 import hspgemm as h
+    out = None
+    for _ in range(warmup):
+        out = None
+        out = fn()
+    torch.cuda.synchronize()
+    l0 = h.launch_count()
+    ts = []
+    for _ in range(steps):
+        flush.fill_(1)
+        out = None
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts), (h.launch_count() - l0) // max(1, steps), out
+
+
+def csr_bytes(m, nnz, vb):
+    return (m + 1) * 8 + nnz * (4 + vb)
+
+
+def run_configs(args, A, dA, dev, stream, flush):
+    """Every other configuration of the benchmark set, measured in the same
+    run on the same GPU: C = A*A over (or,and) and (min,+) f32 on the R-MAT
+    scale-20 graph; Erdos-Renyi n=4096 f64; the Galerkin product R*A*R^T on
+    the 128^3 Laplacian; SpRef A(I,J) with |I| = |J| = 2^18 on the scale-20
+    graph; 2000 batched ER products; the serving stream on the scale-22
+    graph.  Each entry: median ms, rate, whole-operation fraction of the
+    measured HBM copy bandwidth (algorithmic bytes: inputs read once, output
+    written once) and launches."""
+    import torch
+
+    from paper_1109_3739_gb300 import hspgemm as h
+    from paper_1109_3739_gb300 import inputs as I
+    hbm, _ = peaks()
+    steps, warm = 3, 1
+    out = {}
+
+    def entry(ms, launches, units, unit, alg):
+        return {"ms": ms, "value": units / (ms / 1000.0), "unit": unit, "gpu_launches": launches,
+                "step_hbm_fraction": alg / (ms / 1000.0) / 1e9 / hbm, "alg_bytes": alg}
+
+    f = row_flops(A)
+    flops = int(f.sum())
+    # config 2, the other two semirings on the same graph
+    dAb = h.DeviceCSR(dA.m, dA.n, dA.rowptr, dA.col, None, "bool")
+    ms, nl, C = time_device(lambda: h.spgemm("or_and", dAb, dAb, stream=stream), steps, warm, flush, stream)
+    nnz_c = C.nnz
+    C = None
+    out["rmat20_AxA_or_and"] = {**entry(ms, nl, flops, "mults/s", 3 * (A.m + 1) * 8 + 2 * A.nnz * 4 + nnz_c * 4),
+                                "nnz_C": nnz_c}
+    ms, nl, C = time_device(lambda: h.spgemm("min_plus", dA, dA, stream=stream), steps, warm, flush, stream)
+    out["rmat20_AxA_min_plus_f32"] = {**entry(ms, nl, flops, "mults/s", 2 * csr_bytes(A.m, A.nnz, 4) +
+                                              csr_bytes(A.m, C.nnz, 4)), "nnz_C": C.nnz}
+    C = None
+    dAb = None
+    torch.cuda.empty_cache()
+    # config 1: ER n = 4096, 8 nonzeros per column, f64
+    E = I.er_matrix(4096, 4096, 8, seed=1, dtype="f64")
+    dE = h.DeviceCSR.from_host(E, device=dev)
+    fe = int(row_flops(E).sum())
+    ms, nl, C = time_device(lambda: h.spgemm("plus_times", dE, dE, stream=stream), 10, 3, flush, stream)
+    out["er4096_AxA_f64"] = {**entry(ms, nl, fe, "mults/s", 2 * csr_bytes(E.m, E.nnz, 8) + csr_bytes(E.m, C.nnz, 8)),
+                             "nnz_C": C.nnz}
+    C = dE = None
+    # config 3a: Galerkin R*A*R^T, 7-point Laplacian on 128^3, 2x2x2 aggregation, f64
+    L = I.laplacian7(128, "f64")
+    R = I.aggregation_R(128, 2, "f64")
+    RT = I.aggregation_RT(128, 2, "f64")
+    dL, dR, dRT = (h.DeviceCSR.from_host(x, device=dev) for x in (L, R, RT))
+    fg = int(row_flops_ab(R, L).sum())
+
+    def galerkin():
+        RA = h.spgemm("plus_times", dR, dL, stream=stream)
+        return RA, h.spgemm("plus_times", RA, dRT, stream=stream)
+
+    ms, nl, (RA, G) = time_device(galerkin, steps, warm, flush, stream)
+    fg += int(row_flops_ab_dev(RA, RT))
+    alg = (csr_bytes(R.m, R.nnz, 8) + csr_bytes(L.m, L.nnz, 8) + csr_bytes(RA.m, RA.nnz, 8) * 2 +
+           csr_bytes(RT.m, RT.nnz, 8) + csr_bytes(G.m, G.nnz, 8))
+    out["galerkin128_RART_f64"] = {**entry(ms, nl, fg, "mults/s", alg), "nnz_RA": RA.nnz, "nnz_C": G.nnz}
+    RA = G = dL = dR = dRT = None
+    # config 3b: SpRef A(I, J), I and J random sorted subsets of 2^18 vertices
+    Iv = I.random_subset_sorted(A.n, 1 << 18, seed=3, stream=8)
+    Jv = I.random_subset_sorted(A.n, 1 << 18, seed=3, stream=9)
+    dI = torch.from_numpy(Iv.astype(np.int32)).to(dev)
+    dJ = torch.from_numpy(Jv.astype(np.int32)).to(dev)
+    ms, nl, B = time_device(lambda: h.spref(dA, dI, dJ, stream=stream), 10, 3, flush, stream)
+    deg = np.diff(A.rowptr)
+    gathered = int(deg[Iv].sum())
+    alg = (len(Iv) + len(Jv)) * 4 + len(Iv) * 16 + gathered * 8 + csr_bytes(B.m, B.nnz, 4)
+    out["spref_rmat20_2^18x2^18"] = {**entry(ms, nl, B.nnz, "entries/s", alg), "nnz_B": B.nnz,
+                                      "gathered": gathered}
+    B = dI = dJ = None
+    torch.cuda.empty_cache()
+    # config 4: 2000 batched ER products (one batched call against one call per problem)
+    sub = argparse.Namespace(**vars(args))
+    sub.steps, sub.warmup, sub.no_tune, sub.batch = 3, 1, True, 2000
+    b = run_batched(sub)
+    out["batched_er2000_f64"] = {"ms": b["ms_per_step"], "value": b["value"], "unit": "mults/s",
+                                 "gpu_launches": b["gpu_launches"],
+                                 "step_hbm_fraction": b["config"]["step_hbm_fraction"],
+                                 "one_call_per_problem_ms": b["one_call_per_problem"]["ms_per_step"],
+                                 "speedup_vs_one_call_per_problem": b["speedup_vs_one_call_per_problem"],
+                                 "numeric_graph_replay_ms": b["numeric_graph_replay"]["ms_per_step"]}
+    torch.cuda.empty_cache()
+    # config 5: the serving stream on the resident scale-22 graph (one arrival rate)
+    sub = argparse.Namespace(**vars(args))
+    sub.rate, sub.requests = 80.0, 200
+    sv = run_serving(sub)
+    run = sv["runs"][-1]
+    out["serving_rmat22_ef16_i32"] = {"rate": run["rate"], "requests": sub.requests,
+                                      "value": run["batched"]["req_per_s"], "unit": "req/s",
+                                      "p50_ms": run["batched"]["all"]["p50_ms"],
+                                      "p99_ms": run["batched"]["all"]["p99_ms"],
+                                      "serial_req_per_s": run["serial"]["req_per_s"],
+                                      "serial_p50_ms": run["serial"]["all"]["p50_ms"],
+                                      "serial_p99_ms": run["serial"]["all"]["p99_ms"],
+                                      "per_kind": run["batched"]}
+    torch.cuda.empty_cache()
+    return out
+
+
 # ----------------------------------------------------------------- GPU arm
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
-        return run_batched(args)
+        print(json.dumps(run_batched(args)), flush=True)
+        return
     if args.workload == "serving":
-        return run_serving(args)
+        print(json.dumps(run_serving(args)), flush=True)
+        return
     if args.workload == "sparse":
         return run_sparse(args)
     if args.workload == "tallskinny":
@@ -631,6 +781,54 @@ def main():
     def step():
         return h.spgemm("plus_times", dA, dA, stream=stream)
 
+    # nnz(C) and C's row offsets from one product (they size the end-to-end
+    # leg's pinned arrays and the roofline's bins); then torch's cache is
+    # emptied so the end-to-end leg starts from a clean device
+    C = step()
+    torch.cuda.synchronize(dev)
+    nnz_c = C.nnz
+    c_rowptr = C.rowptr.cpu().numpy()
+    C = None
+    torch.cuda.empty_cache()
+
+    # ---- end to end, first (before any other large allocation): pinned
+    # host A -> device, product, C -> pinned host, through hs_spgemm_to_host
+    e2e = None
+    if args.e2e_steps > 0 and rank == 0:
+        hA = [torch.from_numpy(np.asarray(x)).pin_memory() for x in (A.rowptr, A.col, A.val)]
+        h2d = sum(t.numel() * t.element_size() for t in hA)
+        out_rp = torch.empty(A.m + 1, dtype=torch.int64, pin_memory=True)
+        out_j = torch.empty(nnz_c, dtype=torch.int32, pin_memory=True)
+        out_v = torch.empty(nnz_c, dtype=torch.float32, pin_memory=True)
+        d2h = out_rp.numel() * 8 + nnz_c * 8
+        etimes, h2d_ms = [], []
+        for i in range(args.e2e_steps + 1):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            eh0 = torch.cuda.Event(enable_timing=True)
+            eh1 = torch.cuda.Event(enable_timing=True)
+            eh0.record(stream)
+            rp, cj, cv = (t.to(dev, non_blocking=True) for t in hA)
+            eh1.record(stream)
+            M = h.DeviceCSR(A.m, A.n, rp, cj, cv, "f32")
+            got = h.spgemm_to_host("plus_times", M, M, out_rp, out_j, out_v, blocks=E2E_BLOCKS,
+                                   stage_on_device=True, stream=stream)
+            torch.cuda.synchronize(dev)
+            dt = time.perf_counter() - t0
+            assert got == nnz_c
+            M = rp = cj = cv = None
+            if i > 0:
+                etimes.append(dt)
+                h2d_ms.append(eh0.elapsed_time(eh1))
+        e2e = {"value": flops / statistics.median(etimes), "unit": "mults/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": 1000 * statistics.median(etimes),
+               "h2d_ms": statistics.median(h2d_ms),
+               "product_and_d2h_ms": 1000 * statistics.median(etimes) - statistics.median(h2d_ms),
+               "api": f"spgemm_to_host, {E2E_BLOCKS} row blocks"}
+        hA = out_rp = out_j = out_v = None
+        torch.cuda.empty_cache()
+
     tuning = None
     if not args.no_tune:  # row-bin thresholds picked by measurement on this workload
         from paper_1109_3739_gb300 import tune
@@ -643,8 +841,6 @@ def main():
         C = None
         C = step()
     torch.cuda.synchronize(dev)
-    nnz_c = C.nnz
-    c_rowptr = C.rowptr.cpu().numpy()
     C = None
 
     if dist:
@@ -729,35 +925,6 @@ def main():
     step_bytes = 2 * ((A.m + 1) * 8 + A.nnz * (4 + vb)) + (A.m + 1) * 8 + nnz_c * (4 + vb)
     step_ms = total_ms / args.steps
 
-    # ---- end to end: pinned host A -> device, product, C -> pinned host
-    e2e = None
-    if args.e2e_steps > 0 and rank == 0:
-        hA = [torch.from_numpy(np.asarray(x)).pin_memory() for x in (A.rowptr, A.col, A.val)]
-        h2d = sum(t.numel() * t.element_size() for t in hA)
-        out_rp = torch.empty(A.m + 1, dtype=torch.int64, pin_memory=True)
-        out_j = torch.empty(nnz_c, dtype=torch.int32, pin_memory=True)
-        out_v = torch.empty(nnz_c, dtype=torch.float32, pin_memory=True)
-        d2h = out_rp.numel() * 8 + nnz_c * 8
-        etimes = []
-        for i in range(args.e2e_steps + 1):
-            torch.cuda.synchronize(dev)
-            t0 = time.perf_counter()
-            rp, cj, cv = (t.to(dev, non_blocking=True) for t in hA)
-            M = h.DeviceCSR(A.m, A.n, rp, cj, cv, "f32")
-            # the product comes back to the pinned host arrays row block by row
-            # block, each block's copy beside the next block's product
-            got = h.spgemm_to_host("plus_times", M, M, out_rp, out_j, out_v, blocks=E2E_BLOCKS,
-                                   stage_on_device=True, stream=stream)
-            torch.cuda.synchronize(dev)
-            dt = time.perf_counter() - t0
-            assert got == nnz_c
-            M = None
-            if i > 0:
-                etimes.append(dt)
-        e2e = {"value": flops / statistics.median(etimes), "unit": "mults/s",
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "ms_per_step": 1000 * statistics.median(etimes), "api": f"spgemm_to_host, {E2E_BLOCKS} row blocks"}
-
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
@@ -781,6 +948,11 @@ def main():
         C = None
     unsorted = {"ms_per_step": statistics.median(uts), "value": flops / (statistics.median(uts) / 1000.0),
                 "steps": len(uts), "what": "rows in any column order (HS_FLAG_UNSORTED), same product"}
+    torch.cuda.empty_cache()
+
+    configs = None
+    if rank == 0 and world == 1 and not args.no_configs and args.scale == 20:
+        configs = run_configs(args, A, dA, dev, stream, flush)
 
     if rank == 0:
         print(json.dumps({
@@ -796,6 +968,7 @@ def main():
             "gpu_launches": launches,
             "tuning": tuning,
             "unsorted_output": unsorted,
+            "configs": configs,
             "phases_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         }), flush=True)
     if dist:

@@ -242,14 +242,18 @@ template <> __device__ __forceinline__ NoVal shfl_val<NoVal>(NoVal x, int) { ret
 // consecutive entries of B (coalesced, no search).  The remaining short
 // segments are dealt one product per lane: lane l takes product base+l of
 // their concatenation and finds its segment by a binary search over the
-// inclusive length scan (shuffles only).  visit(col, prod, p) runs on every
-// lane that holds a product, p being the product's index in the order of the
-// segments (as if they were walked lane by lane).  Returns the number of
-// products.  All 32 lanes must call this together.
-template <class SR, int U = 2, class Visit>
+// inclusive length scan (shuffles only).  SB such rounds are taken at once,
+// their B loads all issued before the first visit, so a lane has SB
+// independent reads in flight instead of one round trip per round.
+// visit(col, prod, p) runs on every lane that holds a product, p being the
+// product's index in the order of the segments (as if they were walked lane
+// by lane).  Returns the number of products.  All 32 lanes must call this
+// together.
+template <class SR, int U = 2, int SB = 4, class Visit>
 __device__ __forceinline__ int warp_expand(const DevCsr &B, int64_t s, int len, typename SR::val_t a,
                                             Visit &visit) {
   using T = typename SR::val_t;
+  using VisitT = std::decay_t<Visit>;
   const int lane = lane_id();
   const int incl = warp_incl_scan(len);
   const int total = __shfl_sync(FULL, incl, 31);
@@ -278,8 +282,8 @@ __device__ __forceinline__ int warp_expand(const DevCsr &B, int64_t s, int len, 
         if constexpr (SR::needs_b)
           if (ok) b[u] = __ldg(bv + off + 32 * u);
       }
-      if constexpr (two_stage<std::decay_t<Visit>>::value) {
-        typename std::decay_t<Visit>::State st[U];
+      if constexpr (two_stage<VisitT>::value) {
+        typename VisitT::State st[U];
 #pragma unroll
         for (int u = 0; u < U; ++u)
           if (off + 32 * u < ll) st[u] = visit.prep(c[u]);
@@ -299,34 +303,60 @@ __device__ __forceinline__ int warp_expand(const DevCsr &B, int64_t s, int len, 
       }
     }
   }
-  // short segments: one product per lane
+  // short segments: one product per lane, SB rounds of 32 at a time
   const int slen = len < 32 ? len : 0;
   const int sincl = warp_incl_scan(slen);
   const int stotal = __shfl_sync(FULL, sincl, 31);
-  for (int base = 0; base < stotal; base += 32) {
-    const int p = base + lane;
-    int src = 0;  // number of lanes whose inclusive end is <= p
+  const int sexcl = sincl - slen;
+  for (int base = 0; base < stotal; base += 32 * SB) {
+    int col[SB], pidx[SB];
+    T pv[SB];
+    bool ok[SB];
 #pragma unroll
-    for (int step = 16; step >= 1; step >>= 1) {
-      int v = __shfl_sync(FULL, sincl, src + step - 1);
-      if (v <= p) src += step;
-    }
-    const int64_t ss = __shfl_sync(FULL, s, src);
-    const int sex = __shfl_sync(FULL, sincl - slen, src);
-    const int fex = __shfl_sync(FULL, ex_full, src);
-    const T aa = shfl_val<T>(a, src);
-    if (p < stotal) {
-      const int64_t pos = ss + (p - sex);
-      if (HS_G(B.dbg, pos >= 0 && pos < B.nnz, 4, pos)) {
-        const int col = __ldg(B.j + pos);
-        if constexpr (SR::has_val) {
-          T b{};
-          if constexpr (SR::needs_b) b = load_val<T>(B.v, pos);
-          visit(col, SR::mul(aa, b), fex + (p - sex));
-        } else {
-          visit(col, NoVal{}, fex + (p - sex));
+    for (int u = 0; u < SB; ++u) {
+      ok[u] = false;
+      col[u] = 0;
+      pidx[u] = 0;
+      pv[u] = T{};
+      if (base + 32 * u < stotal) {  // warp-uniform: the shuffles below see every lane
+        const int p = base + 32 * u + lane;
+        int src = 0;  // number of lanes whose inclusive end is <= p
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+          const int v = __shfl_sync(FULL, sincl, src + step - 1);
+          if (v <= p) src += step;
+        }
+        const int64_t ss = __shfl_sync(FULL, s, src);
+        const int sex = __shfl_sync(FULL, sexcl, src);
+        const int fex = __shfl_sync(FULL, ex_full, src);
+        const T aa = shfl_val<T>(a, src);
+        if (p < stotal) {
+          const int64_t pos = ss + (p - sex);
+          if (HS_G(B.dbg, pos >= 0 && pos < B.nnz, 4, pos)) {
+            ok[u] = true;
+            col[u] = __ldg(B.j + pos);
+            pidx[u] = fex + (p - sex);
+            if constexpr (SR::has_val) {
+              T b{};
+              if constexpr (SR::needs_b) b = load_val<T>(B.v, pos);
+              pv[u] = SR::mul(aa, b);
+            }
+          }
         }
       }
+    }
+    if constexpr (two_stage<VisitT>::value) {
+      typename VisitT::State st[SB];
+#pragma unroll
+      for (int u = 0; u < SB; ++u)
+        if (ok[u]) st[u] = visit.prep(col[u]);
+#pragma unroll
+      for (int u = 0; u < SB; ++u)
+        if (ok[u]) visit.commit(st[u], pv[u]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < SB; ++u)
+        if (ok[u]) visit(col[u], pv[u], pidx[u]);
     }
   }
   return total;

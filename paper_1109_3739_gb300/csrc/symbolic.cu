@@ -131,10 +131,10 @@ __global__ void __launch_bounds__(NT) k_sym_cta(SymArgs a) {
 }
 
 // --------------------------------------------------------------- heavy
-// Per row and per chunk of 2^20 columns: the products set their bits, and a
-// bit that was clear counts one new column of its 4096-column segment.  The
-// segment counts give the chunk's histogram and, scanned, each segment's
-// place in the row's sorted column list.  Each warp then walks pairs of
+// Per row and per chunk of 2^20 columns: the products set their bits (an OR
+// whose old value nobody waits for), then each 4096-column segment's bits are
+// counted by popcount.  The segment counts give the chunk's histogram and,
+// scanned, each segment's place in the row's sorted column list.  Each warp then walks pairs of
 // segments, every lane eight consecutive words: the lanes' bit counts are
 // scanned across the warp, the columns go to a per-warp staging buffer in
 // ascending order and leave it in coalesced stores.
@@ -142,29 +142,17 @@ constexpr int SH_SEGS = BITMAP_COLS / SEG_W;  // segments per chunk (256)
 constexpr int SH_BUF = 384;                   // per-warp list staging entries
 static_assert(SEG_W == 4096, "two segments are 256 words: eight per lane");
 
-// Product visitor: prep sets the column's bit (the old word comes back),
-// commit counts the column for its segment if the bit was clear.
+// Product visitor: sets the column's bit; the old word is not needed (the
+// segment counts come from the finished bitmap), so no lane waits for it.
 struct SymHeavyBit {
-  static constexpr bool kTwoStage = true;
-  struct State {
-    unsigned old, bit;
-    int seg;
-  };
   unsigned *bitmap;
-  int *scnt;
   int lo;
   unsigned span;
   long long *dbg;
-  __device__ __forceinline__ State prep(int col) const {
+  __device__ __forceinline__ void operator()(int col, NoVal, int) const {
     const unsigned x = (unsigned)(col - lo);
-    if (!HS_G(dbg, x < span, 33, col)) return State{1u, 1u, 0};
-    const unsigned bit = 1u << (x & 31);
-    return State{atomicOr(bitmap + (x >> 5), bit), bit, (int)(x / SEG_W)};
+    if (HS_G(dbg, x < span, 33, col)) atomicOr(bitmap + (x >> 5), 1u << (x & 31));
   }
-  __device__ __forceinline__ void commit(const State &s, NoVal) const {
-    if (!(s.old & s.bit)) atomicAdd(scnt + s.seg, 1);
-  }
-  __device__ __forceinline__ void operator()(int col, NoVal v, int) const { commit(prep(col), v); }
 };
 
 struct SymHeavySmem {
@@ -217,10 +205,20 @@ __global__ void __launch_bounds__(1024, 1) k_sym_heavy(SymArgs a) {
       const int words = (hi - lo + 31) >> 5;
       const int nsc = (hi - lo + SEG_W - 1) / SEG_W;
       for (int wd = threadIdx.x; wd < words; wd += blockDim.x) sm.bitmap[wd] = 0u;
-      for (int g = threadIdx.x; g <= SH_SEGS; g += blockDim.x) sm.scnt[g] = 0;
       __syncthreads();
       cta_products<StructSR, CH, 4>(A, B, A.p[r], A.p[r + 1], nchunk > 1, lo, hi, sm.ex, sm.wtmp,
-                                    SymHeavyBit{sm.bitmap, sm.scnt, lo, (unsigned)(hi - lo), a.A.dbg});
+                                    SymHeavyBit{sm.bitmap, lo, (unsigned)(hi - lo), a.A.dbg});
+      // columns per segment: one warp per segment, four words per lane
+      for (int g = warp; g < nsc; g += nw) {
+        int pc = 0;
+#pragma unroll
+        for (int q = 0; q < SEG_W / 32 / 32; ++q) {
+          const int wd = g * (SEG_W / 32) + q * 32 + lane;
+          pc += wd < words ? __popc(sm.bitmap[wd]) : 0;
+        }
+        pc = warp_sum(pc);
+        if (lane == 0) sm.scnt[g] = pc;
+      }
       __syncthreads();
       if (hist)
         for (int g = threadIdx.x; g < nsc; g += blockDim.x)
