@@ -459,4 +459,186 @@ void launch_validate(const int64_t *p, const int32_t *j, int64_t rows, int64_t n
   k_validate<<<grid_for(rows, 8, 16), 256, 0, st>>>(p, j, rows, ncols, flag);
 }
 
+// ------------------------------------------------------- heavy row parts
+// A heavy row's columns are cut into parts of whole SEG_W-column segments:
+// a part takes segments in order while its outputs stay within caph and its
+// span within `span` segments (a segment holds at most SEG_W <= caph
+// outputs, so every segment fits a part of its own; were one to hold more,
+// its part would carry its true count, which the numeric kernel rejects);
+// parts without outputs are dropped.  One warp walks one row's segment counts, 32 at a time, the
+// greedy state kept identical in every lane; `emit(part, seg_lo, seg_hi,
+// pc, done)` runs on lane 0.
+template <class Emit>
+__device__ __forceinline__ int walk_parts(const uint32_t *hist, int nseg, int caph, int span, long long *dbg,
+                                          Emit &&emit) {
+  const int lane = lane_id();
+  int start = 0, sum = 0, parts = 0;
+  long long done = 0;
+  for (int g0 = 0; g0 < nseg; g0 += 32) {
+    const int v = g0 + lane < nseg ? (int)hist[g0 + lane] : 0;
+    const int lim = min(32, nseg - g0);
+    for (int j = 0; j < lim; ++j) {
+      const int x = __shfl_sync(FULL, v, j);
+      const int g = g0 + j;
+      if (g - start >= span || sum + x > caph) {
+        if (sum > 0) {
+          if (lane == 0) emit(parts, start, g, sum, done);
+          ++parts;
+          done += sum;
+        }
+        start = g;
+        sum = 0;
+      }
+      sum += x;
+    }
+  }
+  if (sum > 0) {
+    if (lane == 0) emit(parts, start, nseg, sum, done);
+    ++parts;
+  }
+  return parts;
+}
+
+__global__ void k_count_parts(RowSet A, const int *list, const int *key_off, int key_lo, const int32_t *hslot,
+                              const uint32_t *hist, const int64_t *loff, int nseg, int caph, int span, int64_t nmax,
+                              int64_t *cnt, int64_t *cap) {
+  const int lane = lane_id();
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int lo = key_off[key_lo];
+  const int64_t count = key_off[NKEYS] - lo;
+  for (int64_t w = wid; w < nmax; w += nw) {
+    int64_t parts = 0, room = 0;
+    if (w < count) {
+      const int r = list[lo + w];
+      const int h = (r >= 0 && r < A.nslots) ? hslot[r] : -1;
+      if (h >= 0 && loff[r] >= 0) {
+        parts = walk_parts(hist + (int64_t)h * nseg, nseg, caph, span, nullptr,
+                           [](int, int, int, int, long long) {});
+        room = parts * (A.p[r + 1] - A.p[r]);
+      }
+    }
+    if (lane == 0) {
+      cnt[w] = parts;
+      cap[w] = room;
+    }
+  }
+}
+
+void launch_count_parts(const RowSet &A, const int *list, const int *key_off, int key_lo, const int32_t *hslot,
+                        const uint32_t *hist, const int64_t *loff, int nseg, int caph, int span, int64_t nmax,
+                        int64_t *cnt, int64_t *cap, cudaStream_t st) {
+  if (nmax <= 0) return;
+  count_launch();
+  k_count_parts<<<grid_for(nmax, 8, 16), 256, 0, st>>>(A, list, key_off, key_lo, hslot, hist, loff, nseg, caph,
+                                                       span, nmax, cnt, cap);
+}
+
+__global__ void k_plan_parts(RowSet A, const int *list, int count, const int32_t *hslot, const uint32_t *hist,
+                             const int64_t *loff, int nseg, int caph, int span, const int64_t *off,
+                             const int64_t *poff, HeavyUnit *units) {
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w = wid; w < count; w += nw) {
+    const int r = list[w];
+    const int h = (r >= 0 && r < A.nslots) ? hslot[r] : -1;
+    if (h < 0 || loff[r] < 0) continue;
+    const int64_t base = w ? off[w - 1] : 0;
+    const int64_t end = off[w];
+    const int64_t pbase = w ? poff[w - 1] : 0;
+    const int64_t nq = A.p[r + 1] - A.p[r];
+    walk_parts(hist + (int64_t)h * nseg, nseg, caph, span, nullptr,
+               [&](int p, int s0, int s1, int pc, long long done) {
+                 if (base + p < end) units[base + p] = HeavyUnit{r, s0, s1, pc, done, pbase + p * nq, 0, 0};
+               });
+  }
+}
+
+void launch_plan_parts(const RowSet &A, const int *list, int count, const int32_t *hslot, const uint32_t *hist,
+                       const int64_t *loff, int nseg, int caph, int span, const int64_t *off, const int64_t *poff,
+                       HeavyUnit *units, cudaStream_t st) {
+  if (count <= 0) return;
+  count_launch();
+  k_plan_parts<<<grid_for(count, 8, 16), 256, 0, st>>>(A, list, count, hslot, hist, loff, nseg, caph, span, off,
+                                                       poff, units);
+}
+
+// One warp per unit: its row's A entries 32 at a time, each entry's B
+// segment inside the part from the segment index (or a binary search of a B
+// row without one), the non-empty ones compacted by ballot into the unit's
+// slice with the running product count as their exclusive prefix.  The
+// searches of many units run at once, so their latency is hidden here
+// instead of sitting on the numeric kernel's path.
+template <int AB>
+__global__ void k_build_pairs(RowSet A, RightOp B, HeavyUnit *units, int64_t nunits, const int32_t *bci_id,
+                              const int32_t *bci, int nseg, int64_t *pstart, int32_t *ppre, void *paval) {
+  using VT = typename std::conditional<AB == 8, unsigned long long, unsigned>::type;
+  const int lane = lane_id();
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t bstride = (int64_t)nseg + 1;
+  for (int64_t ui = wid; ui < nunits; ui += nw) {
+    const HeavyUnit u = units[ui];
+    if (!HS_G(A.dbg, u.row >= 0 && u.row < A.nslots && u.seg_lo >= 0 && u.seg_lo < u.seg_hi && u.seg_hi <= nseg,
+              75, ui))
+      continue;
+    const int64_t lo = (int64_t)u.seg_lo * SEG_W, hi = (int64_t)u.seg_hi * SEG_W;
+    const int64_t q0 = A.p[u.row], q1 = A.p[u.row + 1];
+    int out = 0;
+    long long prod = 0;
+    for (int64_t qb = q0; qb < q1; qb += 32) {
+      const int64_t q = qb + lane;
+      int64_t s0 = 0, s1 = 0;
+      VT av = 0;
+      if (q < q1 && HS_G(A.dbg, q >= 0 && q < A.nnz, 1, q)) {
+        const int k = __ldg(A.j + q);
+        if (HS_G(A.dbg, k >= 0 && k < B.m, 2, k)) {
+          const int64_t base = __ldg(B.p + k), end = __ldg(B.p + k + 1);
+          const int t = bci_id ? __ldg(bci_id + k) : -1;
+          s0 = s1 = base;  // an empty B row: an empty segment at its start
+          if (t >= 0) {
+            s0 = base + __ldg(bci + (int64_t)t * bstride + u.seg_lo);
+            s1 = base + __ldg(bci + (int64_t)t * bstride + u.seg_hi);
+          } else if (end > base) {
+            s0 = lower_bound_col(B.j, base, end, (int)lo);
+            s1 = hi > 0x7fffffffLL ? end : lower_bound_col(B.j, s0, end, (int)hi);
+          }
+          if (!HS_G(A.dbg, base <= s0 && s0 <= s1 && s1 <= end, 65, s1)) s0 = s1 = 0;
+          if constexpr (AB > 0)
+            if (s1 > s0) av = __ldg(reinterpret_cast<const VT *>(A.v) + q);
+        }
+      }
+      const int len = (int)(s1 - s0);
+      const unsigned m = __ballot_sync(FULL, len > 0);
+      const int incl = warp_incl_scan(len);
+      if (len > 0) {
+        const int64_t at = u.poff + out + __popc(m & ((1u << lane) - 1u));
+        pstart[at] = s0;
+        ppre[at] = (int32_t)(prod + incl - len);
+        if constexpr (AB > 0) reinterpret_cast<VT *>(paval)[at] = av;
+      }
+      out += __popc(m);
+      prod += __shfl_sync(FULL, incl, 31);
+    }
+    if (lane == 0) {
+      units[ui].npairs = out;
+      units[ui].nprod = HS_G(A.dbg, prod < 0x7fffffffLL, 76, ui) ? (int32_t)prod : 0;
+    }
+  }
+}
+
+void launch_build_pairs(const RowSet &A, const RightOp &B, HeavyUnit *units, int64_t nunits, const int32_t *bci_id,
+                        const int32_t *bci, int nseg, int a_bytes, int64_t *pstart, int32_t *ppre, void *paval,
+                        cudaStream_t st) {
+  if (nunits <= 0) return;
+  count_launch();
+  const int g = grid_for(nunits, 8, 16);
+  if (a_bytes == 8)
+    k_build_pairs<8><<<g, 256, 0, st>>>(A, B, units, nunits, bci_id, bci, nseg, pstart, ppre, paval);
+  else if (a_bytes == 4)
+    k_build_pairs<4><<<g, 256, 0, st>>>(A, B, units, nunits, bci_id, bci, nseg, pstart, ppre, paval);
+  else
+    k_build_pairs<0><<<g, 256, 0, st>>>(A, B, units, nunits, bci_id, bci, nseg, pstart, ppre, paval);
+}
+
 }  // namespace hs

@@ -415,6 +415,27 @@ __device__ __forceinline__ void prefetch_l2(const void *p, int64_t bytes) {
   }
 }
 
+// Asynchronous copy (cp.async, 16-byte pieces, completed by cp.async.wait_all
+// and a barrier) of the global bytes [src, src + bytes) into shared memory at
+// dst + off, off = src mod 16: the copy runs from the 16-byte boundary at or
+// below src to the one at or above src + bytes, so dst needs bytes + 32 bytes
+// of room and the source buffer 16 bytes of slack past its end.  Every
+// thread of the group calls it with its rank.
+__device__ __forceinline__ int async_copy16(void *dst, const void *src, int64_t bytes, int rank, int nthreads) {
+  const uint64_t s = (uint64_t)src;
+  const uint64_t s0 = s & ~(uint64_t)15;
+  const int64_t chunks = (int64_t)((s + (uint64_t)bytes + 15 - s0) >> 4);
+  const unsigned d0 = (unsigned)__cvta_generic_to_shared(dst);
+  for (int64_t c = rank; c < chunks; c += nthreads)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d0 + (unsigned)(c << 4)),
+                 "l"(__cvta_generic_to_global((const void *)(s0 + (uint64_t)(c << 4))))
+                 : "memory");
+  return (int)(s - s0);
+}
+__device__ __forceinline__ void async_copy_wait() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 __host__ __device__ __forceinline__ int next_pow2(int x) {
   int p = 1;
   while (p < x) p <<= 1;
@@ -435,11 +456,13 @@ template <typename T, int CH> struct CtaExpandSmem {
 // only; all threads of the CTA must call it together.
 // Each segment may also be charged K units of fixed cost (its setup in the
 // warp loop): warps then split the cost, not just the products, so a warp
-// whose range holds many short segments gets fewer products.
+// whose range holds many short segments gets fewer products.  excl may hold
+// a running prefix that starts at ebase instead of 0 (a batch of a longer
+// list).
 template <class SR, int U = 2, int K = 0, class Visit>
 __device__ __forceinline__ void cta_expand_staged(const DevCsr &B, const int64_t *sbeg, const int *excl,
                                                   const typename SR::val_t *aval, int n, int total,
-                                                  Visit &visit) {
+                                                  Visit &visit, int ebase = 0) {
   using T = typename SR::val_t;
   const int lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   // entry e occupies [X_e, X_e+1) with X_e = excl[e] + K*e: K units of its
@@ -451,7 +474,7 @@ __device__ __forceinline__ void cta_expand_staged(const DevCsr &B, const int64_t
   int l = 0, h = n;
   while (l < h) {
     const int mid = (l + h) >> 1;
-    if (excl[mid] + (int64_t)K * mid <= pb) l = mid + 1;
+    if (excl[mid] - ebase + (int64_t)K * mid <= pb) l = mid + 1;
     else h = mid;
   }
   for (int eb = l - 1; eb < n; eb += 32) {
@@ -460,7 +483,7 @@ __device__ __forceinline__ void cta_expand_staged(const DevCsr &B, const int64_t
     int len = 0;
     T a{};
     if (e < n) {
-      const int64_t x0 = excl[e] + (int64_t)K * e + K, x1 = excl[e + 1] + (int64_t)K * (e + 1);
+      const int64_t x0 = excl[e] - ebase + (int64_t)K * e + K, x1 = excl[e + 1] - ebase + (int64_t)K * (e + 1);
       const int64_t cb = max(x0, pb), ce = min(x1, pe);
       if (ce > cb) {
         len = (int)(ce - cb);
@@ -469,7 +492,7 @@ __device__ __forceinline__ void cta_expand_staged(const DevCsr &B, const int64_t
       }
     }
     warp_expand<SR, U>(B, s, len, a, visit);
-    if (eb + 32 >= n || excl[eb + 32] + (int64_t)K * (eb + 32) >= pe) break;
+    if (eb + 32 >= n || excl[eb + 32] - ebase + (int64_t)K * (eb + 32) >= pe) break;
   }
 }
 

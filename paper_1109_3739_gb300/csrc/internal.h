@@ -25,6 +25,8 @@ constexpr int CAP_MID_S = 1024, CAP_MID = 2048;
 // Column segments recorded for rows that may need column parts: width SEG_W
 // (a multiple of 1024, at most every numeric table's capacity).
 constexpr int SEG_W = 4096;
+constexpr int HV_SPAN_SEGS = 64;      // segments a heavy column part spans at most (2^18 columns)
+constexpr int HU_SPAN_SEGS = 32;      // the same for the parts of the unit kernel (2^17 columns)
 constexpr int BITMAP_COLS = 1 << 20;  // columns covered by the heavy symbolic bitmap
 constexpr int SEG_SMEM = 1024;        // segment counters kept in shared memory when nseg <= this
 
@@ -172,6 +174,49 @@ void launch_sym_mid(const SymArgs &a, cudaStream_t st);
 void launch_sym_large(const SymArgs &a, cudaStream_t st);
 void launch_sym_heavy(const SymArgs &a, cudaStream_t st);
 
+// A unit of the numeric heavy pass: one column part of one heavy row.  The
+// part spans segments [seg_lo, seg_hi) of SEG_W columns, holds pc outputs,
+// and its outputs start `done` entries into the row (and into the row's
+// sorted column list).  Units of one row are independent: they write
+// disjoint ranges of C, so any CTA may take any unit.
+struct HeavyUnit {
+  int32_t row;     // row slot
+  int32_t seg_lo;
+  int32_t seg_hi;
+  int32_t pc;
+  int64_t done;
+  int64_t poff;    // the unit's slice of the pair arrays (room for every A entry of its row)
+  int32_t npairs;  // A entries with products in the part (the slice's used length)
+  int32_t nprod;   // products in the part
+};
+// outputs a heavy column part holds at most, by value width (the part's
+// values live in shared memory)
+inline int heavy_part_cap(int value_bytes) { return value_bytes == 8 ? 4096 : (value_bytes == 0 ? 16384 : 8192); }
+// the same for the unit kernel: 16 KB of values, and never less than one
+// segment's SEG_W columns (structure only: 2^16 outputs)
+inline int unit_part_cap(int value_bytes) {
+  return value_bytes == 0 ? 65536 : (16384 / value_bytes > SEG_W ? 16384 / value_bytes : SEG_W);
+}
+// parts per heavy row (numeric heavy bin, in list order) into cnt[0..nmax),
+// 0 for rows without a sorted column list (loff < 0), and the room the row's
+// units need in the pair arrays (parts x A entries) into cap[0..nmax); then
+// the units themselves at the scanned offsets (off, poff: inclusive scans of
+// cnt and cap)
+void launch_count_parts(const RowSet &A, const int *list, const int *key_off, int key_lo, const int32_t *hslot,
+                        const uint32_t *hist, const int64_t *loff, int nseg, int caph, int span, int64_t nmax,
+                        int64_t *cnt, int64_t *cap, cudaStream_t st);
+void launch_plan_parts(const RowSet &A, const int *list, int count, const int32_t *hslot, const uint32_t *hist,
+                       const int64_t *loff, int nseg, int caph, int span, const int64_t *off, const int64_t *poff,
+                       HeavyUnit *units, cudaStream_t st);
+// Each unit's B segments: for every A entry of its row whose B row has
+// entries inside the part's columns, (segment start, exclusive prefix of the
+// products, the entry's value when the semiring reads it), compacted into the
+// unit's slice; sets npairs and nprod.  a_bytes: width of A's values to copy
+// (0: none).
+void launch_build_pairs(const RowSet &A, const RightOp &B, HeavyUnit *units, int64_t nunits, const int32_t *bci_id,
+                        const int32_t *bci, int nseg, int a_bytes, int64_t *pstart, int32_t *ppre, void *paval,
+                        cudaStream_t st);
+
 // numeric_*.cu
 struct NumArgs {
   RowSet A;
@@ -194,6 +239,14 @@ struct NumArgs {
   const int32_t *bci_id;  // per B row: its row of the segment index (-1 none), or null
   const int32_t *bci;     // segment index: nseg+1 offsets per indexed B row
   int unsorted;           // hash bins write their entries in table order (no sort)
+  const HeavyUnit *units; // heavy bin by units (rows with sorted lists), or null: one CTA per row
+  int64_t nunits;
+  int *udyn;              // the unit kernel's work counter
+  int lists_partial;      // with units: some heavy rows have no list (the row kernel takes them)
+  const int64_t *pstart;  // units' B segments (launch_build_pairs)
+  const int32_t *ppre;
+  const void *paval;
+  int pair_abytes;        // width of the left values the pairs carry (0: none)
 };
 // kind: 0 tiny, 1 warp_s, 2 warp, 3 mid_s, 4 mid, 5 large_s, 6 large, 7 heavy
 // (bin key KEY_TINY + kind; heavy takes every key from KEY_HEAVY on).

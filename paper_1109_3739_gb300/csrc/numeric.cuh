@@ -252,12 +252,12 @@ __global__ void __launch_bounds__(NT, 1) k_num_cta(NumArgs a) {
 // comes from the B segment index when the B row has one (its offset at the
 // part's last segment), else from a search from the cursor.
 constexpr int HV_NT = 512;          // threads per CTA; two CTAs share an SM
-constexpr int HV_WMAX = 1 << 18;    // columns per part: a 32 KB bitmap
+constexpr int HV_WMAX = HV_SPAN_SEGS * SEG_W;  // columns per part: a 32 KB bitmap
 constexpr int HV_WORDS = HV_WMAX / 32;
 constexpr int HV_CH = 512;          // A entries staged per expansion round
 
 template <typename T> constexpr int heavy_cap() {
-  return vbytes<T>() == 8 ? 4096 : (vbytes<T>() == 0 ? 16384 : 8192);
+  return vbytes<T>() == 8 ? 4096 : (vbytes<T>() == 0 ? 16384 : 8192);  // as heavy_part_cap()
 }
 
 template <typename T> struct HeavySmem {
@@ -333,8 +333,10 @@ __global__ void __launch_bounds__(HV_NT, 2) k_num_heavy(NumArgs a) {
     const int idx = sm.row;
     if (idx >= a.count) break;
     const int r0 = a.list[idx];
-    // a bad row id is processed as an empty row so the loop reaches its barriers
-    const bool r_ok = HS_G(dbg, r0 >= 0 && r0 < a.A.nslots, 36, r0);
+    // a bad row id is processed as an empty row so the loop reaches its barriers;
+    // so is a row that the unit kernel takes (it has a sorted column list)
+    const bool r_ok = HS_G(dbg, r0 >= 0 && r0 < a.A.nslots, 36, r0) &&
+                      !(a.units && a.loff && a.loff[r0] >= 0 && a.hslot[r0] >= 0);
     const int r = r_ok ? r0 : 0;
     const int64_t o = nout_row(a.A, r);
     const int64_t cb = a.Cp[o];
@@ -656,6 +658,149 @@ __global__ void __launch_bounds__(HV_NT, 2) k_num_heavy(NumArgs a) {
   }
 }
 
+// ------------------------------------------------------------ heavy units
+// The heavy bin's rows that have a sorted column list, by units: one column
+// part of one row per unit, handed out to CTAs by an atomic counter, so a hub
+// row's parts run on many SMs at once and no row's length sets the kernel's
+// tail.  Everything a unit reads that depends on other data has been laid out
+// before the kernel runs: the part's slice of the row's sorted column list
+// (written by the symbolic pass) and the part's B segments with their product
+// prefix and left value (launch_build_pairs, which does the segment searches
+// for all units in bulk).  A unit copies both into shared memory with
+// cp.async, then: the list slice is written as C's columns and gives the
+// part's occupancy bitmap and word ranks; the products add their value at
+// rank(col) = wpre[word] + popcount(bits below col), spread evenly over the
+// warps by their prefix; the values leave in column order.  Parts span at
+// most 2^17 columns and hold 16 KB of values (a whole segment's 4096 for
+// 8-byte values), so four CTAs of 256 threads share an SM (three for 8-byte
+// values).
+constexpr int HU_NT = 256;
+constexpr int HU_WMAX = HU_SPAN_SEGS * SEG_W;
+constexpr int HU_WORDS = HU_WMAX / 32;
+constexpr int HU_PB = 384;  // B segments copied per batch
+// as unit_part_cap(): 16 KB of values, at least one segment's SEG_W outputs
+template <typename T> constexpr int unit_cap() {
+  return vbytes<T>() == 0 ? 65536 : (16384 / vbytes<T>() > SEG_W ? 16384 / vbytes<T>() : SEG_W);
+}
+
+template <typename T> struct UnitSmem {
+  static constexpr int CAP = vbytes<T>() ? unit_cap<T>() : 1;
+  // the part's values; first the list slice lands here (4-byte column ids
+  // plus the copy's 32 bytes of alignment room)
+  static constexpr size_t VBYTES = ((size_t)CAP * (vbytes<T>() > 4 ? vbytes<T>() : 4) + 32 + 15) & ~(size_t)15;
+  alignas(16) unsigned char vals_raw[VBYTES];
+  alignas(16) unsigned bitmap[HU_WORDS];  // all zero at every unit's start
+  alignas(16) int64_t sbeg[HU_PB + 4];   // B segment starts (+ copy room)
+  alignas(16) int excl[HU_PB + 8];       // their product prefix, then the batch's end
+  alignas(16) unsigned char aval_raw[(HU_PB + 4) * (vbytes<T>() > 4 ? 8 : 4) + 16];
+  uint16_t wpre[HU_WORDS];                // set bits before word w within the part
+  int wtmp[33];
+  int unit;
+};
+
+template <class SR>
+__global__ void __launch_bounds__(HU_NT, 4) k_num_units(NumArgs a) {
+  using T = typename SR::val_t;
+  using L = UnitSmem<T>;
+  constexpr int CAP = unit_cap<T>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto &sm = *reinterpret_cast<L *>(smem_raw);
+  const DevCsr B = ndev_b(a.B);
+  T *Cv = reinterpret_cast<T *>(a.Cv);
+  T *vals = reinterpret_cast<T *>(sm.vals_raw);
+  const int tid = threadIdx.x, lane = lane_id();
+  const int64_t n = a.B.n;
+  const int nseg = (int)((n + SEG_W - 1) / SEG_W);
+  long long *dbg = a.A.dbg;
+  if constexpr (SR::has_val)
+    for (int w = tid; w < HU_WORDS; w += HU_NT) sm.bitmap[w] = 0u;
+  while (true) {
+    if (tid == 0) sm.unit = atomicAdd(a.udyn, 1);
+    __syncthreads();
+    const int64_t ui = sm.unit;
+    if (ui >= a.nunits) break;
+    const HeavyUnit u = a.units[ui];
+    // every thread reads the same words, so a failed check skips the unit in
+    // every thread alike and the barriers below stay matched
+    bool ok = HS_G(dbg, u.row >= 0 && u.row < a.A.nslots, 71, u.row) &&
+              HS_G(dbg, u.seg_lo >= 0 && u.seg_lo < u.seg_hi && u.seg_hi <= nseg &&
+                            u.seg_hi - u.seg_lo <= HU_SPAN_SEGS, 72, u.seg_lo) &&
+              HS_G(dbg, u.pc > 0 && u.pc <= CAP, 73, u.pc) &&
+              HS_G(dbg, u.npairs >= 0 && u.npairs <= a.A.p[u.row + 1] - a.A.p[u.row] && u.nprod >= 0, 77,
+                   u.npairs);
+    const int r = ok ? u.row : 0;
+    const int64_t o = nout_row(a.A, r);
+    const int64_t cb = a.Cp[o];
+    const int64_t lofs = ok ? a.loff[r] : -1;
+    ok = ok && HS_G(dbg, lofs >= 0 && u.done >= 0 && u.done + u.pc <= a.Cp[o + 1] - cb, 74, u.done);
+    if (ok) {
+      const int lo = u.seg_lo * SEG_W;
+      const int hi = (int)min((int64_t)u.seg_hi * SEG_W, n);
+      const int pc = u.pc;
+      const int32_t *Lp = a.glist + lofs + u.done;
+      const int64_t out = cb + u.done;
+      if constexpr (SR::has_val) {
+        // the list slice and the first batch of B segments, copied at once
+        const int nb0 = u.npairs < HU_PB ? u.npairs : HU_PB;
+        const int lofb = async_copy16(sm.vals_raw, Lp, (int64_t)pc * 4, tid, HU_NT) >> 2;
+        const int sofb = async_copy16(sm.sbeg, a.pstart + u.poff, (int64_t)nb0 * 8, tid, HU_NT) >> 3;
+        const int eofb = async_copy16(sm.excl, a.ppre + u.poff, (int64_t)nb0 * 4, tid, HU_NT) >> 2;
+        int aofb = 0;
+        if constexpr (SR::needs_a)
+          aofb = async_copy16(sm.aval_raw, reinterpret_cast<const T *>(a.paval) + u.poff,
+                              (int64_t)nb0 * sizeof(T), tid, HU_NT) / (int)sizeof(T);
+        async_copy_wait();
+        __syncthreads();
+        // columns out, bits and word ranks in (entry i starts word w when
+        // entry i-1 lies in another word)
+        const int32_t *Ls = reinterpret_cast<const int32_t *>(sm.vals_raw) + lofb;
+        for (int i = tid; i < pc; i += HU_NT) {
+          const int col = Ls[i];
+          __stcs(a.Cj + out + i, col);
+          const int xx = col - lo;
+          if (!HS_G(dbg, xx >= 0 && xx < hi - lo, 63, col)) continue;
+          const int w = xx >> 5;
+          atomicOr(sm.bitmap + w, 1u << (xx & 31));
+          if (i == 0 || ((Ls[i - 1] - lo) >> 5) != w) sm.wpre[w] = (uint16_t)i;
+        }
+        __syncthreads();  // the list slice is read: its room becomes the values
+        for (int i = tid; i < pc; i += HU_NT) vals[i] = SR::identity();
+        HeavyAdd<SR> add_val{sm.bitmap, sm.wpre, vals, lo, (unsigned)(hi - lo), pc, a.err, dbg};
+        for (int pb = 0; pb < u.npairs; pb += HU_PB) {
+          const int nb = min(HU_PB, u.npairs - pb);
+          int so = sofb, eo = eofb, ao = aofb;
+          if (pb > 0) {  // the next batch (rows with many A entries)
+            __syncthreads();
+            so = async_copy16(sm.sbeg, a.pstart + u.poff + pb, (int64_t)nb * 8, tid, HU_NT) >> 3;
+            eo = async_copy16(sm.excl, a.ppre + u.poff + pb, (int64_t)nb * 4, tid, HU_NT) >> 2;
+            if constexpr (SR::needs_a)
+              ao = async_copy16(sm.aval_raw, reinterpret_cast<const T *>(a.paval) + u.poff + pb,
+                                (int64_t)nb * sizeof(T), tid, HU_NT) / (int)sizeof(T);
+            async_copy_wait();
+            __syncthreads();  // every copy has landed (the batch end below may share a copied piece)
+          }
+          int *ex = sm.excl + eo;
+          if (tid == 0) ex[nb] = pb + nb < u.npairs ? __ldg(a.ppre + u.poff + pb + nb) : u.nprod;
+          __syncthreads();
+          const int base = ex[0];
+          cta_expand_staged<SR, 4, 32>(B, sm.sbeg + so, ex, reinterpret_cast<const T *>(sm.aval_raw) + ao, nb,
+                                       ex[nb] - base, add_val, base);
+        }
+        __syncthreads();
+        // values in column order; the part's bitmap words cleared for the next unit
+        for (int i = tid; i < pc; i += HU_NT) __stcs(Cv + out + i, vals[i]);
+        const int words = (hi - lo + 31) >> 5;
+        for (int w = tid; w < words; w += HU_NT) sm.bitmap[w] = 0u;
+      } else {
+        // structure only: the list slice is the part's columns
+        for (int i = tid; i < pc; i += HU_NT) __stcs(a.Cj + out + i, __ldg(Lp + i));
+      }
+    }
+    (void)lane;
+    __syncthreads();  // sm.unit and the part's buffers are free for the next unit
+  }
+}
+
 // ------------------------------------------------------------ launchers
 inline int ngrid_cap(int items, int per_block, int per_sm) {
   int g = (items + per_block - 1) / per_block;
@@ -708,10 +853,20 @@ template <class SR> void launch_numeric_sr(int kind, const NumArgs &a, cudaStrea
       break;
     case 6: launch_num_cta<SR, 2 * CAPL, CAPL, 1024>(a, st); break;
     case 7: {
-      const size_t bytes = sizeof(HeavySmem<T>);
-      set_smem_attr(k_num_heavy<SR>, bytes);
-      count_launch();
-      k_num_heavy<SR><<<ngrid_cap(a.count, 1, 2), HV_NT, bytes, st>>>(a);
+      if (a.units && a.nunits > 0) {
+        const size_t ub = sizeof(UnitSmem<T>);
+        auto ku = k_num_units<SR>;
+        set_smem_attr(ku, ub);
+        count_launch();
+        const int items = a.nunits < (1 << 30) ? (int)a.nunits : (1 << 30);
+        ku<<<ngrid_cap(items, 1, fit_per_sm(ku, HU_NT, ub)), HU_NT, ub, st>>>(a);
+      }
+      if (!a.units || a.lists_partial) {  // rows without a list: one CTA per row
+        const size_t bytes = sizeof(HeavySmem<T>);
+        set_smem_attr(k_num_heavy<SR>, bytes);
+        count_launch();
+        k_num_heavy<SR><<<ngrid_cap(a.count, 1, 2), HV_NT, bytes, st>>>(a);
+      }
       break;
     }
   }

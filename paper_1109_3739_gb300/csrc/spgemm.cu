@@ -236,7 +236,7 @@ struct SmallBlock {  // device counters, read back in one copy
   int key_cnt[NKEYS];
   int key_off[NKEYS + 1];
   int key_cur[NKEYS];
-  int dyn[2];
+  int dyn[3];  // symbolic heavy rows, numeric heavy rows, numeric heavy units
   int nhist;
   int err;
   int valflag;
@@ -245,6 +245,8 @@ struct SmallBlock {  // device counters, read back in one copy
   unsigned long long lpool;  // heavy rows' column lists: pool entries handed out
   int bci_cnt;               // B segment index rows handed out
   int pad2;
+  long long nunits;          // numeric heavy units (column parts of rows with lists)
+  long long npcap;           // their room in the pair arrays
   long long nnz;
   unsigned long long zeros;  // A entries whose B row is empty
   long long dbg[2];  // guarded builds: first failed check (code, index)
@@ -506,9 +508,10 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
       const size_t want = (size_t)hb->stats[3] * 4;
       const size_t bytes = want < budget ? want : budget;
       if (bytes >= 4) {
-        glist = (int32_t *)mem.raw(bytes);
+        // (16 bytes of slack: the numeric units copy their slices in 16-byte pieces)
+        glist = (int32_t *)mem.raw(bytes + 16);
         loff = glist ? (int64_t *)mem.raw(sizeof(int64_t) * (size_t)nslots) : nullptr;
-        if (glist) mem.scratch.push_back({glist, bytes});
+        if (glist) mem.scratch.push_back({glist, bytes + 16});
         if (loff) mem.scratch.push_back({loff, sizeof(int64_t) * (size_t)nslots});
         mem.failed = false;  // optional buffers
         if (!loff) glist = nullptr;
@@ -561,6 +564,30 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
     launch_scatter_num(rs, f, Cp, bins, sb->key_cur, list, st);
     CK(cudaMemcpyAsync(&sb->nnz, Cp + m, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
   }
+  // numeric heavy rows that have a sorted column list run as units (column
+  // parts spread over the SMs): their parts are counted now, so that the
+  // number of units comes back with nnz(C); the numeric heavy rows are a
+  // subset of the symbolic heavy rows, whose number bounds the count array
+  int64_t *pcnt = nullptr, *pcap = nullptr;
+  const int64_t nsh_rows = key_off[NKEYS] - key_off[KEY_HEAVY];
+  const int ucap = unit_part_cap(vb);
+  if (glist && nsh_rows > 0) {
+    pcnt = mem.tmp<int64_t>((size_t)nsh_rows);
+    pcap = pcnt ? mem.tmp<int64_t>((size_t)nsh_rows) : nullptr;
+    int64_t *ptmp = pcap ? mem.tmp<int64_t>((size_t)scan_tmp_elems(nsh_rows)) : nullptr;
+    mem.failed = false;  // optional: without units the heavy rows run one CTA per row
+    if (!ptmp) pcnt = nullptr;
+    if (pcnt) {
+      PhaseTimer t("scan_bin", st);
+      launch_count_parts(rs, list, sb->key_off, KEY_HEAVY, hslot, hist, loff, nseg, ucap, HU_SPAN_SEGS, nsh_rows,
+                         pcnt, pcap, st);
+      launch_scan_i64(pcnt, nsh_rows, ptmp, st);
+      launch_scan_i64(pcap, nsh_rows, ptmp, st);
+      CK(cudaMemcpyAsync(&sb->nunits, pcnt + nsh_rows - 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(&sb->npcap, pcap + nsh_rows - 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+    }
+    cudaGetLastError();
+  }
   if (int e = phase_check("scan_bin", st, sb->dbg)) return e;
   CK(cudaMemcpyAsync(hb, sb, sizeof(SmallBlock), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -589,9 +616,39 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
   }
 
   // ---- numeric
-  // heavy bin: per-A-entry cursors into B rows (relative offsets)
+  // heavy bin: units, planned from the segment counts of the rows with lists
+  // and, for semirings with values, each unit's B segments (start, product
+  // prefix, left value) laid out by launch_build_pairs once the segment
+  // index exists (below)
+  HeavyUnit *units = nullptr;
+  int64_t *pstart = nullptr;
+  int32_t *ppre = nullptr;
+  void *paval = nullptr;
+  const int64_t nunits = pcnt ? hb->nunits : 0;
+  const int64_t npcap = pcnt ? hb->npcap : 0;
+  const int nheavy = key_off[NKEYS] - key_off[KEY_HEAVY];
+  const int a_bytes = (sr == HS_PLUS_TIMES || sr == HS_MIN_PLUS || sr == HS_SELECT1ST) ? vb : 0;
+  if (nheavy > 0 && nunits > 0) {
+    units = mem.tmp<HeavyUnit>((size_t)nunits);
+    if (units && vb) {  // 16 bytes of slack each: the units copy their slices in 16-byte pieces
+      pstart = (int64_t *)mem.tmp<char>((size_t)npcap * 8 + 16);
+      ppre = (int32_t *)mem.tmp<char>((size_t)npcap * 4 + 16);
+      paval = a_bytes ? (void *)mem.tmp<char>((size_t)npcap * a_bytes + 16) : nullptr;
+      if (!pstart || !ppre || (a_bytes && !paval)) units = nullptr;
+    }
+    mem.failed = false;  // optional, as above
+    if (units) {
+      PhaseTimer t("scan_bin", st);
+      launch_plan_parts(rs, list + key_off[KEY_HEAVY], nheavy, hslot, hist, loff, nseg, ucap, HU_SPAN_SEGS, pcnt,
+                        pcap, units, st);
+    }
+    cudaGetLastError();
+  }
+  // rows that a unit does not cover (no list): one CTA per row, with
+  // per-A-entry cursors into B rows (relative offsets)
+  const bool lists_partial = lcap < (int64_t)hb->stats[3];
   int32_t *gcur = nullptr, *gend = nullptr;
-  if (key_off[NKEYS] > key_off[KEY_HEAVY]) {
+  if (nheavy > 0 && (!units || lists_partial)) {
     gcur = mem.tmp<int32_t>((size_t)A->nnz);
     gend = mem.tmp<int32_t>((size_t)A->nnz);
     if (!gcur || !gend) return HS_ENOMEM;
@@ -626,9 +683,22 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
     }
     cudaGetLastError();
   }
+  if (units && vb) {
+    PhaseTimer t("heavy_pairs", st);
+    launch_build_pairs(rs, rb, units, nunits, bci_id, bci, nseg, a_bytes, pstart, ppre, paval, st);
+    if (int e = phase_check("heavy_pairs", st, sb->dbg)) return e;
+  }
   NumArgs na{rs, rb,   f,    nullptr, 0,    Cp,    C->idx, C->val, hslot,
              hist, nseg, &sb->dyn[1], &sb->err, gcur, gend, glist, loff, bci_id, bci};
   na.unsorted = (flags & HS_FLAG_UNSORTED) ? 1 : 0;
+  na.units = units;
+  na.nunits = units ? nunits : 0;
+  na.udyn = &sb->dyn[2];
+  na.lists_partial = lists_partial ? 1 : 0;
+  na.pstart = pstart;
+  na.ppre = ppre;
+  na.paval = paval;
+  na.pair_abytes = a_bytes;
   const char *names[NUM_KINDS] = {"numeric_tiny", "numeric_warp_s", "numeric_warp",  "numeric_mid_s",
                                   "numeric_mid",  "numeric_large_s", "numeric_large", "numeric_heavy"};
   static_assert(KEY_TINY + NUM_KINDS - 1 == KEY_HEAVY, "one key per numeric kind before the heavy keys");
@@ -1125,7 +1195,12 @@ int hs_plan_execute(const hs_plan *P, const void *A_val, const void *B_val, void
   na.A.v = A_val;
   na.B.v = B_val;
   na.Cv = C_val;
-  CK(cudaMemsetAsync(P->dyn, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(P->dyn, 0, 2 * sizeof(int), st));  // the heavy rows' and units' counters
+  // the heavy units' B segments carry A's values: laid out again from the new ones
+  if (na.units && na.pstart && na.nunits > 0)
+    launch_build_pairs(na.A, na.B, const_cast<HeavyUnit *>(na.units), na.nunits, na.bci_id, na.bci, na.nseg,
+                       na.pair_abytes, const_cast<int64_t *>(na.pstart), const_cast<int32_t *>(na.ppre),
+                       const_cast<void *>(na.paval), st);
   for (int kind = 0; kind < NUM_KINDS; ++kind) {
     if (P->count[kind] <= 0) continue;
     na.list = P->list + P->off[kind];
