@@ -290,6 +290,36 @@ void hs_plan_destroy(hs_plan *plan, void *stream);
 int hs_batch_stack(int64_t count, const hs_mat *A, const hs_mat *B, hs_mat *SA, hs_mat *SB,
                    int64_t *row_offsets, const hs_allocator *al, void *stream);
 
+/* Batched products in one persistent launch (the paper has no counterpart:
+ * many independent products C_i = A_i * B_i, uneven in size, served at once).
+ * hs_batch_plan_create stacks the problems as hs_batch_stack does (A_i and B_i
+ * are read only here), finds each row's products once (one host
+ * synchronisation) and allocates C with room for the flop bound
+ * sum_r min(f_r, n); nothing is computed yet.  Semirings and dtypes as
+ * hs_spgemm: (+,x) F64/F32/I64, (min,+) F32/I32, (or,and) BOOL.  Rows with
+ * more than 4096 products are not taken (HS_EUNSUPPORTED: use
+ * hs_spgemm_batched).
+ * hs_batch_plan_execute computes C: one memset of the plan's work counters
+ * and one cooperative kernel whose resident CTAs take rows from atomic
+ * counters through four phases (products per row, distinct columns per row,
+ * row offsets, values) separated by grid-wide barriers with bounded waits.
+ * It allocates nothing and does not synchronise with the host, so it can be
+ * captured in a CUDA graph and replayed; each execution recomputes C from the
+ * stacked inputs.
+ * hs_batch_plan_result (one host synchronisation) describes the last
+ * execution's C: the stacked product whose rows row_offsets[i] ..
+ * row_offsets[i+1] are C_i (local column ids), with arrays owned by the plan
+ * (valid until the next execution or hs_batch_plan_destroy), and returns
+ * HS_ETIMEDOUT if a barrier wait expired, HS_EUNSUPPORTED if a row did not fit
+ * the kernel's tables, HS_EINTERNAL after a failed device check.
+ * row_offsets (host, count + 1 entries) may be null. */
+typedef struct hs_batch_plan hs_batch_plan;
+int hs_batch_plan_create(int semiring, int64_t count, const hs_mat *A, const hs_mat *B, hs_batch_plan **plan,
+                         const hs_allocator *al, void *stream, uint32_t flags);
+int hs_batch_plan_execute(hs_batch_plan *plan, void *stream);
+int hs_batch_plan_result(hs_batch_plan *plan, hs_mat *C, int64_t *row_offsets, void *stream);
+void hs_batch_plan_destroy(hs_batch_plan *plan, void *stream);
+
 /* SpGEMM for callers that cannot allocate device memory while they run (the
  * paper has no counterpart): for example code that has given the GPU's memory
  * to its own pool and must keep its footprint fixed, or code running where a

@@ -465,12 +465,12 @@ void launch_validate(const int64_t *p, const int32_t *j, int64_t rows, int64_t n
 // span within `span` segments (a segment holds at most SEG_W <= caph
 // outputs, so every segment fits a part of its own; were one to hold more,
 // its part would carry its true count, which the numeric kernel rejects);
-// parts without outputs are dropped.  One warp walks one row's segment counts, 32 at a time, the
-// greedy state kept identical in every lane; `emit(part, seg_lo, seg_hi,
-// pc, done)` runs on lane 0.
+// parts without outputs are dropped.  One warp walks one row's segment
+// counts, 32 at a time, the greedy state kept identical in every lane;
+// `emit(part, seg_lo, seg_hi, pc, done)` runs on lane 0 (done: the row's
+// outputs before the part).
 template <class Emit>
-__device__ __forceinline__ int walk_parts(const uint32_t *hist, int nseg, int caph, int span, long long *dbg,
-                                          Emit &&emit) {
+__device__ __forceinline__ int walk_parts(const uint32_t *hist, int nseg, int caph, int span, Emit &&emit) {
   const int lane = lane_id();
   int start = 0, sum = 0, parts = 0;
   long long done = 0;
@@ -513,8 +513,7 @@ __global__ void k_count_parts(RowSet A, const int *list, const int *key_off, int
       const int r = list[lo + w];
       const int h = (r >= 0 && r < A.nslots) ? hslot[r] : -1;
       if (h >= 0 && loff[r] >= 0) {
-        parts = walk_parts(hist + (int64_t)h * nseg, nseg, caph, span, nullptr,
-                           [](int, int, int, int, long long) {});
+        parts = walk_parts(hist + (int64_t)h * nseg, nseg, caph, span, [](int, int, int, int, long long) {});
         room = parts * (A.p[r + 1] - A.p[r]);
       }
     }
@@ -535,8 +534,8 @@ void launch_count_parts(const RowSet &A, const int *list, const int *key_off, in
 }
 
 __global__ void k_plan_parts(RowSet A, const int *list, int count, const int32_t *hslot, const uint32_t *hist,
-                             const int64_t *loff, int nseg, int caph, int span, const int64_t *off,
-                             const int64_t *poff, HeavyUnit *units) {
+                             const int64_t *loff, const int64_t *Cp, int nseg, int caph, int span,
+                             const int64_t *off, const int64_t *poff, HeavyUnit *units) {
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t w = wid; w < count; w += nw) {
@@ -547,19 +546,23 @@ __global__ void k_plan_parts(RowSet A, const int *list, int count, const int32_t
     const int64_t end = off[w];
     const int64_t pbase = w ? poff[w - 1] : 0;
     const int64_t nq = A.p[r + 1] - A.p[r];
-    walk_parts(hist + (int64_t)h * nseg, nseg, caph, span, nullptr,
-               [&](int p, int s0, int s1, int pc, long long done) {
-                 if (base + p < end) units[base + p] = HeavyUnit{r, s0, s1, pc, done, pbase + p * nq, 0, 0};
-               });
+    const int64_t o = A.ids ? (int64_t)A.ids[r] : (int64_t)r;
+    const int64_t cb = Cp[o], c = Cp[o + 1] - cb, lb = loff[r];
+    walk_parts(hist + (int64_t)h * nseg, nseg, caph, span, [&](int p, int s0, int s1, int pc, long long done) {
+      // a part must lie inside its row (else pc 0: the numeric kernel rejects the unit)
+      const bool fits = HS_G(A.dbg, done + pc <= c, 74, done);
+      if (base + p < end)
+        units[base + p] = HeavyUnit{r, s0, s1, fits ? pc : 0, done, pbase + p * nq, 0, 0, cb + done, lb + done};
+    });
   }
 }
 
 void launch_plan_parts(const RowSet &A, const int *list, int count, const int32_t *hslot, const uint32_t *hist,
-                       const int64_t *loff, int nseg, int caph, int span, const int64_t *off, const int64_t *poff,
-                       HeavyUnit *units, cudaStream_t st) {
+                       const int64_t *loff, const int64_t *Cp, int nseg, int caph, int span, const int64_t *off,
+                       const int64_t *poff, HeavyUnit *units, cudaStream_t st) {
   if (count <= 0) return;
   count_launch();
-  k_plan_parts<<<grid_for(count, 8, 16), 256, 0, st>>>(A, list, count, hslot, hist, loff, nseg, caph, span, off,
+  k_plan_parts<<<grid_for(count, 8, 16), 256, 0, st>>>(A, list, count, hslot, hist, loff, Cp, nseg, caph, span, off,
                                                        poff, units);
 }
 

@@ -174,12 +174,13 @@ void launch_sym_mid(const SymArgs &a, cudaStream_t st);
 void launch_sym_large(const SymArgs &a, cudaStream_t st);
 void launch_sym_heavy(const SymArgs &a, cudaStream_t st);
 
+
 // A unit of the numeric heavy pass: one column part of one heavy row.  The
 // part spans segments [seg_lo, seg_hi) of SEG_W columns, holds pc outputs,
 // and its outputs start `done` entries into the row (and into the row's
 // sorted column list).  Units of one row are independent: they write
 // disjoint ranges of C, so any CTA may take any unit.
-struct HeavyUnit {
+struct alignas(16) HeavyUnit {
   int32_t row;     // row slot
   int32_t seg_lo;
   int32_t seg_hi;
@@ -188,6 +189,8 @@ struct HeavyUnit {
   int64_t poff;    // the unit's slice of the pair arrays (room for every A entry of its row)
   int32_t npairs;  // A entries with products in the part (the slice's used length)
   int32_t nprod;   // products in the part
+  int64_t out;     // position in C of the part's first entry (C's row offset + done)
+  int64_t lofs;    // position of the part's first column in the sorted-list pool
 };
 // outputs a heavy column part holds at most, by value width (the part's
 // values live in shared memory)
@@ -206,8 +209,8 @@ void launch_count_parts(const RowSet &A, const int *list, const int *key_off, in
                         const uint32_t *hist, const int64_t *loff, int nseg, int caph, int span, int64_t nmax,
                         int64_t *cnt, int64_t *cap, cudaStream_t st);
 void launch_plan_parts(const RowSet &A, const int *list, int count, const int32_t *hslot, const uint32_t *hist,
-                       const int64_t *loff, int nseg, int caph, int span, const int64_t *off, const int64_t *poff,
-                       HeavyUnit *units, cudaStream_t st);
+                       const int64_t *loff, const int64_t *Cp, int nseg, int caph, int span, const int64_t *off,
+                       const int64_t *poff, HeavyUnit *units, cudaStream_t st);
 // Each unit's B segments: for every A entry of its row whose B row has
 // entries inside the part's columns, (segment start, exclusive prefix of the
 // products, the entry's value when the semiring reads it), compacted into the

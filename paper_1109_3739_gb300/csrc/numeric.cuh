@@ -714,31 +714,29 @@ __global__ void __launch_bounds__(HU_NT, 4) k_num_units(NumArgs a) {
   long long *dbg = a.A.dbg;
   if constexpr (SR::has_val)
     for (int w = tid; w < HU_WORDS; w += HU_NT) sm.bitmap[w] = 0u;
+  if (tid == 0) sm.unit = atomicAdd(a.udyn, 1);
+  __syncthreads();
   while (true) {
-    if (tid == 0) sm.unit = atomicAdd(a.udyn, 1);
-    __syncthreads();
     const int64_t ui = sm.unit;
     if (ui >= a.nunits) break;
     const HeavyUnit u = a.units[ui];
+    // the next unit is claimed now; its descriptor is brought into L2 once
+    // the counter answers, so neither round trip waits at the unit's end
+    int nxt = 0;
+    if (tid == 0) nxt = atomicAdd(a.udyn, 1);
     // every thread reads the same words, so a failed check skips the unit in
-    // every thread alike and the barriers below stay matched
-    bool ok = HS_G(dbg, u.row >= 0 && u.row < a.A.nslots, 71, u.row) &&
-              HS_G(dbg, u.seg_lo >= 0 && u.seg_lo < u.seg_hi && u.seg_hi <= nseg &&
-                            u.seg_hi - u.seg_lo <= HU_SPAN_SEGS, 72, u.seg_lo) &&
-              HS_G(dbg, u.pc > 0 && u.pc <= CAP, 73, u.pc) &&
-              HS_G(dbg, u.npairs >= 0 && u.npairs <= a.A.p[u.row + 1] - a.A.p[u.row] && u.nprod >= 0, 77,
-                   u.npairs);
-    const int r = ok ? u.row : 0;
-    const int64_t o = nout_row(a.A, r);
-    const int64_t cb = a.Cp[o];
-    const int64_t lofs = ok ? a.loff[r] : -1;
-    ok = ok && HS_G(dbg, lofs >= 0 && u.done >= 0 && u.done + u.pc <= a.Cp[o + 1] - cb, 74, u.done);
+    // every thread alike and the barriers below stay matched (the planner
+    // checked that the part lies inside its row)
+    const bool ok = HS_G(dbg, u.seg_lo >= 0 && u.seg_lo < u.seg_hi && u.seg_hi <= nseg &&
+                                  u.seg_hi - u.seg_lo <= HU_SPAN_SEGS, 72, u.seg_lo) &&
+                    HS_G(dbg, u.pc > 0 && u.pc <= CAP, 73, u.pc) &&
+                    HS_G(dbg, u.npairs >= 0 && u.nprod >= 0 && u.out >= 0 && u.lofs >= 0, 77, u.npairs);
     if (ok) {
       const int lo = u.seg_lo * SEG_W;
       const int hi = (int)min((int64_t)u.seg_hi * SEG_W, n);
       const int pc = u.pc;
-      const int32_t *Lp = a.glist + lofs + u.done;
-      const int64_t out = cb + u.done;
+      const int32_t *Lp = a.glist + u.lofs;
+      const int64_t out = u.out;
       if constexpr (SR::has_val) {
         // the list slice and the first batch of B segments, copied at once
         const int nb0 = u.npairs < HU_PB ? u.npairs : HU_PB;
@@ -763,6 +761,7 @@ __global__ void __launch_bounds__(HU_NT, 4) k_num_units(NumArgs a) {
           atomicOr(sm.bitmap + w, 1u << (xx & 31));
           if (i == 0 || ((Ls[i - 1] - lo) >> 5) != w) sm.wpre[w] = (uint16_t)i;
         }
+        if (tid == 0 && nxt < a.nunits) prefetch_l2(a.units + nxt, sizeof(HeavyUnit));
         __syncthreads();  // the list slice is read: its room becomes the values
         for (int i = tid; i < pc; i += HU_NT) vals[i] = SR::identity();
         HeavyAdd<SR> add_val{sm.bitmap, sm.wpre, vals, lo, (unsigned)(hi - lo), pc, a.err, dbg};
@@ -797,7 +796,9 @@ __global__ void __launch_bounds__(HU_NT, 4) k_num_units(NumArgs a) {
       }
     }
     (void)lane;
-    __syncthreads();  // sm.unit and the part's buffers are free for the next unit
+    __syncthreads();  // every thread has read sm.unit; the part's buffers are free
+    if (tid == 0) sm.unit = nxt;
+    __syncthreads();
   }
 }
 

@@ -524,6 +524,42 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
     cudaGetLastError();
   }
 
+  // the B segment index: for every B row longer than min_len, the offset of
+  // its first entry in each SEG_W-column segment (the table kept within an
+  // eighth of the free memory, at most 4 GiB); built once, on first need
+  int32_t *bci_id = nullptr, *bci = nullptr;
+  bool bci_done = false;
+  auto build_bci = [&]() -> int {
+    if (bci_done || B->nnz <= 0) return HS_OK;
+    bci_done = true;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+      const size_t budget = free_b / 8 < ((size_t)4 << 30) ? free_b / 8 : ((size_t)4 << 30);
+      const int64_t stride = (int64_t)nseg + 1;
+      const int64_t row_bytes = stride * 4;
+      int64_t min_len = 32;
+      const int64_t need = (B->nnz * row_bytes + (int64_t)budget - 1) / (int64_t)(budget ? budget : 1);
+      if (need > min_len) min_len = need;
+      int64_t max_rows = B->nnz / (min_len + 1);
+      if (max_rows > (int64_t)(budget / row_bytes)) max_rows = (int64_t)(budget / row_bytes);
+      if (max_rows > 0 && min_len < 0x7fffffff) {
+        bci_id = (int32_t *)mem.raw(sizeof(int32_t) * (size_t)B->m);
+        bci = bci_id ? (int32_t *)mem.raw((size_t)max_rows * (size_t)row_bytes) : nullptr;
+        if (bci_id) mem.scratch.push_back({bci_id, sizeof(int32_t) * (size_t)B->m});
+        if (bci) mem.scratch.push_back({bci, (size_t)max_rows * (size_t)row_bytes});
+        mem.failed = false;  // optional: without it the part ends are searched
+        if (!bci) bci_id = nullptr;
+        else {
+          PhaseTimer t("bci", st);
+          launch_build_bci(rb, nseg, (int)min_len, max_rows, bci_id, bci, &sb->bci_cnt, st);
+          if (int e = phase_check("bci", st, sb->dbg)) return e;
+        }
+      }
+    }
+    cudaGetLastError();
+    return HS_OK;
+  };
+
   // ---- symbolic
   SymArgs sa{rs, rb, f, nullptr, 0, Cp, hslot, hist, nseg, &sb->dyn[0], &sb->err, glist, loff, &sb->lpool, lcap};
   auto sym_bin = [&](int k0, int k1) {
@@ -588,6 +624,7 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
     }
     cudaGetLastError();
   }
+
   if (int e = phase_check("scan_bin", st, sb->dbg)) return e;
   CK(cudaMemcpyAsync(hb, sb, sizeof(SmallBlock), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -639,8 +676,8 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
     mem.failed = false;  // optional, as above
     if (units) {
       PhaseTimer t("scan_bin", st);
-      launch_plan_parts(rs, list + key_off[KEY_HEAVY], nheavy, hslot, hist, loff, nseg, ucap, HU_SPAN_SEGS, pcnt,
-                        pcap, units, st);
+      launch_plan_parts(rs, list + key_off[KEY_HEAVY], nheavy, hslot, hist, loff, Cp, nseg, ucap, HU_SPAN_SEGS,
+                        pcnt, pcap, units, st);
     }
     cudaGetLastError();
   }
@@ -653,36 +690,10 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
     gend = mem.tmp<int32_t>((size_t)A->nnz);
     if (!gcur || !gend) return HS_ENOMEM;
   }
-  // heavy bin: the B segment index (rows longer than min_len; the table kept
-  // within an eighth of the free memory, at most 4 GiB)
-  int32_t *bci_id = nullptr, *bci = nullptr;
-  if (key_off[NKEYS] > key_off[KEY_HEAVY] && B->nnz > 0) {
-    size_t free_b = 0, total_b = 0;
-    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
-      const size_t budget = free_b / 8 < ((size_t)4 << 30) ? free_b / 8 : ((size_t)4 << 30);
-      const int64_t stride = (int64_t)nseg + 1;
-      const int64_t row_bytes = stride * 4;
-      int64_t min_len = 32;
-      const int64_t need = (B->nnz * row_bytes + (int64_t)budget - 1) / (int64_t)(budget ? budget : 1);
-      if (need > min_len) min_len = need;
-      int64_t max_rows = B->nnz / (min_len + 1);
-      if (max_rows > (int64_t)(budget / row_bytes)) max_rows = (int64_t)(budget / row_bytes);
-      if (max_rows > 0 && min_len < 0x7fffffff) {
-        bci_id = (int32_t *)mem.raw(sizeof(int32_t) * (size_t)B->m);
-        bci = bci_id ? (int32_t *)mem.raw((size_t)max_rows * (size_t)row_bytes) : nullptr;
-        if (bci_id) mem.scratch.push_back({bci_id, sizeof(int32_t) * (size_t)B->m});
-        if (bci) mem.scratch.push_back({bci, (size_t)max_rows * (size_t)row_bytes});
-        mem.failed = false;  // optional: without it the part ends are searched
-        if (!bci) bci_id = nullptr;
-        else {
-          PhaseTimer t("bci", st);
-          launch_build_bci(rb, nseg, (int)min_len, max_rows, bci_id, bci, &sb->bci_cnt, st);
-          if (int e = phase_check("bci", st, sb->dbg)) return e;
-        }
-      }
-    }
-    cudaGetLastError();
-  }
+  // heavy bin: the B segment index (built before the symbolic pass when
+  // symbolic units used it)
+  if (key_off[NKEYS] > key_off[KEY_HEAVY])
+    if (int e = build_bci()) return e;
   if (units && vb) {
     PhaseTimer t("heavy_pairs", st);
     launch_build_pairs(rs, rb, units, nunits, bci_id, bci, nseg, a_bytes, pstart, ppre, paval, st);

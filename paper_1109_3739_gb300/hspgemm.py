@@ -107,6 +107,14 @@ def _lib():
             L.hs_trim_memory.restype = ci
             L.hs_test_lookback_expiry.argtypes = [ci, i64]
             L.hs_test_lookback_expiry.restype = ci
+            L.hs_batch_plan_create.argtypes = [ci, i64, P(hs_mat), P(hs_mat), P(vp), P(hs_allocator), vp, u32]
+            L.hs_batch_plan_create.restype = ci
+            L.hs_batch_plan_execute.argtypes = [vp, vp]
+            L.hs_batch_plan_execute.restype = ci
+            L.hs_batch_plan_result.argtypes = [vp, P(hs_mat), P(ctypes.c_int64), vp]
+            L.hs_batch_plan_result.restype = ci
+            L.hs_batch_plan_destroy.argtypes = [vp, vp]
+            L.hs_batch_plan_destroy.restype = None
             L.hs_set_tuning.argtypes = [P(hs_tuning)]
             L.hs_set_tuning.restype = ci
             L.hs_get_tuning.argtypes = [P(hs_tuning)]
@@ -284,6 +292,57 @@ def spgemm_batched(semiring: str, As: list, Bs: list, validate: bool = False, st
     if st != 0:
         raise HsError(st, "hs_spgemm_batched")
     return _adopt_output(al, c), np.array(offs[:], dtype=np.int64)
+
+
+class BatchPlan:
+    """C_i = A_i * B_i for every pair by one persistent launch per execution
+    (hs_batch_plan_*): created once (the problems stacked, C sized by the flop
+    bound), then execute() recomputes C with no allocation and no host
+    synchronisation (capturable in a CUDA graph); result() returns (C,
+    row_offsets) as for spgemm_batched, C's arrays owned by the plan."""
+
+    def __init__(self, semiring: str, As: list, Bs: list, stream=None):
+        L = _lib()
+        self.count = len(As)
+        if self.count != len(Bs):
+            raise ValueError("As and Bs differ in length")
+        dev = _device_of(As[0]) if self.count else _torch().device("cuda")
+        self._al = _TorchAlloc(dev)
+        A_arr = (hs_mat * max(self.count, 1))(*[x.desc() for x in As])
+        B_arr = (hs_mat * max(self.count, 1))(*[x.desc() for x in Bs])
+        h = ctypes.c_void_p()
+        st = L.hs_batch_plan_create(SEMIRING[semiring], self.count, A_arr, B_arr, ctypes.byref(h),
+                                    ctypes.byref(self._al.struct), _stream_ptr(stream), 0)
+        if st != 0:
+            raise HsError(st, "hs_batch_plan_create")
+        self._h = h
+
+    def execute(self, stream=None):
+        st = _lib().hs_batch_plan_execute(self._h, _stream_ptr(stream))
+        if st != 0:
+            raise HsError(st, "hs_batch_plan_execute")
+
+    def result(self, stream=None):
+        """(C, row_offsets) of the last execution (synchronises; C views the plan's arrays)."""
+        torch = _torch()
+        c = hs_mat()
+        offs = (ctypes.c_int64 * (self.count + 1))()
+        st = _lib().hs_batch_plan_result(self._h, ctypes.byref(c), offs, _stream_ptr(stream))
+        if st != 0:
+            raise HsError(st, "hs_batch_plan_result")
+        live = self._al.live
+        nnz = int(c.nnz)
+        rowptr = live[int(c.ptr)].view(torch.int64)[:c.m + 1]
+        col = live[int(c.idx)].view(torch.int32)[:nnz]
+        tdt = {"f64": torch.float64, "f32": torch.float32, "i32": torch.int32, "i64": torch.int64}
+        dt = DTYPE_NAME[c.dtype]
+        val = live[int(c.val)].view(tdt[dt])[:nnz] if c.val else None
+        return DeviceCSR(c.m, c.n, rowptr, col, val, dt), np.array(offs[:], dtype=np.int64)
+
+    def close(self, stream=None):
+        if self._h is not None:
+            _lib().hs_batch_plan_destroy(self._h, _stream_ptr(stream))
+            self._h = None
 
 
 FLAG_STAGE_ON_DEVICE = 2

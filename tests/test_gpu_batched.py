@@ -85,3 +85,77 @@ def test_full_batch_sampled():
         A, B = probs[i]
         _, rn = oracle.spgemm_count(A, B, nthreads=NT)
         np.testing.assert_array_equal(np.diff(rp[offs[i]:offs[i + 1] + 1]), rn)
+
+
+# ---- one persistent launch per execution (hs_batch_plan_*)
+@pytest.mark.parametrize("sr,dt", [("plus_times", "f64"), ("plus_times", "f32"), ("or_and", "bool"),
+                                   ("plus_times", "i64"), ("min_plus", "i32"), ("min_plus", "f32")])
+def test_persistent_plan_every_problem(sr, dt):
+    h = H()
+    probs = I.batched_er(40, seed=7, dtype=dt, nmax=2048)
+    As = [h.DeviceCSR.from_host(a) for a, _ in probs]
+    Bs = [h.DeviceCSR.from_host(b) for _, b in probs]
+    plan = h.BatchPlan(sr, As, Bs)
+    try:
+        plan.execute()
+        C, offs = plan.result()
+        assert len(offs) == 41 and offs[-1] == sum(a.m for a, _ in probs)
+        for i, (A, B) in enumerate(probs):
+            check_problem(sr, C, offs, i, A, B)
+    finally:
+        plan.close()
+
+
+def test_persistent_plan_graph_replay_mixed_rows():
+    """Rows of every tier (warp rows, CTA rows, a CTA row of more than 2048
+    outputs done column range by column range), empty and rectangular
+    problems; the execution captured in a CUDA graph and replayed twice."""
+    import torch
+    h = H()
+    probs = [
+        (I.er_matrix(16, 200, 4, seed=21), I.er_matrix(200, 12000, 1, seed=22)),  # f = 3000, c > 2048
+        (I.er_matrix(3000, 3000, 12, seed=23), I.er_matrix(3000, 3000, 12, seed=24)),
+        (I.er_matrix(500, 700, 2, seed=25), I.er_matrix(700, 40, 3, seed=26)),
+        (I.CSR(5, 7, np.zeros(6, np.int64), np.zeros(0, np.int32), np.zeros(0), "f64"),
+         I.er_matrix(7, 9, 2, seed=27)),
+        (I.er_matrix(64, 64, 8, seed=28), I.er_matrix(64, 64, 8, seed=29)),
+    ]
+    f0 = np.diff(probs[0][1].rowptr)[probs[0][0].col].sum() / probs[0][0].m
+    assert 2048 < f0 <= 4096
+    As = [h.DeviceCSR.from_host(a) for a, _ in probs]
+    Bs = [h.DeviceCSR.from_host(b) for _, b in probs]
+    plan = h.BatchPlan("plus_times", As, Bs)
+    try:
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            plan.execute()
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        l0 = h.launch_count()
+        with torch.cuda.graph(g):
+            plan.execute()
+        assert h.launch_count() - l0 == 1  # one kernel per execution (besides one memset)
+        first = None
+        for rep in range(2):
+            g.replay()
+            torch.cuda.synchronize()
+            C, offs = plan.result()
+            for i, (A, B) in enumerate(probs):
+                check_problem("plus_times", C, offs, i, A, B)
+            host = (C.rowptr.cpu().clone(), C.col.cpu().clone(), C.val.cpu().clone())
+            if first is None:
+                first = host
+            else:  # replays are deterministic in structure; values agree within the oracle's tolerance above
+                assert torch.equal(first[0], host[0]) and torch.equal(first[1], host[1])
+    finally:
+        plan.close()
+
+
+def test_persistent_plan_rejects_rows_beyond_its_tables():
+    h = H()
+    A = I.er_matrix(4, 100, 4, seed=31)       # rows of 100 entries
+    B = I.er_matrix(100, 10000, 5, seed=32)   # rows of 500 entries: 50000 products per row of A
+    with pytest.raises(h.HsError) as e:
+        h.BatchPlan("plus_times", [h.DeviceCSR.from_host(A)], [h.DeviceCSR.from_host(B)])
+    assert e.value.code == -7
