@@ -854,11 +854,25 @@ def main():
             if i > 0:
                 etimes.append(dt)
                 h2d_ms.append(eh0.elapsed_time(eh1))
+        # the link's own device-to-host rate: one plain copy of 1 GiB into pinned memory
+        probe_d = torch.empty(1 << 30, dtype=torch.uint8, device=dev)
+        probe_h = torch.empty(1 << 30, dtype=torch.uint8, pin_memory=True)
+        link = []
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            probe_h.copy_(probe_d, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            link.append((1 << 30) / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+        probe_d = probe_h = None
         e2e = {"value": flops / statistics.median(etimes), "unit": "mults/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": 1000 * statistics.median(etimes),
                "h2d_ms": statistics.median(h2d_ms),
                "product_and_d2h_ms": 1000 * statistics.median(etimes) - statistics.median(h2d_ms),
+               "link_d2h_gbs": statistics.median(link),
                "api": f"spgemm_to_host, {E2E_BLOCKS} row blocks"}
         hA = out_rp = out_j = out_v = None
         torch.cuda.empty_cache()

@@ -241,11 +241,17 @@ int hs_trim_memory(void);
  *   sym_heavy_from  symbolic rows with f > sym_heavy_from take the bitmap
  *                   kernel that also writes their sorted column lists
  *                   (4096..large capacity; 0 = the large capacity)
+ *   sort_max        numeric rows with 32 < f <= sort_max whose output count
+ *   sort_pct        c is at least sort_pct percent of f sort their products
+ *                   in a warp's registers (expand, sort, compress) instead of
+ *                   hashing them (sort_max 32..1024, 1024; sort_pct 0..101,
+ *                   50; 101 switches the sort tiers off)
  * Results do not depend on the thresholds.  hs_set_tuning(NULL) restores the
  * defaults (given last above).  Both calls return HS_OK (hs_get_tuning:
  * HS_EINVAL for NULL). */
 typedef struct hs_tuning {
   int32_t warp_s_max, mid_s_max, large_s_max, sym_mid_s_max, sym_heavy_from;
+  int32_t sort_max, sort_pct;
 } hs_tuning;
 int hs_set_tuning(const hs_tuning *t);
 int hs_get_tuning(hs_tuning *t);

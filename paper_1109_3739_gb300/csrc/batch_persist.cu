@@ -8,17 +8,19 @@
 // kernel whose CTAs stay resident and pull their work from atomic counters,
 // the phases separated by grid-wide barriers (bounded waits):
 //   1. products per row f_r (Algorithm 1's row-wise work), and the rows'
-//      tiers: f_r <= 256 to a warp, larger rows to the whole CTA;
+//      tiers: f_r <= 1024 to a warp (256 when a problem has 2^22 columns or
+//      more), larger rows to the whole CTA;
 //   2. distinct columns per row (the occupancy half of Figure 1's sparse
-//      accumulator, as a shared hash set: a warp's 512 slots, or the CTA's
+//      accumulator, as a shared hash set: a warp's 2048 slots, or the CTA's
 //      8192), a CTA row's outputs also counted in 16 column buckets when they
 //      exceed one CTA table (2048 values);
 //   3. the row counts scanned into C's row offsets (each CTA scans a block of
 //      rows, then adds the totals of the blocks before it);
-//   4. the values: each row accumulated in a shared hash table of keys and
-//      values and written in ascending column order at its offset (a CTA row
-//      with more than 2048 outputs column range by column range, ranges cut
-//      from its buckets).
+//   4. the values, written in ascending column order at the row's offset: a
+//      warp row by sorting its products (256, 512 or 1024 keys) in the warp's
+//      registers and folding equal columns (sort_row), a CTA row in a shared hash table of keys and
+//      values (with more than 2048 outputs column range by column range,
+//      ranges cut from its buckets).
 // No allocation and no host synchronisation happen in an execution, so it
 // can be captured in a CUDA graph and replayed.
 #include <algorithm>
@@ -32,7 +34,8 @@
 namespace hs {
 
 constexpr int BP_NT = 256, BP_NW = BP_NT / 32;
-constexpr int BPW_SLOTS = 512, BPW_CAP = 256;    // warp tier: rows with f <= 256
+constexpr int BPW_SYM = 2048;                    // warp tier symbolic set: f <= 1024
+constexpr int BPW_FS = 256, BPW_F = 1024;        // warp tier values: 32*8 or 32*32 sorted products
 constexpr int BPC_SYM = 8192;                    // CTA tier symbolic set: f <= 4096
 constexpr int BPC_SLOTS = 4096, BPC_CAP = 2048;  // CTA tier values: at most 2048 per column range
 constexpr int BP_FMAX = 4096;                    // rows with more products are not taken
@@ -55,6 +58,7 @@ struct BpArgs {
   RightOp B;
   int64_t m;           // stacked rows
   int32_t *wlist;      // warp-tier rows
+  int wf_max;          // products of a warp-tier row at most (BPW_F, or BPW_FS for very wide problems)
   int32_t *clist;      // CTA-tier rows
   int32_t *cbig;       // per CTA-tier row: its bucket record, or -1
   int32_t *buckets;    // BP_NBUCK counts per CTA row with more than BPC_CAP outputs
@@ -67,6 +71,12 @@ struct BpArgs {
   BpCounters *ctr;
   long long spin_limit;
 };
+
+// bytes of a warp's shared region: its symbolic set, then its sorted products
+template <typename T> __host__ __device__ constexpr size_t bp_warp_bytes() {
+  return SortSmemLayout<T, BPW_F / 32>::per_warp > (size_t)BPW_SYM * 4 ? SortSmemLayout<T, BPW_F / 32>::per_warp
+                                                                       : (size_t)BPW_SYM * 4;
+}
 
 // Grid-wide barrier for co-resident CTAs (cooperative launch): the last CTA to
 // arrive opens the next generation.  Waits are bounded: a CTA that gives up
@@ -111,7 +121,7 @@ template <class SR>
 __global__ void __launch_bounds__(BP_NT, 2) k_batch_persist(BpArgs a) {
   using T = typename SR::val_t;
   using Struct = Semiring<OR_AND, NoVal>;
-  using LW = WarpNumSmem<T, BPW_SLOTS, BPW_CAP>;
+  using LW = SortSmemLayout<T, BPW_F / 32>;
   using LC = CtaNumLayout<T, BPC_SLOTS, BPC_CAP>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_item, s_count, s_cnt_b[BP_NBUCK], s_wtmp[33];
@@ -134,8 +144,8 @@ __global__ void __launch_bounds__(BP_NT, 2) k_batch_persist(BpArgs a) {
       a.Cp[r + 1] = 0;
       if (fr > BP_FMAX) atomicOr(&ctr->err, 1);
     }
-    bp_append(r < a.m && fr > 0 && fr <= BPW_CAP, (int)r, &ctr->nwarp, a.wlist);
-    bp_append(r < a.m && fr > BPW_CAP && fr <= BP_FMAX, (int)r, &ctr->ncta, a.clist);
+    bp_append(r < a.m && fr > 0 && fr <= a.wf_max, (int)r, &ctr->nwarp, a.wlist);
+    bp_append(r < a.m && fr > a.wf_max && fr <= BP_FMAX, (int)r, &ctr->ncta, a.clist);
   }
   if (blockIdx.x == 0 && tid == 0) a.Cp[0] = 0;
   bp_grid_sync(ctr, a.spin_limit);
@@ -182,18 +192,18 @@ __global__ void __launch_bounds__(BP_NT, 2) k_batch_persist(BpArgs a) {
       }
       __syncthreads();
     }
-    int *wkeys = reinterpret_cast<int *>(smem_raw) + warp * BPW_SLOTS;  // a warp's set
+    int *wkeys = reinterpret_cast<int *>(smem_raw + (size_t)warp * bp_warp_bytes<T>());  // a warp's set
     while (true) {
       int i = 0;
       if (lane == 0) i = atomicAdd(&ctr->sym_w, 1);
       i = __shfl_sync(FULL, i, 0);
       if (i >= nw_rows) break;
       const int r = a.wlist[i];
-      for (int s = lane; s < BPW_SLOTS; s += 32) wkeys[s] = EMPTY;
+      for (int s = lane; s < BPW_SYM; s += 32) wkeys[s] = EMPTY;
       __syncwarp();
       int cnt = 0;
       warp_products<Struct>(A, B, A.p[r], A.p[r + 1],
-                            [&](int col, NoVal, int) { cnt += hash_insert_key(wkeys, BPW_SLOTS - 1, col); });
+                            [&](int col, NoVal, int) { cnt += hash_insert_key(wkeys, BPW_SYM - 1, col); });
       cnt = warp_sum(cnt);
       if (lane == 0) a.Cp[r + 1] = cnt;
       __syncwarp();
@@ -302,12 +312,9 @@ __global__ void __launch_bounds__(BP_NT, 2) k_batch_persist(BpArgs a) {
       }
       __syncthreads();
     }
-    unsigned char *wb = smem_raw + (size_t)warp * LW::per_warp;
-    int *wkeys = reinterpret_cast<int *>(wb);
-    T *wvals = reinterpret_cast<T *>(wb + (size_t)BPW_SLOTS * 4);
-    int *wck = reinterpret_cast<int *>(wb + LW::region0);
-    T *wcv = reinterpret_cast<T *>(wb + LW::region0 + (size_t)BPW_CAP * 4);
-    EmitScratch *wes = reinterpret_cast<EmitScratch *>(wb + LW::region0 + LW::compact);
+    unsigned char *wb = smem_raw + (size_t)warp * bp_warp_bytes<T>();
+    int *s_col = reinterpret_cast<int *>(wb);
+    T *s_val = reinterpret_cast<T *>(wb + LW::col_bytes);
     while (true) {
       int i = 0;
       if (lane == 0) i = atomicAdd(&ctr->num_w, 1);
@@ -316,19 +323,25 @@ __global__ void __launch_bounds__(BP_NT, 2) k_batch_persist(BpArgs a) {
       const int r = a.wlist[i];
       const int64_t cb = a.Cp[r];
       const int c = (int)(a.Cp[r + 1] - cb);
-      const int slots = max(64, min(BPW_SLOTS, next_pow2(2 * min(c, BPW_CAP))));
-      const unsigned mask = slots - 1;
-      for (int s = lane; s < slots; s += 32) {
-        wkeys[s] = EMPTY;
-        if constexpr (SR::has_val) wvals[s] = SR::identity();
+      int64_t fr = 0;  // the row's products, again (its A entries' B row lengths)
+      for (int64_t q = A.p[r] + lane; q < A.p[r + 1]; q += 32) {
+        if (!HS_G(dbg, q >= 0 && q < A.nnz, 50, q)) break;
+        const int k = __ldg(A.j + q);
+        if (HS_G(dbg, k >= 0 && k < B.rows, 51, k)) fr += __ldg(B.p + k + 1) - __ldg(B.p + k);
       }
-      __syncwarp();
-      warp_products<SR>(A, B, A.p[r], A.p[r + 1],
-                        [&](int col, T v, int) { hash_insert_val<SR>(wkeys, wvals, mask, col, v, &ctr->kerr); });
-      __syncwarp();
-      if (HS_G(dbg, cb + c <= a.cap, 81, cb + c))
-        group_sort_emit<WarpGroup, T, SR::has_val>(wkeys, wvals, slots, c, wck, wcv, wb, nullptr, wes, a.Cj + cb,
-                                                   SR::has_val ? Cv + cb : nullptr, &ctr->kerr, BPW_CAP, dbg);
+      fr = warp_sum(fr);
+      if (HS_G(dbg, cb + c <= a.cap, 81, cb + c)) {
+        T *out_v = SR::has_val ? Cv + cb : nullptr;
+        if (fr <= BPW_FS)
+          sort_row<SR, BPW_FS / 32, true>(A, B, A.p[r], A.p[r + 1], (int)fr, c, s_col, s_val, a.Cj + cb, out_v,
+                                          &ctr->kerr);
+        else if (fr <= 2 * BPW_FS)
+          sort_row<SR, 2 * BPW_FS / 32, false>(A, B, A.p[r], A.p[r + 1], (int)fr, c, s_col, s_val, a.Cj + cb,
+                                               out_v, &ctr->kerr);
+        else
+          sort_row<SR, BPW_F / 32, false>(A, B, A.p[r], A.p[r + 1], (int)fr, c, s_col, s_val, a.Cj + cb, out_v,
+                                          &ctr->kerr);
+      }
       __syncwarp();
     }
   }
@@ -336,7 +349,7 @@ __global__ void __launch_bounds__(BP_NT, 2) k_batch_persist(BpArgs a) {
 
 template <class SR> size_t bp_smem() {
   using T = typename SR::val_t;
-  const size_t w = (size_t)BP_NW * WarpNumSmem<T, BPW_SLOTS, BPW_CAP>::per_warp;
+  const size_t w = (size_t)BP_NW * bp_warp_bytes<T>();
   const size_t c = CtaNumLayout<T, BPC_SLOTS, BPC_CAP>::bytes;
   const size_t s = (size_t)BPC_SYM * 4 + sizeof(CtaExpandSmem<NoVal, BP_CH>);
   return std::max(w, std::max(c, s));
@@ -523,6 +536,12 @@ extern "C" int hs_batch_plan_create(int semiring, int64_t count, const hs_mat *A
   a.A = rs;
   a.B = rb;
   a.m = m;
+  // the sorted warp rows pack (column - the row's least column) into 32-bit
+  // keys with 10 bits of product index: problems of 2^22 columns or more
+  // send rows above 256 products to the CTA tier
+  int64_t nmax = 0;
+  for (int64_t i = 0; i < count; ++i) nmax = B[i].n > nmax ? B[i].n : nmax;
+  a.wf_max = nmax >= SORT_PACKED_COLS ? BPW_FS : BPW_F;
   a.wlist = (int32_t *)bp_alloc(P, 4 * (size_t)(m > 0 ? m : 1), st);
   a.clist = (int32_t *)bp_alloc(P, 4 * (size_t)(m > 0 ? m : 1), st);
   a.cbig = (int32_t *)bp_alloc(P, 4 * (size_t)(m > 0 ? m : 1), st);

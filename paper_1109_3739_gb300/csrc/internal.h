@@ -19,8 +19,20 @@ constexpr int KEY_MID_S = 4;    // symbolic: f <= 1024;  numeric: c <= 1024
 constexpr int KEY_MID = 5;      // symbolic: f <= 4096;  numeric: c <= CAP_MID
 constexpr int KEY_LARGE_S = 6;  // numeric: c <= cap_large / 2
 constexpr int KEY_LARGE = 7;    // symbolic: f <= min(16384, cap_large); numeric: c <= cap_large
-constexpr int KEY_HEAVY = 8;    // 8 + (62 - floor(log2 f)): symbolic bitmap / numeric column parts
+// numeric rows with little compression, one warp sorting 32*K products:
+constexpr int KEY_SORT_XS = 8;  // f <= 128 (K = 4)
+constexpr int KEY_SORT_S = 9;   // f <= 256 (K = 8)
+constexpr int KEY_SORT_M = 10;  // f <= 512 (K = 16)
+constexpr int KEY_SORT = 11;    // f <= 1024 (K = 32)
+constexpr int KEY_HEAVY = 12;   // 12 + (62 - floor(log2 f)): symbolic bitmap / numeric column parts
 constexpr int F_TINY = 32, F_WARP_S = 128, F_WARP = 512, F_MID_S = 1024, F_MID = 4096, F_LARGE = 16384;
+constexpr int F_SORT_XS = 128, F_SORT_S = 256, F_SORT_M = 512, F_SORT = 1024;
+// Sort tiers pack (column - min column) << log2(32K) | product index into 32
+// bits for 32*K-product rows; the tiers above 256 products hold no 64-bit
+// fallback, so a matrix with at least SORT_PACKED_COLS columns keeps rows
+// of more than 256 products out of them (numeric_bins).
+constexpr int SORT_WIDE_K = 8;
+constexpr int64_t SORT_PACKED_COLS = (1 << 22) - 1;
 constexpr int CAP_MID_S = 1024, CAP_MID = 2048;
 // Column segments recorded for rows that may need column parts: width SEG_W
 // (a multiple of 1024, at most every numeric table's capacity).
@@ -48,6 +60,8 @@ struct BinCfg {
   int large_s_max;     // numeric: rows with CAP_MID < c <= this take the half-capacity large tier
   int sym_mid_s_max;   // symbolic: rows with 512 < f <= this take the 2048-slot tier (512..1024)
   int sym_heavy_from;  // symbolic: rows with f > this take the bitmap kernel (4096..cap_large)
+  int sort_max;        // numeric: rows with 32 < f <= this and 100*c >= sort_pct*f sort their products (32..1024)
+  int sort_pct;        // (0..101; 101 switches the sort tiers off)
 };
 // Symbolic bins.  Every row that may end in the numeric heavy bin (c >
 // cap_large needs f > cap_large) takes the bitmap kernel, which also writes
@@ -66,6 +80,8 @@ __host__ __device__ inline int sym_key(int64_t f, const BinCfg &b) {
 __host__ __device__ inline int num_key(int64_t f, int64_t c, const BinCfg &b) {
   if (c <= 0) return 0;
   if (f <= F_TINY) return KEY_TINY;
+  if (f <= b.sort_max && c * 100 >= f * b.sort_pct)
+    return f <= F_SORT_XS ? KEY_SORT_XS : (f <= F_SORT_S ? KEY_SORT_S : (f <= F_SORT_M ? KEY_SORT_M : KEY_SORT));
   if (f <= b.warp_s_max) return KEY_WARP_S;
   if (f <= F_WARP) return KEY_WARP;
   if (c <= b.mid_s_max) return KEY_MID_S;
@@ -76,6 +92,11 @@ __host__ __device__ inline int num_key(int64_t f, int64_t c, const BinCfg &b) {
 }
 // the default thresholds for a value width, clamped tuning values otherwise
 BinCfg bin_config(int value_bytes);
+// the numeric pass's thresholds for a product with ncols columns
+inline BinCfg numeric_bins(BinCfg b, int64_t ncols) {
+  if (ncols >= SORT_PACKED_COLS && b.sort_max > F_SORT_S) b.sort_max = F_SORT_S;
+  return b;
+}
 
 // ---------------------------------------------------------- device views
 struct RowSet {          // the left operand's stored rows
@@ -251,10 +272,10 @@ struct NumArgs {
   const void *paval;
   int pair_abytes;        // width of the left values the pairs carry (0: none)
 };
-// kind: 0 tiny, 1 warp_s, 2 warp, 3 mid_s, 4 mid, 5 large_s, 6 large, 7 heavy
-// (bin key KEY_TINY + kind; heavy takes every key from KEY_HEAVY on).
-// dtype codes as in the ABI.
-constexpr int NUM_KINDS = 8;
+// kind: 0 tiny, 1 warp_s, 2 warp, 3 mid_s, 4 mid, 5 large_s, 6 large,
+// 7 sort_xs, 8 sort_s, 9 sort_m, 10 sort, 11 heavy (bin key KEY_TINY + kind;
+// heavy takes every key from KEY_HEAVY on).  dtype codes as in the ABI.
+constexpr int NUM_KINDS = 12;
 bool launch_numeric_pt(int dtype, int kind, const NumArgs &a, cudaStream_t st);
 bool launch_numeric_mp(int dtype, int kind, const NumArgs &a, cudaStream_t st);
 bool launch_numeric_oa(int kind, const NumArgs &a, cudaStream_t st);

@@ -225,9 +225,9 @@ static int spgemm_noalloc_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat 
 
   launch_scan_i64(Cp, m + 1, scan_tmp, st);
   NA_CK(cudaMemsetAsync(sb->key_cnt, 0, sizeof(int) * NKEYS, st));
-  launch_num_count(rs, f, Cp, bins, sb->key_cnt, st);
+  launch_num_count(rs, f, Cp, numeric_bins(bins, n), sb->key_cnt, st);
   launch_key_offsets(sb->key_cnt, sb->key_off, sb->key_cur, st);
-  launch_scatter_num(rs, f, Cp, bins, sb->key_cur, list, st);
+  launch_scatter_num(rs, f, Cp, numeric_bins(bins, n), sb->key_cur, list, st);
   NA_CK(cudaMemcpyAsync(&sb->nnz, Cp + m, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
   if (int e = check_last()) return e;
   NA_CK(cudaMemcpyAsync(&hb, sb, sizeof(NaBlock), cudaMemcpyDeviceToHost, st));

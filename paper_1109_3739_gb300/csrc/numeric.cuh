@@ -22,6 +22,7 @@
 #pragma once
 #include "common.cuh"
 #include "internal.h"
+#include "sortrow.cuh"
 
 namespace hs {
 
@@ -818,6 +819,51 @@ template <class K> int fit_per_sm(K kernel, int threads, size_t smem) {
   return n < 1 ? 1 : n;
 }
 
+// ------------------------------------------------------------- sort tiers
+// Rows with 32 < f <= F_SORT whose output count is close to their product
+// count: one warp per row sorts the row's products (sort_row), one kernel
+// per register width K (32*K products), so each kernel's code stays small.
+// Only the tiers of at most 32*SORT_WIDE_K products sort 64-bit keys for
+// rows spanning too many columns.
+constexpr int NSORT_WPB = 4;
+static_assert(SORT_WIDE_K * 32 == F_SORT_S, "the wide-key tiers are those of at most 256 products");
+template <typename T, int K> struct SortSmemLayout {
+  static constexpr size_t col_bytes = ((size_t)sr_pad_len(32 * K) * 4 + 15) & ~(size_t)15;
+  static constexpr size_t per_warp = col_bytes + (((size_t)32 * K * vbytes<T>() + 15) & ~(size_t)15);
+};
+template <class SR, int K>
+__global__ void __launch_bounds__(NSORT_WPB * 32, K >= 32 ? 6 : 8) k_num_sort(NumArgs a) {
+  using T = typename SR::val_t;
+  using L = SortSmemLayout<T, K>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int w = threadIdx.x >> 5;
+  int *s_col = reinterpret_cast<int *>(smem_raw + (size_t)w * L::per_warp);
+  T *s_val = reinterpret_cast<T *>(smem_raw + (size_t)w * L::per_warp + L::col_bytes);
+  const DevCsr A = ndev_a(a.A), B = ndev_b(a.B);
+  T *Cv = reinterpret_cast<T *>(a.Cv);
+  for (int idx = blockIdx.x * NSORT_WPB + w; idx < a.count; idx += gridDim.x * NSORT_WPB) {
+    const int r = a.list[idx];
+    if (!HS_G(a.A.dbg, r >= 0 && r < a.A.nslots, 35, r)) continue;
+    const int64_t o = nout_row(a.A, r);
+    const int64_t cb = a.Cp[o];
+    const int c = (int)(a.Cp[o + 1] - cb);
+    const int64_t F = a.f[r];
+    T *out_v = SR::has_val ? Cv + cb : nullptr;
+    sort_row<SR, K, (K <= SORT_WIDE_K)>(A, B, A.p[r], A.p[r + 1], F <= 32 * K ? (int)F : -1, c, s_col, s_val,
+                                        a.Cj + cb, out_v, a.err);
+    __syncwarp();
+  }
+}
+
+template <class SR, int K> void launch_num_sort(const NumArgs &a, cudaStream_t st) {
+  using T = typename SR::val_t;
+  const size_t bytes = SortSmemLayout<T, K>::per_warp * NSORT_WPB;
+  auto k = k_num_sort<SR, K>;
+  set_smem_attr(k, bytes);
+  count_launch();
+  k<<<ngrid_cap(a.count, NSORT_WPB, fit_per_sm(k, NSORT_WPB * 32, bytes)), NSORT_WPB * 32, bytes, st>>>(a);
+}
+
 template <class SR, int SLOTS, int CAP> void launch_num_warp(const NumArgs &a, cudaStream_t st) {
   using T = typename SR::val_t;
   const size_t bytes = WarpNumSmem<T, SLOTS, CAP>::per_warp * NWARP_WPB;
@@ -853,7 +899,11 @@ template <class SR> void launch_numeric_sr(int kind, const NumArgs &a, cudaStrea
       if constexpr (CAPL / 2 > CAP_MID) launch_num_cta<SR, CAPL, CAPL / 2, 512>(a, st);
       break;
     case 6: launch_num_cta<SR, 2 * CAPL, CAPL, 1024>(a, st); break;
-    case 7: {
+    case 7: launch_num_sort<SR, 4>(a, st); break;
+    case 8: launch_num_sort<SR, 8>(a, st); break;
+    case 9: launch_num_sort<SR, 16>(a, st); break;
+    case 10: launch_num_sort<SR, 32>(a, st); break;
+    case 11: {
       if (a.units && a.nunits > 0) {
         const size_t ub = sizeof(UnitSmem<T>);
         auto ku = k_num_units<SR>;

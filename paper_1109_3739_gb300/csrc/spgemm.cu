@@ -303,7 +303,8 @@ static bool numeric_supported(int sr, int adt, int bdt, int &out_dt) {
 
 // ----------------------------------------------------------------- tuning
 static std::mutex g_tune_mu;
-static hs_tuning g_tune = {F_WARP_S, CAP_MID_S, 4096, F_MID_S, 0};
+static const hs_tuning k_tune_default = {F_WARP_S, CAP_MID_S, 4096, F_MID_S, 0, F_SORT, 50};
+static hs_tuning g_tune = k_tune_default;
 
 static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
@@ -320,6 +321,8 @@ BinCfg bin_config(int value_bytes) {
   b.large_s_max = clampi(t.large_s_max, CAP_MID, b.cap_large / 2 > CAP_MID ? b.cap_large / 2 : CAP_MID);
   b.sym_mid_s_max = clampi(t.sym_mid_s_max, F_WARP, F_MID_S);
   b.sym_heavy_from = t.sym_heavy_from <= 0 ? b.cap_large : clampi(t.sym_heavy_from, F_MID, b.cap_large);
+  b.sort_max = clampi(t.sort_max, F_TINY, F_SORT);
+  b.sort_pct = clampi(t.sort_pct, 0, 101);
   return b;
 }
 
@@ -595,9 +598,9 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
     PhaseTimer t("scan_bin", st);
     launch_scan_i64(Cp, m + 1, scan_tmp, st);
     CK(cudaMemsetAsync(sb->key_cnt, 0, sizeof(int) * NKEYS, st));
-    launch_num_count(rs, f, Cp, bins, sb->key_cnt, st);
+    launch_num_count(rs, f, Cp, numeric_bins(bins, n), sb->key_cnt, st);
     launch_key_offsets(sb->key_cnt, sb->key_off, sb->key_cur, st);
-    launch_scatter_num(rs, f, Cp, bins, sb->key_cur, list, st);
+    launch_scatter_num(rs, f, Cp, numeric_bins(bins, n), sb->key_cur, list, st);
     CK(cudaMemcpyAsync(&sb->nnz, Cp + m, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
   }
   // numeric heavy rows that have a sorted column list run as units (column
@@ -710,8 +713,9 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
   na.ppre = ppre;
   na.paval = paval;
   na.pair_abytes = a_bytes;
-  const char *names[NUM_KINDS] = {"numeric_tiny", "numeric_warp_s", "numeric_warp",  "numeric_mid_s",
-                                  "numeric_mid",  "numeric_large_s", "numeric_large", "numeric_heavy"};
+  const char *names[NUM_KINDS] = {"numeric_tiny",   "numeric_warp_s", "numeric_warp",   "numeric_mid_s",
+                                  "numeric_mid",    "numeric_large_s", "numeric_large", "numeric_sort_xs",
+                                  "numeric_sort_s", "numeric_sort_m",  "numeric_sort",  "numeric_heavy"};
   static_assert(KEY_TINY + NUM_KINDS - 1 == KEY_HEAVY, "one key per numeric kind before the heavy keys");
   {
     PhaseTimer t("numeric", st);
@@ -1401,7 +1405,7 @@ int hs_spasgn(const hs_mat *A, const int32_t *I, int64_t nI, const int32_t *J, i
 
 int hs_set_tuning(const hs_tuning *t) {
   std::lock_guard<std::mutex> g(g_tune_mu);
-  g_tune = t ? *t : hs_tuning{F_WARP_S, CAP_MID_S, 4096, F_MID_S, 0};
+  g_tune = t ? *t : k_tune_default;
   return HS_OK;
 }
 

@@ -21,6 +21,8 @@ CANDIDATES = {
     "large_s_max": (2048, 3072, 4096),
     "sym_mid_s_max": (512, 768, 1024),
     "sym_heavy_from": (4096, 6144, 0),
+    "sort_pct": (101, 25, 50, 75, 90),
+    "sort_max": (256, 512, 1024),
 }
 
 

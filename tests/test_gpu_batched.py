@@ -119,6 +119,7 @@ def test_persistent_plan_graph_replay_mixed_rows():
         (I.CSR(5, 7, np.zeros(6, np.int64), np.zeros(0, np.int32), np.zeros(0), "f64"),
          I.er_matrix(7, 9, 2, seed=27)),
         (I.er_matrix(64, 64, 8, seed=28), I.er_matrix(64, 64, 8, seed=29)),
+        (I.er_matrix(2000, 2000, 26, seed=30), I.er_matrix(2000, 2000, 26, seed=31)),  # warp rows of 257..1024
     ]
     f0 = np.diff(probs[0][1].rowptr)[probs[0][0].col].sum() / probs[0][0].m
     assert 2048 < f0 <= 4096
@@ -148,6 +149,34 @@ def test_persistent_plan_graph_replay_mixed_rows():
                 first = host
             else:  # replays are deterministic in structure; values agree within the oracle's tolerance above
                 assert torch.equal(first[0], host[0]) and torch.equal(first[1], host[1])
+    finally:
+        plan.close()
+
+
+def test_persistent_plan_problem_wider_than_a_packed_key():
+    """A problem of 2^25 + 2^20 columns beside a narrow one: warp rows (at most
+    256 products once a problem is that wide) sort 64-bit keys, longer rows
+    take the CTA tier."""
+    h = H()
+    n, k = (1 << 25) + (1 << 20), 2048
+    A0 = I.er_matrix(300, k, 1, seed=41)
+    per = (np.arange(k) % 40) + 1
+    rows = np.repeat(np.arange(k, dtype=np.int64), per)
+    keys = np.unique(rows * n + I.random_sequence(n, len(rows), 42).astype(np.int64))
+    rowptr, cols = I.csr_from_unique_sorted_keys(keys, k, n)
+    B0 = I.CSR(k, n, rowptr, cols, I.random_values(len(cols), "f64", 43), "f64")
+    probs = [(A0, B0), (I.er_matrix(1000, 1000, 20, seed=44), I.er_matrix(1000, 1000, 20, seed=45))]
+    f0 = np.diff(B0.rowptr)[A0.col]
+    rf = np.bincount(np.repeat(np.arange(A0.m), np.diff(A0.rowptr)), weights=f0, minlength=A0.m)
+    assert (rf > 256).any() and ((rf > 32) & (rf <= 256)).sum() > 50
+    As = [h.DeviceCSR.from_host(a) for a, _ in probs]
+    Bs = [h.DeviceCSR.from_host(b) for _, b in probs]
+    plan = h.BatchPlan("plus_times", As, Bs)
+    try:
+        plan.execute()
+        C, offs = plan.result()
+        for i, (A, B) in enumerate(probs):
+            check_problem("plus_times", C, offs, i, A, B)
     finally:
         plan.close()
 

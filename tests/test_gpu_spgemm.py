@@ -90,11 +90,11 @@ def test_wide_columns_multi_chunk():
     """More than 2^20 columns: the heavy symbolic bitmap runs several chunks."""
     n = 3 * (1 << 20) + 12345
     A = rand_sparse(64, 400, 0.8, 5, "f32")  # ~320 entries per row
-    # B: 400 rows with 60 random distinct columns each in [0, n)
-    cols = np.sort(np.stack([I.random_subset_sorted(n, 60, 100 + r) for r in range(400)]), axis=1)
-    rowptr = np.arange(0, 401 * 60, 60, dtype=np.int64)
-    B = I.CSR(400, n, rowptr, cols.reshape(-1).astype(np.int32),
-              I.random_values(400 * 60, "f32", 7), "f32")
+    # B: 400 rows of (up to) 60 random distinct columns each in [0, n)
+    rows = np.repeat(np.arange(400, dtype=np.int64), 60)
+    keys = np.unique(rows * n + I.random_sequence(n, len(rows), 100).astype(np.int64))
+    rowptr, cols = I.csr_from_unique_sorted_keys(keys, 400, n)
+    B = I.CSR(400, n, rowptr, cols, I.random_values(len(cols), "f32", 7), "f32")
     f, rf = oracle.flops(A, B)
     assert rf.max() > 16384
     check("plus_times", A, B, what="wide")

@@ -16,9 +16,12 @@ pytestmark = pytest.mark.gpu
 NT = os.cpu_count() or 1
 
 SETTINGS = [
-    {"warp_s_max": 32, "mid_s_max": 0, "large_s_max": 2048, "sym_mid_s_max": 512, "sym_heavy_from": 0},
-    {"warp_s_max": 64, "mid_s_max": 768, "large_s_max": 3072, "sym_mid_s_max": 768, "sym_heavy_from": 4096},
-    {"warp_s_max": 128, "mid_s_max": 512, "large_s_max": 4096, "sym_mid_s_max": 1024, "sym_heavy_from": 6144},
+    {"warp_s_max": 32, "mid_s_max": 0, "large_s_max": 2048, "sym_mid_s_max": 512, "sym_heavy_from": 0,
+     "sort_max": 1024, "sort_pct": 0},
+    {"warp_s_max": 64, "mid_s_max": 768, "large_s_max": 3072, "sym_mid_s_max": 768, "sym_heavy_from": 4096,
+     "sort_max": 256, "sort_pct": 75},
+    {"warp_s_max": 128, "mid_s_max": 512, "large_s_max": 4096, "sym_mid_s_max": 1024, "sym_heavy_from": 6144,
+     "sort_max": 1024, "sort_pct": 101},
 ]
 
 
@@ -77,7 +80,7 @@ def test_out_of_range_thresholds_are_clamped():
     ref = h.spgemm("plus_times", dA, dA)
     try:
         h.set_tuning({"warp_s_max": 100000, "mid_s_max": -5, "large_s_max": 1 << 30, "sym_mid_s_max": 0,
-                      "sym_heavy_from": 1})
+                      "sym_heavy_from": 1, "sort_max": 1 << 20, "sort_pct": -3})
         C = h.spgemm("plus_times", dA, dA, validate=True)
         assert torch.equal(C.rowptr, ref.rowptr) and torch.equal(C.col, ref.col)
         R, bound = oracle.spgemm("plus_times", A, A, with_bound=True, nthreads=NT)
