@@ -333,12 +333,14 @@ def run_batched(args):
         tp, _ = timed(lambda: pgraph.replay(), args.steps, args.warmup)
         P, _ = bp.result(stream=stream)
         p_nnz = P.nnz
+        p_phases = bp.phase_ms(stream=stream)
         P = None
         bp.close()
         pgraph = bp = None
         torch.cuda.empty_cache()
         persistent = {"ms_per_step": statistics.median(tp), "value": flops / (statistics.median(tp) / 1000.0),
                       "gpu_launches": p_launches, "host_syncs": 0, "nnz_C": p_nnz,
+                      "phases_ms": {k: round(v, 3) for k, v in p_phases.items()},
                       "what": "hs_batch_plan_execute captured once in a CUDA graph and replayed: one cooperative "
                               "kernel (rows pulled from atomic counters through four phases) and one memset"}
     l0 = h.launch_count()

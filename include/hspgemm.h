@@ -236,8 +236,9 @@ int hs_trim_memory(void);
  *   large_s_max     numeric rows with 2048 < c <= large_s_max take the tier
  *                   of half the large capacity (2048..4096 for 4-byte values
  *                   and bool; that tier is empty for 8-byte values; 4096)
- *   sym_mid_s_max   symbolic rows with 512 < f <= sym_mid_s_max take
- *                   2048-slot tables, the others up to f = 4096 take 8192 (512..1024; 1024)
+ *   sym_mid_s_max   symbolic rows with 512 < f <= sym_mid_s_max take one
+ *                   warp's 2048-slot table, the others up to f = 4096 a CTA's
+ *                   8192 (512..1024; 1024)
  *   sym_heavy_from  symbolic rows with f > sym_heavy_from take the bitmap
  *                   kernel that also writes their sorted column lists
  *                   (4096..large capacity; 0 = the large capacity)
@@ -325,6 +326,12 @@ int hs_batch_plan_create(int semiring, int64_t count, const hs_mat *A, const hs_
 int hs_batch_plan_execute(hs_batch_plan *plan, void *stream);
 int hs_batch_plan_result(hs_batch_plan *plan, hs_mat *C, int64_t *row_offsets, void *stream);
 void hs_batch_plan_destroy(hs_batch_plan *plan, void *stream);
+/* Profiling: the last execution's phase times in milliseconds, from the GPU's
+ * global timer read by the first CTA at the grid barriers (ms[0] products per
+ * row, ms[1] distinct columns, ms[2] row offsets, ms[3] values, ms[4] the
+ * whole kernel, ending when the last CTA leaves).  One host synchronisation.
+ * HS_EINVAL for NULL arguments. */
+int hs_batch_plan_phase_ms(hs_batch_plan *plan, double *ms, void *stream);
 
 /* SpGEMM for callers that cannot allocate device memory while they run (the
  * paper has no counterpart): for example code that has given the GPU's memory

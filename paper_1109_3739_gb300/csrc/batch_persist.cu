@@ -51,7 +51,19 @@ struct BpCounters {
   int err;   // bit 0: a row outside the tiers; 1: a barrier wait expired; 2: a column range too full
   int kerr;  // consistency codes of the row routines (hash table full, count mismatch)
   int pad[4];
+  unsigned long long tns[6];  // global timer: start, after phases 1, 2, 3 (CTA 0), -, last CTA's exit
 };
+
+__device__ __forceinline__ unsigned long long bp_now() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// CTA 0 stamps phase boundaries (profiling only: the host reads them with
+// hs_batch_plan_phase_ms)
+__device__ __forceinline__ void bp_stamp(BpCounters *c, int i) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) c->tns[i] = bp_now();
+}
 
 struct BpArgs {
   RowSet A;
@@ -60,6 +72,7 @@ struct BpArgs {
   int32_t *wlist;      // warp-tier rows
   int wf_max;          // products of a warp-tier row at most (BPW_F, or BPW_FS for very wide problems)
   int32_t *clist;      // CTA-tier rows
+  int32_t *fw;         // products per row (phase 1), read by the later phases
   int32_t *cbig;       // per CTA-tier row: its bucket record, or -1
   int32_t *buckets;    // BP_NBUCK counts per CTA row with more than BPC_CAP outputs
   int nbig_cap;        // records available
@@ -131,6 +144,7 @@ __global__ void __launch_bounds__(BP_NT, 2) k_batch_persist(BpArgs a) {
   long long *dbg = a.A.dbg;
   const int64_t n = a.B.n;
 
+  bp_stamp(ctr, 0);
   // ---- 1. products per row, tiers
   for (int64_t r0 = (int64_t)blockIdx.x * BP_NT; r0 < a.m; r0 += (int64_t)gridDim.x * BP_NT) {
     const int64_t r = r0 + tid;
@@ -142,6 +156,7 @@ __global__ void __launch_bounds__(BP_NT, 2) k_batch_persist(BpArgs a) {
         if (HS_G(dbg, k >= 0 && k < B.rows, 51, k)) fr += __ldg(B.p + k + 1) - __ldg(B.p + k);
       }
       a.Cp[r + 1] = 0;
+      a.fw[r] = (int32_t)(fr < 0x7fffffff ? fr : 0x7fffffff);
       if (fr > BP_FMAX) atomicOr(&ctr->err, 1);
     }
     bp_append(r < a.m && fr > 0 && fr <= a.wf_max, (int)r, &ctr->nwarp, a.wlist);
@@ -149,6 +164,7 @@ __global__ void __launch_bounds__(BP_NT, 2) k_batch_persist(BpArgs a) {
   }
   if (blockIdx.x == 0 && tid == 0) a.Cp[0] = 0;
   bp_grid_sync(ctr, a.spin_limit);
+  bp_stamp(ctr, 1);
   const int nw_rows = *(volatile int *)&ctr->nwarp, nc_rows = *(volatile int *)&ctr->ncta;
 
   // ---- 2. distinct columns per row
@@ -199,17 +215,19 @@ __global__ void __launch_bounds__(BP_NT, 2) k_batch_persist(BpArgs a) {
       i = __shfl_sync(FULL, i, 0);
       if (i >= nw_rows) break;
       const int r = a.wlist[i];
-      for (int s = lane; s < BPW_SYM; s += 32) wkeys[s] = EMPTY;
+      const int slots = max(64, min(BPW_SYM, next_pow2(2 * a.fw[r])));  // load at most one half
+      for (int s = lane; s < slots; s += 32) wkeys[s] = EMPTY;
       __syncwarp();
       int cnt = 0;
       warp_products<Struct>(A, B, A.p[r], A.p[r + 1],
-                            [&](int col, NoVal, int) { cnt += hash_insert_key(wkeys, BPW_SYM - 1, col); });
+                            [&](int col, NoVal, int) { cnt += hash_insert_key(wkeys, slots - 1, col); });
       cnt = warp_sum(cnt);
       if (lane == 0) a.Cp[r + 1] = cnt;
       __syncwarp();
     }
   }
   bp_grid_sync(ctr, a.spin_limit);
+  bp_stamp(ctr, 2);
 
   // ---- 3. row offsets: block b of rows is scanned by CTA b, after the totals of the blocks before it
   {
@@ -257,6 +275,7 @@ __global__ void __launch_bounds__(BP_NT, 2) k_batch_persist(BpArgs a) {
     }
   }
   bp_grid_sync(ctr, a.spin_limit);
+  bp_stamp(ctr, 3);
 
   // ---- 4. values, in ascending column order at the row offsets
   T *Cv = reinterpret_cast<T *>(a.Cv);
@@ -323,13 +342,7 @@ __global__ void __launch_bounds__(BP_NT, 2) k_batch_persist(BpArgs a) {
       const int r = a.wlist[i];
       const int64_t cb = a.Cp[r];
       const int c = (int)(a.Cp[r + 1] - cb);
-      int64_t fr = 0;  // the row's products, again (its A entries' B row lengths)
-      for (int64_t q = A.p[r] + lane; q < A.p[r + 1]; q += 32) {
-        if (!HS_G(dbg, q >= 0 && q < A.nnz, 50, q)) break;
-        const int k = __ldg(A.j + q);
-        if (HS_G(dbg, k >= 0 && k < B.rows, 51, k)) fr += __ldg(B.p + k + 1) - __ldg(B.p + k);
-      }
-      fr = warp_sum(fr);
+      const int fr = a.fw[r];
       if (HS_G(dbg, cb + c <= a.cap, 81, cb + c)) {
         T *out_v = SR::has_val ? Cv + cb : nullptr;
         if (fr <= BPW_FS)
@@ -345,6 +358,8 @@ __global__ void __launch_bounds__(BP_NT, 2) k_batch_persist(BpArgs a) {
       __syncwarp();
     }
   }
+  __syncthreads();
+  if (threadIdx.x == 0) atomicMax(&ctr->tns[5], bp_now());
 }
 
 template <class SR> size_t bp_smem() {
@@ -544,6 +559,7 @@ extern "C" int hs_batch_plan_create(int semiring, int64_t count, const hs_mat *A
   a.wf_max = nmax >= SORT_PACKED_COLS ? BPW_FS : BPW_F;
   a.wlist = (int32_t *)bp_alloc(P, 4 * (size_t)(m > 0 ? m : 1), st);
   a.clist = (int32_t *)bp_alloc(P, 4 * (size_t)(m > 0 ? m : 1), st);
+  a.fw = (int32_t *)bp_alloc(P, 4 * (size_t)(m > 0 ? m : 1), st);
   a.cbig = (int32_t *)bp_alloc(P, 4 * (size_t)(m > 0 ? m : 1), st);
   a.buckets = (int32_t *)bp_alloc(P, 4 * (size_t)nbig_cap * BP_NBUCK, st);
   a.nbig_cap = nbig_cap;
@@ -554,7 +570,7 @@ extern "C" int hs_batch_plan_create(int semiring, int64_t count, const hs_mat *A
   a.blk = (int64_t *)bp_alloc(P, 8 * (size_t)P->grid, st);
   a.ctr = (BpCounters *)bp_alloc(P, sizeof(BpCounters), st);
   a.spin_limit = 1LL << 24;  // polls of a barrier word (64 ns naps): about a second
-  if (!a.wlist || !a.clist || !a.cbig || !a.buckets || !a.Cp || !a.Cj || (P->vb && !a.Cv) || !a.blk || !a.ctr) {
+  if (!a.wlist || !a.clist || !a.fw || !a.cbig || !a.buckets || !a.Cp || !a.Cj || (P->vb && !a.Cv) || !a.blk || !a.ctr) {
     hs_batch_plan_destroy(P, stream);
     return HS_ENOMEM;
   }
@@ -573,6 +589,31 @@ extern "C" int hs_batch_plan_execute(hs_batch_plan *P, void *stream) {
   const int e = bp_dispatch(P->kind, &P->args, P->grid, st, true);
   if (e != HS_OK) cudaGetLastError();
   return e;
+}
+
+extern "C" int hs_batch_plan_phase_ms(hs_batch_plan *P, double *ms, void *stream) {
+  if (!P || !ms) return HS_EINVAL;
+  unsigned long long *h = nullptr;
+  if (cudaMallocHost(&h, sizeof(unsigned long long) * 6) != cudaSuccess) {
+    cudaGetLastError();
+    return HS_ENOMEM;
+  }
+  cudaMemcpyAsync(h, P->args.ctr->tns, sizeof(unsigned long long) * 6, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  const cudaError_t ce = cudaStreamSynchronize((cudaStream_t)stream);
+  if (ce == cudaSuccess) {
+    auto span = [&](int a, int b) { return h[b] >= h[a] ? (double)(h[b] - h[a]) * 1e-6 : 0.0; };
+    ms[0] = span(0, 1);  // products per row, tiers
+    ms[1] = span(1, 2);  // distinct columns per row
+    ms[2] = span(2, 3);  // row offsets
+    ms[3] = span(3, 5);  // values
+    ms[4] = span(0, 5);  // the whole execution
+  }
+  cudaFreeHost(h);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    return HS_ECUDA;
+  }
+  return HS_OK;
 }
 
 extern "C" int hs_batch_plan_result(hs_batch_plan *P, hs_mat *C, int64_t *row_offsets, void *stream) {

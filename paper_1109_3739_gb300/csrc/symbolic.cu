@@ -73,16 +73,20 @@ __global__ void __launch_bounds__(TINY_WPB * 32, 4) k_sym_tiny(SymArgs a) {
 }
 
 // --------------------------------------------------------------- warp
-constexpr int WARP_WPB = 8, WARP_SLOTS = 1024;
+// one warp per row, a private table of 2f slots (at most SLOTS): rows of at
+// most 512 products (1024 slots) and, in their own launch, of 513..1024
+// products (2048 slots)
+constexpr int WARP_WPB = 8;
+template <int SLOTS>
 __global__ void __launch_bounds__(WARP_WPB * 32, 4) k_sym_warp(SymArgs a) {
-  __shared__ int tables[WARP_WPB][WARP_SLOTS];
+  extern __shared__ __align__(16) int tables[];
   const int w = threadIdx.x >> 5, lane = lane_id();
-  int *keys = tables[w];
+  int *keys = tables + w * SLOTS;
   const DevCsr A = dev_a(a.A), B = dev_b(a.B);
   for (int idx = blockIdx.x * WARP_WPB + w; idx < a.count; idx += gridDim.x * WARP_WPB) {
     const int r = a.list[idx];
     if (!HS_G(a.A.dbg, r >= 0 && r < a.A.nslots, 35, r)) continue;
-    const int slots = max(64, min(WARP_SLOTS, next_pow2(2 * (int)a.f[r])));
+    const int slots = max(64, min(SLOTS, next_pow2(2 * (int)a.f[r])));
     for (int s = lane; s < slots; s += 32) keys[s] = EMPTY;
     __syncwarp();
     int cnt = 0;
@@ -311,11 +315,15 @@ template <class K> static int fit_per_sm(K kernel, int threads, size_t smem) {
   return n < 1 ? 1 : n;
 }
 
-void launch_sym_warp(const SymArgs &a, cudaStream_t st) {
+template <int SLOTS> static void launch_sym_warp_slots(const SymArgs &a, cudaStream_t st) {
   if (a.count <= 0) return;
+  const size_t bytes = sizeof(int) * WARP_WPB * SLOTS;
+  set_smem_attr(k_sym_warp<SLOTS>, bytes);
   count_launch();
-  k_sym_warp<<<grid_cap(a.count, WARP_WPB, fit_per_sm(k_sym_warp, WARP_WPB * 32, 0)), WARP_WPB * 32, 0, st>>>(a);
+  k_sym_warp<SLOTS><<<grid_cap(a.count, WARP_WPB, fit_per_sm(k_sym_warp<SLOTS>, WARP_WPB * 32, bytes)),
+                      WARP_WPB * 32, bytes, st>>>(a);
 }
+void launch_sym_warp(const SymArgs &a, cudaStream_t st) { launch_sym_warp_slots<2 * F_WARP>(a, st); }
 
 template <int SLOTS, int NT> static void launch_sym_cta(const SymArgs &a, cudaStream_t st) {
   if (a.count <= 0) return;
@@ -325,7 +333,7 @@ template <int SLOTS, int NT> static void launch_sym_cta(const SymArgs &a, cudaSt
   k_sym_cta<SLOTS, NT><<<grid_cap(a.count, 1, fit_per_sm(k_sym_cta<SLOTS, NT>, NT, bytes)), NT, bytes, st>>>(a);
 }
 // table capacity 2f: mid rows have f <= 4096, large rows f <= min(16384, cap_large) = 8192 at most
-void launch_sym_mid_s(const SymArgs &a, cudaStream_t st) { launch_sym_cta<2 * F_MID_S, 256>(a, st); }
+void launch_sym_mid_s(const SymArgs &a, cudaStream_t st) { launch_sym_warp_slots<2 * F_MID_S>(a, st); }
 void launch_sym_mid(const SymArgs &a, cudaStream_t st) { launch_sym_cta<2 * F_MID, 256>(a, st); }
 void launch_sym_large(const SymArgs &a, cudaStream_t st) { launch_sym_cta<16384, 512>(a, st); }
 

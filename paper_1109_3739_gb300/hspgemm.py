@@ -116,6 +116,8 @@ def _lib():
             L.hs_batch_plan_result.restype = ci
             L.hs_batch_plan_destroy.argtypes = [vp, vp]
             L.hs_batch_plan_destroy.restype = None
+            L.hs_batch_plan_phase_ms.argtypes = [vp, P(ctypes.c_double), vp]
+            L.hs_batch_plan_phase_ms.restype = ci
             L.hs_set_tuning.argtypes = [P(hs_tuning)]
             L.hs_set_tuning.restype = ci
             L.hs_get_tuning.argtypes = [P(hs_tuning)]
@@ -339,6 +341,14 @@ class BatchPlan:
         dt = DTYPE_NAME[c.dtype]
         val = live[int(c.val)].view(tdt[dt])[:nnz] if c.val else None
         return DeviceCSR(c.m, c.n, rowptr, col, val, dt), np.array(offs[:], dtype=np.int64)
+
+    def phase_ms(self, stream=None) -> dict:
+        """The last execution's phase times (hs_batch_plan_phase_ms), in ms."""
+        ms = (ctypes.c_double * 5)()
+        st = _lib().hs_batch_plan_phase_ms(self._h, ms, _stream_ptr(stream))
+        if st != 0:
+            raise HsError(st, "hs_batch_plan_phase_ms")
+        return dict(zip(("products", "symbolic", "offsets", "values", "kernel"), ms[:]))
 
     def close(self, stream=None):
         if self._h is not None:

@@ -142,6 +142,9 @@ def test_persistent_plan_graph_replay_mixed_rows():
             g.replay()
             torch.cuda.synchronize()
             C, offs = plan.result()
+            ph = plan.phase_ms()
+            assert ph["kernel"] > 0 and all(v >= 0 for v in ph.values())
+            assert sum(ph[k] for k in ("products", "symbolic", "offsets", "values")) <= ph["kernel"] * 1.001
             for i, (A, B) in enumerate(probs):
                 check_problem("plus_times", C, offs, i, A, B)
             host = (C.rowptr.cpu().clone(), C.col.cpu().clone(), C.val.cpu().clone())
