@@ -41,12 +41,13 @@ constexpr int BPC_SLOTS = 4096, BPC_CAP = 2048;  // CTA tier values: at most 204
 constexpr int BP_FMAX = 4096;                    // rows with more products are not taken
 constexpr int BP_NBUCK = 16;                     // column buckets of a row with more than BPC_CAP outputs
 constexpr int BP_CH = 256;                       // A entries staged per round (CTA tier)
+constexpr int BP_CLAIM = 4;                      // warp rows a warp claims per atomic
 
 // counters, zeroed before every execution
 struct BpCounters {
   unsigned bar[2];  // grid barrier: arrivals, generation
-  int nwarp, ncta;  // rows of each tier
-  int sym_w, sym_c, num_w, num_c;  // work handed out per phase and tier
+  int nwarp[3], ncta;  // rows of each tier (warp rows by the keys they sort: 256, 512, 1024)
+  int sym_w, sym_c, num_w[3], num_c;  // work handed out per phase and tier
   int nbig;                         // CTA rows that need column ranges
   int err;   // bit 0: a row outside the tiers; 1: a barrier wait expired; 2: a column range too full
   int kerr;  // consistency codes of the row routines (hash table full, count mismatch)
@@ -69,7 +70,7 @@ struct BpArgs {
   RowSet A;
   RightOp B;
   int64_t m;           // stacked rows
-  int32_t *wlist;      // warp-tier rows
+  int32_t *wlist[3];   // warp-tier rows of at most 256, 512 and wf_max products
   int wf_max;          // products of a warp-tier row at most (BPW_F, or BPW_FS for very wide problems)
   int32_t *clist;      // CTA-tier rows
   int32_t *fw;         // products per row (phase 1), read by the later phases
@@ -159,13 +160,16 @@ __global__ void __launch_bounds__(BP_NT, 2) k_batch_persist(BpArgs a) {
       a.fw[r] = (int32_t)(fr < 0x7fffffff ? fr : 0x7fffffff);
       if (fr > BP_FMAX) atomicOr(&ctr->err, 1);
     }
-    bp_append(r < a.m && fr > 0 && fr <= a.wf_max, (int)r, &ctr->nwarp, a.wlist);
+    bp_append(r < a.m && fr > 0 && fr <= BPW_FS, (int)r, &ctr->nwarp[0], a.wlist[0]);
+    bp_append(r < a.m && fr > BPW_FS && fr <= 2 * BPW_FS && fr <= a.wf_max, (int)r, &ctr->nwarp[1], a.wlist[1]);
+    bp_append(r < a.m && fr > 2 * BPW_FS && fr <= a.wf_max, (int)r, &ctr->nwarp[2], a.wlist[2]);
     bp_append(r < a.m && fr > a.wf_max && fr <= BP_FMAX, (int)r, &ctr->ncta, a.clist);
   }
   if (blockIdx.x == 0 && tid == 0) a.Cp[0] = 0;
   bp_grid_sync(ctr, a.spin_limit);
   bp_stamp(ctr, 1);
-  const int nw_rows = *(volatile int *)&ctr->nwarp, nc_rows = *(volatile int *)&ctr->ncta;
+  const int nw0 = *(volatile int *)&ctr->nwarp[0], nw1 = *(volatile int *)&ctr->nwarp[1];
+  const int nw_rows = nw0 + nw1 + *(volatile int *)&ctr->nwarp[2], nc_rows = *(volatile int *)&ctr->ncta;
 
   // ---- 2. distinct columns per row
   {
@@ -177,13 +181,14 @@ __global__ void __launch_bounds__(BP_NT, 2) k_batch_persist(BpArgs a) {
       const int i = s_item;
       if (i >= nc_rows) break;
       const int r = a.clist[i];
-      for (int s = tid; s < BPC_SYM; s += BP_NT) ckeys[s] = EMPTY;
+      const int cslots = max(64, min(BPC_SYM, next_pow2(2 * a.fw[r])));  // load at most one half
+      for (int s = tid; s < cslots; s += BP_NT) ckeys[s] = EMPTY;
       if (tid < BP_NBUCK) s_cnt_b[tid] = 0;
       if (tid == 0) s_count = 0;
       __syncthreads();
       int cnt = 0;
       cta_products<Struct, BP_CH>(A, B, A.p[r], A.p[r + 1], false, 0, 0, cex, s_wtmp, [&](int col, NoVal, int) {
-        if (hash_insert_key(ckeys, BPC_SYM - 1, col)) {
+        if (hash_insert_key(ckeys, cslots - 1, col)) {
           ++cnt;
           const int bkt = (int)(((int64_t)col * BP_NBUCK) / n);
           if (HS_G(dbg, bkt >= 0 && bkt < BP_NBUCK, 82, col)) atomicAdd(&s_cnt_b[bkt], 1);
@@ -209,12 +214,15 @@ __global__ void __launch_bounds__(BP_NT, 2) k_batch_persist(BpArgs a) {
       __syncthreads();
     }
     int *wkeys = reinterpret_cast<int *>(smem_raw + (size_t)warp * bp_warp_bytes<T>());  // a warp's set
-    while (true) {
-      int i = 0;
-      if (lane == 0) i = atomicAdd(&ctr->sym_w, 1);
-      i = __shfl_sync(FULL, i, 0);
-      if (i >= nw_rows) break;
-      const int r = a.wlist[i];
+    for (int i = 0, iend = 0;; ++i) {
+      if (i >= iend) {
+        int i0 = 0;
+        if (lane == 0) i0 = atomicAdd(&ctr->sym_w, BP_CLAIM);
+        i = __shfl_sync(FULL, i0, 0);
+        iend = min(i + BP_CLAIM, nw_rows);
+        if (i >= iend) break;
+      }
+      const int r = i < nw0 ? a.wlist[0][i] : (i < nw0 + nw1 ? a.wlist[1][i - nw0] : a.wlist[2][i - nw0 - nw1]);
       const int slots = max(64, min(BPW_SYM, next_pow2(2 * a.fw[r])));  // load at most one half
       for (int s = lane; s < slots; s += 32) wkeys[s] = EMPTY;
       __syncwarp();
@@ -334,26 +342,36 @@ __global__ void __launch_bounds__(BP_NT, 2) k_batch_persist(BpArgs a) {
     unsigned char *wb = smem_raw + (size_t)warp * bp_warp_bytes<T>();
     int *s_col = reinterpret_cast<int *>(wb);
     T *s_val = reinterpret_cast<T *>(wb + LW::col_bytes);
-    while (true) {
-      int i = 0;
-      if (lane == 0) i = atomicAdd(&ctr->num_w, 1);
-      i = __shfl_sync(FULL, i, 0);
-      if (i >= nw_rows) break;
-      const int r = a.wlist[i];
+    // rows of 1024, then 512, then 256 keys: the warps of an SM mostly run the
+    // same width at a time, and the expansion has one call site for all three
+    int g = 2, i = 0, iend = 0;  // rows [i, iend) of group g claimed by this warp
+    while (g >= 0) {
+      if (i >= iend) {
+        int i0 = 0;
+        if (lane == 0) i0 = atomicAdd(&ctr->num_w[g], BP_CLAIM);
+        i = __shfl_sync(FULL, i0, 0);
+        iend = min(i + BP_CLAIM, *(volatile int *)&ctr->nwarp[g]);
+        if (i >= iend) {
+          --g;
+          continue;
+        }
+      }
+      const int r = a.wlist[g][i++];
       const int64_t cb = a.Cp[r];
       const int c = (int)(a.Cp[r + 1] - cb);
       const int fr = a.fw[r];
-      if (HS_G(dbg, cb + c <= a.cap, 81, cb + c)) {
+      int kmn = 0, kmx = 0;
+      const int got = sort_expand<SR>(A, B, A.p[r], A.p[r + 1], BPW_F, s_col, s_val, &kmn, &kmx);
+      if (got != fr || fr > (BPW_FS << g)) {
+        if (lane == 0) atomicExch(&ctr->kerr, 12);
+      } else if (HS_G(dbg, cb + c <= a.cap, 81, cb + c)) {
         T *out_v = SR::has_val ? Cv + cb : nullptr;
-        if (fr <= BPW_FS)
-          sort_row<SR, BPW_FS / 32, true>(A, B, A.p[r], A.p[r + 1], (int)fr, c, s_col, s_val, a.Cj + cb, out_v,
-                                          &ctr->kerr);
-        else if (fr <= 2 * BPW_FS)
-          sort_row<SR, 2 * BPW_FS / 32, false>(A, B, A.p[r], A.p[r + 1], (int)fr, c, s_col, s_val, a.Cj + cb,
-                                               out_v, &ctr->kerr);
+        if (g == 0)
+          sort_finish<SR, BPW_FS / 32, true>(fr, c, kmn, kmx, s_col, s_val, a.Cj + cb, out_v, &ctr->kerr, dbg);
+        else if (g == 1)
+          sort_finish<SR, 2 * BPW_FS / 32, false>(fr, c, kmn, kmx, s_col, s_val, a.Cj + cb, out_v, &ctr->kerr, dbg);
         else
-          sort_row<SR, BPW_F / 32, false>(A, B, A.p[r], A.p[r + 1], (int)fr, c, s_col, s_val, a.Cj + cb, out_v,
-                                          &ctr->kerr);
+          sort_finish<SR, BPW_F / 32, false>(fr, c, kmn, kmx, s_col, s_val, a.Cj + cb, out_v, &ctr->kerr, dbg);
       }
       __syncwarp();
     }
@@ -557,7 +575,9 @@ extern "C" int hs_batch_plan_create(int semiring, int64_t count, const hs_mat *A
   int64_t nmax = 0;
   for (int64_t i = 0; i < count; ++i) nmax = B[i].n > nmax ? B[i].n : nmax;
   a.wf_max = nmax >= SORT_PACKED_COLS ? BPW_FS : BPW_F;
-  a.wlist = (int32_t *)bp_alloc(P, 4 * (size_t)(m > 0 ? m : 1), st);
+  a.wlist[0] = (int32_t *)bp_alloc(P, 4 * 3 * (size_t)(m > 0 ? m : 1), st);
+  a.wlist[1] = a.wlist[0] ? a.wlist[0] + (m > 0 ? m : 1) : nullptr;
+  a.wlist[2] = a.wlist[0] ? a.wlist[1] + (m > 0 ? m : 1) : nullptr;
   a.clist = (int32_t *)bp_alloc(P, 4 * (size_t)(m > 0 ? m : 1), st);
   a.fw = (int32_t *)bp_alloc(P, 4 * (size_t)(m > 0 ? m : 1), st);
   a.cbig = (int32_t *)bp_alloc(P, 4 * (size_t)(m > 0 ? m : 1), st);
@@ -570,7 +590,7 @@ extern "C" int hs_batch_plan_create(int semiring, int64_t count, const hs_mat *A
   a.blk = (int64_t *)bp_alloc(P, 8 * (size_t)P->grid, st);
   a.ctr = (BpCounters *)bp_alloc(P, sizeof(BpCounters), st);
   a.spin_limit = 1LL << 24;  // polls of a barrier word (64 ns naps): about a second
-  if (!a.wlist || !a.clist || !a.fw || !a.cbig || !a.buckets || !a.Cp || !a.Cj || (P->vb && !a.Cv) || !a.blk || !a.ctr) {
+  if (!a.wlist[0] || !a.clist || !a.fw || !a.cbig || !a.buckets || !a.Cp || !a.Cj || (P->vb && !a.Cv) || !a.blk || !a.ctr) {
     hs_batch_plan_destroy(P, stream);
     return HS_ENOMEM;
   }

@@ -107,19 +107,16 @@ template <int K, typename KT> __device__ __forceinline__ void warp_bitonic(KT (&
   }
 }
 
-// Row r of C (A entries [q0, q1), F products, c outputs) by one warp, for
-// F <= 32*K.  s_col holds sr_pad_len(32*K) ints, s_val 32*K values.  Writes
-// c entries at out_j / out_v; a product count other than F or an output count
-// other than c sets *err (the structure disagrees with the symbolic pass).
-template <class SR, int K, bool WIDE>
-__device__ __forceinline__ void sort_row(const DevCsr &A, const DevCsr &B, int64_t q0, int64_t q1, int F, int c,
-                                         int *s_col, typename SR::val_t *s_val, int32_t *out_j,
-                                         typename SR::val_t *out_v, int *err) {
+// The products of A entries [q0, q1) by one warp, in product order, to
+// shared memory (columns at s_col[sr_pad(p)], values at s_val[p], at most
+// nmax of them); returns their number (warp-uniform) and the least and
+// greatest column in *kmn, *kmx.  Shared by every register width, so a kernel
+// that sorts rows of several widths holds one copy of the expansion.
+template <class SR>
+__device__ __forceinline__ int sort_expand(const DevCsr &A, const DevCsr &B, int64_t q0, int64_t q1, int nmax,
+                                           int *s_col, typename SR::val_t *s_val, int *kmn_out, int *kmx_out) {
   using T = typename SR::val_t;
-  constexpr int N = 32 * K;
-  constexpr int PB = ILog2<N>::v;
   const int lane = lane_id();
-  // 1. the products, in product order, to shared memory
   int base = 0, kmn = 0x7fffffff, kmx = -1;
   for (int64_t qb = q0; qb < q1; qb += 32) {
     const int64_t q = qb + lane;
@@ -131,7 +128,7 @@ __device__ __forceinline__ void sort_row(const DevCsr &A, const DevCsr &B, int64
     }
     auto put = [&](int col, T v, int p) {
       const int at = base + p;
-      if (HS_G(A.dbg, at >= 0 && at < N, 90, at)) {
+      if (HS_G(A.dbg, at >= 0 && at < nmax, 90, at)) {
         s_col[sr_pad(at)] = col;
         if constexpr (SR::has_val) s_val[at] = v;
       }
@@ -141,13 +138,23 @@ __device__ __forceinline__ void sort_row(const DevCsr &A, const DevCsr &B, int64
     base += warp_expand<SR>(B, s, (int)(e - s), av, put);
   }
   __syncwarp();
-  if (base != F || F < 0 || F > N) {
-    if (lane == 0) atomicExch(err, 12);
-    return;
-  }
-  if (F == 0) return;
-  kmn = warp_min(kmn);
-  kmx = warp_max(kmx);
+  *kmn_out = warp_min(kmn);
+  *kmx_out = warp_max(kmx);
+  return base;
+}
+
+// Sort and fold a row whose F products (F <= 32*K) sort_expand laid out,
+// writing its c outputs at out_j / out_v.  An output count other than c
+// sets *err (the structure disagrees with the symbolic pass).
+template <class SR, int K, bool WIDE>
+__device__ __forceinline__ void sort_finish(int F, int c, int kmn, int kmx, int *s_col,
+                                            const typename SR::val_t *s_val, int32_t *out_j,
+                                            typename SR::val_t *out_v, int *err, long long *dbg) {
+  using T = typename SR::val_t;
+  constexpr int N = 32 * K;
+  constexpr int PB = ILog2<N>::v;
+  const int lane = lane_id();
+  if (F <= 0) return;
   const unsigned span = (unsigned)kmx - (unsigned)kmn;
   if (span < (1u << (32 - PB)) - 1u) {
     // 2. packed keys, sorted
@@ -194,7 +201,7 @@ __device__ __forceinline__ void sort_row(const DevCsr &A, const DevCsr &B, int64
         if (!fl && valid) v = SR::add(carry, v);  // continues the previous round's last run
         carry = shfl_val<T>(v, 31);
       }
-      if (tail && HS_G(A.dbg, pos >= 0 && pos < c, 91, pos)) {
+      if (tail && HS_G(dbg, pos >= 0 && pos < c, 91, pos)) {
         __stcs(out_j + pos, (int)(kk >> PB) + kmn);
         if constexpr (SR::has_val) __stcs(out_v + pos, v);
       }
@@ -240,7 +247,7 @@ __device__ __forceinline__ void sort_row(const DevCsr &A, const DevCsr &B, int64
     T v{};
     if constexpr (SR::has_val) v = s_val[(unsigned)(key[i] & 0xffffffffull)];
     if (head) {
-      if (seen && HS_G(A.dbg, outi >= 0 && outi < c, 92, outi)) {  // the previous run of this lane is complete
+      if (seen && HS_G(dbg, outi >= 0 && outi < c, 92, outi)) {  // the previous run of this lane is complete
         __stcs(out_j + outi, curcol);
         if constexpr (SR::has_val) __stcs(out_v + outi, acc);
       }
@@ -265,11 +272,27 @@ __device__ __forceinline__ void sort_row(const DevCsr &A, const DevCsr &B, int64
       if (hd) open = false;
     }
   }
-  if (seen && HS_G(A.dbg, outi >= 0 && outi < c, 93, outi)) {
+  if (seen && HS_G(dbg, outi >= 0 && outi < c, 93, outi)) {
     __stcs(out_j + outi, curcol);
     if constexpr (SR::has_val) __stcs(out_v + outi, acc);
   }
   if (total != c && lane == 0) atomicExch(err, 13);
+}
+
+// Row r of C (A entries [q0, q1), F products, c outputs) by one warp, for
+// F <= 32*K.  s_col holds sr_pad_len(32*K) ints, s_val 32*K values.  A
+// product count other than F sets *err.
+template <class SR, int K, bool WIDE>
+__device__ __forceinline__ void sort_row(const DevCsr &A, const DevCsr &B, int64_t q0, int64_t q1, int F, int c,
+                                         int *s_col, typename SR::val_t *s_val, int32_t *out_j,
+                                         typename SR::val_t *out_v, int *err) {
+  int kmn = 0, kmx = 0;
+  const int got = sort_expand<SR>(A, B, q0, q1, 32 * K, s_col, s_val, &kmn, &kmx);
+  if (got != F || F < 0 || F > 32 * K) {
+    if (lane_id() == 0) atomicExch(err, 12);
+    return;
+  }
+  sort_finish<SR, K, WIDE>(F, c, kmn, kmx, s_col, s_val, out_j, out_v, err, A.dbg);
 }
 
 }  // namespace hs

@@ -48,3 +48,44 @@ def test_tuning_keeps_the_defaults_when_nothing_is_faster(monkeypatch):
         assert best == defaults and h.get_tuning() == defaults
     finally:
         h.set_tuning(None)
+
+
+def test_work_shape_and_key():
+    from paper_1109_3739_gb300 import tune
+    f = [0, 10, 100, 100, 300, 5000, 20000]
+    shape = tune.work_shape(f, nnz_c=20000)
+    assert len(shape["bands"]) == len(tune.FLOP_BANDS)
+    assert shape["bands"][0] == 0 and shape["bands"][1] == 0   # 10 of 25510 products: 0 %
+    assert shape["bands"][-1] == 80                             # 20000 / 25510 = 78 % -> 80
+    assert shape["c_per_flop"] == 0.8
+    assert sum(shape["bands"]) in range(95, 106)
+    k1 = tune.cache_key("GB300", "plus_times", "f32", shape)
+    k2 = tune.cache_key("GB300", "plus_times", "f64", shape)
+    assert k1 != k2 and k1 == tune.cache_key("GB300", "plus_times", "f32", dict(shape))
+
+
+def test_tune_cached_times_once_per_key(monkeypatch, tmp_path):
+    from paper_1109_3739_gb300 import hspgemm as h
+    from paper_1109_3739_gb300 import tune
+    calls = []
+
+    def fake_time(run, trials, stream=None):
+        calls.append(1)
+        t = h.get_tuning()
+        return 1.0 + abs(t["sort_pct"] - 75) / 100.0
+
+    monkeypatch.setattr(tune, "time_ms", fake_time)
+    path = str(tmp_path / "tuning.json")
+    try:
+        best, log, hit = tune.tune_cached(lambda: None, "key-a", trials=1, path=path)
+        assert not hit and best["sort_pct"] == 75 and len(log) == len(calls) > 1
+        n = len(calls)
+        h.set_tuning(None)
+        best2, log2, hit2 = tune.tune_cached(lambda: None, "key-a", trials=1, path=path)
+        assert hit2 and log2 == [] and len(calls) == n and best2 == best and h.get_tuning() == best
+        _, _, hit3 = tune.tune_cached(lambda: None, "key-b", trials=1, path=path)
+        assert not hit3 and len(calls) > n
+        import json
+        assert set(json.load(open(path))) == {"key-a", "key-b"}
+    finally:
+        h.set_tuning(None)
