@@ -37,9 +37,10 @@ constexpr int BP_NT = 256, BP_NW = BP_NT / 32;
 constexpr int BPW_SYM = 2048;                    // warp tier symbolic set: f <= 1024
 constexpr int BPW_FS = 256, BPW_F = 1024;        // warp tier values: 32*8 or 32*32 sorted products
 constexpr int BPC_SYM = 8192;                    // CTA tier symbolic set: f <= 4096
-constexpr int BPC_SLOTS = 4096, BPC_CAP = 2048;  // CTA tier values: at most 2048 per column range
+constexpr int BPC_SLOTS = 2048, BPC_CAP = 1024;  // CTA tier values: at most 1024 per column range
 constexpr int BP_FMAX = 4096;                    // rows with more products are not taken
 constexpr int BP_NBUCK = 16;                     // column buckets of a row with more than BPC_CAP outputs
+constexpr int BP_REC = BP_NBUCK + 2;             // a bucket record: the counts, then the row's least and greatest column
 constexpr int BP_CH = 256;                       // A entries staged per round (CTA tier)
 constexpr int BP_CLAIM = 4;                      // warp rows a warp claims per atomic
 
@@ -75,7 +76,8 @@ struct BpArgs {
   int32_t *clist;      // CTA-tier rows
   int32_t *fw;         // products per row (phase 1), read by the later phases
   int32_t *cbig;       // per CTA-tier row: its bucket record, or -1
-  int32_t *buckets;    // BP_NBUCK counts per CTA row with more than BPC_CAP outputs
+  int32_t *buckets;    // BP_REC ints per CTA row with more than BPC_CAP outputs
+  void *wscratch;      // per warp: the values of its row's products (BPW_F of them), in global memory
   int nbig_cap;        // records available
   int64_t *Cp;         // m + 1 row offsets (counts first)
   int32_t *Cj;
@@ -86,10 +88,12 @@ struct BpArgs {
   long long spin_limit;
 };
 
-// bytes of a warp's shared region: its symbolic set, then its sorted products
+// bytes of a warp's shared region: its symbolic set, or its sort keys (the
+// products' values wait in global scratch, which keeps the region small and
+// three CTAs on an SM)
 template <typename T> __host__ __device__ constexpr size_t bp_warp_bytes() {
-  return SortSmemLayout<T, BPW_F / 32>::per_warp > (size_t)BPW_SYM * 4 ? SortSmemLayout<T, BPW_F / 32>::per_warp
-                                                                       : (size_t)BPW_SYM * 4;
+  return SortSmemLayout<T, BPW_F / 32>::col_bytes > (size_t)BPW_SYM * 4 ? SortSmemLayout<T, BPW_F / 32>::col_bytes
+                                                                        : (size_t)BPW_SYM * 4;
 }
 
 // Grid-wide barrier for co-resident CTAs (cooperative launch): the last CTA to
@@ -132,13 +136,12 @@ __device__ __forceinline__ void bp_append(bool want, int r, int *count, int32_t 
 }
 
 template <class SR>
-__global__ void __launch_bounds__(BP_NT, 2) k_batch_persist(BpArgs a) {
+__global__ void __launch_bounds__(BP_NT, 3) k_batch_persist(BpArgs a) {
   using T = typename SR::val_t;
   using Struct = Semiring<OR_AND, NoVal>;
-  using LW = SortSmemLayout<T, BPW_F / 32>;
   using LC = CtaNumLayout<T, BPC_SLOTS, BPC_CAP>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_item, s_count, s_cnt_b[BP_NBUCK], s_wtmp[33];
+  __shared__ int s_item, s_count, s_cnt_b[BP_NBUCK], s_wtmp[33], s_kmin, s_kmax;
   const DevCsr A = ndev_a(a.A), B = ndev_b(a.B);
   const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
   BpCounters *ctr = a.ctr;
@@ -184,13 +187,38 @@ __global__ void __launch_bounds__(BP_NT, 2) k_batch_persist(BpArgs a) {
       const int cslots = max(64, min(BPC_SYM, next_pow2(2 * a.fw[r])));  // load at most one half
       for (int s = tid; s < cslots; s += BP_NT) ckeys[s] = EMPTY;
       if (tid < BP_NBUCK) s_cnt_b[tid] = 0;
-      if (tid == 0) s_count = 0;
+      if (tid == 0) {
+        s_count = 0;
+        s_kmin = 0x7fffffff;
+        s_kmax = -1;
+      }
       __syncthreads();
+      {  // the row's column range: first and last column of each of its B rows
+        int lmin = 0x7fffffff, lmax = -1;
+        for (int64_t q = A.p[r] + tid; q < A.p[r + 1]; q += BP_NT) {
+          const int k = __ldg(A.j + q);
+          if (!HS_G(dbg, k >= 0 && k < B.rows, 51, k)) continue;
+          const int64_t b0 = __ldg(B.p + k), b1 = __ldg(B.p + k + 1);
+          if (b0 < b1) {
+            lmin = min(lmin, __ldg(B.j + b0));
+            lmax = max(lmax, __ldg(B.j + b1 - 1));
+          }
+        }
+        lmin = warp_min(lmin);
+        lmax = warp_max(lmax);
+        if (lane == 0) {
+          atomicMin(&s_kmin, lmin);
+          atomicMax(&s_kmax, lmax);
+        }
+      }
+      __syncthreads();
+      const int kmin = s_kmin;
+      const int64_t span = (int64_t)s_kmax - kmin + 1;
       int cnt = 0;
       cta_products<Struct, BP_CH>(A, B, A.p[r], A.p[r + 1], false, 0, 0, cex, s_wtmp, [&](int col, NoVal, int) {
         if (hash_insert_key(ckeys, cslots - 1, col)) {
           ++cnt;
-          const int bkt = (int)(((int64_t)col * BP_NBUCK) / n);
+          const int bkt = (int)(((int64_t)(col - kmin) * BP_NBUCK) / span);
           if (HS_G(dbg, bkt >= 0 && bkt < BP_NBUCK, 82, col)) atomicAdd(&s_cnt_b[bkt], 1);
         }
       });
@@ -203,7 +231,10 @@ __global__ void __launch_bounds__(BP_NT, 2) k_batch_persist(BpArgs a) {
         if (s_count > BPC_CAP) {  // its values need column ranges: keep its buckets
           rec = atomicAdd(&ctr->nbig, 1);
           if (rec < a.nbig_cap) {
-            for (int b = 0; b < BP_NBUCK; ++b) a.buckets[(int64_t)rec * BP_NBUCK + b] = s_cnt_b[b];
+            int32_t *rb = a.buckets + (int64_t)rec * BP_REC;
+            for (int b = 0; b < BP_NBUCK; ++b) rb[b] = s_cnt_b[b];
+            rb[BP_NBUCK] = s_kmin;
+            rb[BP_NBUCK + 1] = s_kmax;
           } else {
             atomicOr(&ctr->err, 4);
             rec = -1;
@@ -307,8 +338,10 @@ __global__ void __launch_bounds__(BP_NT, 2) k_batch_persist(BpArgs a) {
       int done = 0, bk = 0;
       while (done < c) {
         int lo = 0, hi = (int)n, part = c;
-        if (rec >= 0) {
-          const int32_t *bc = a.buckets + (int64_t)rec * BP_NBUCK;
+        if (rec >= 0) {  // bucket b holds columns kmin + [ceil(b*span/16), ceil((b+1)*span/16))
+          const int32_t *bc = a.buckets + (int64_t)rec * BP_REC;
+          const int rkmin = bc[BP_NBUCK];
+          const int64_t rspan = (int64_t)bc[BP_NBUCK + 1] - rkmin + 1;
           const int b0 = bk;
           part = 0;
           while (bk < BP_NBUCK && part + bc[bk] <= BPC_CAP) part += bc[bk++];
@@ -316,8 +349,8 @@ __global__ void __launch_bounds__(BP_NT, 2) k_batch_persist(BpArgs a) {
             if (tid == 0) atomicOr(&ctr->err, 4);
             break;
           }
-          lo = (int)(((int64_t)b0 * n + BP_NBUCK - 1) / BP_NBUCK);
-          hi = bk == BP_NBUCK ? (int)n : (int)(((int64_t)bk * n + BP_NBUCK - 1) / BP_NBUCK);
+          lo = rkmin + (int)(((int64_t)b0 * rspan + BP_NBUCK - 1) / BP_NBUCK);
+          hi = rkmin + (int)(((int64_t)bk * rspan + BP_NBUCK - 1) / BP_NBUCK);
         } else if (!HS_G(dbg, c <= BPC_CAP, 80, c)) {
           break;
         }
@@ -341,7 +374,7 @@ __global__ void __launch_bounds__(BP_NT, 2) k_batch_persist(BpArgs a) {
     }
     unsigned char *wb = smem_raw + (size_t)warp * bp_warp_bytes<T>();
     int *s_col = reinterpret_cast<int *>(wb);
-    T *s_val = reinterpret_cast<T *>(wb + LW::col_bytes);
+    T *s_val = reinterpret_cast<T *>(a.wscratch) + ((size_t)blockIdx.x * BP_NW + warp) * BPW_F;
     // rows of 1024, then 512, then 256 keys: the warps of an SM mostly run the
     // same width at a time, and the expansion has one call site for all three
     int g = 2, i = 0, iend = 0;  // rows [i, iend) of group g claimed by this warp
@@ -581,7 +614,8 @@ extern "C" int hs_batch_plan_create(int semiring, int64_t count, const hs_mat *A
   a.clist = (int32_t *)bp_alloc(P, 4 * (size_t)(m > 0 ? m : 1), st);
   a.fw = (int32_t *)bp_alloc(P, 4 * (size_t)(m > 0 ? m : 1), st);
   a.cbig = (int32_t *)bp_alloc(P, 4 * (size_t)(m > 0 ? m : 1), st);
-  a.buckets = (int32_t *)bp_alloc(P, 4 * (size_t)nbig_cap * BP_NBUCK, st);
+  a.buckets = (int32_t *)bp_alloc(P, 4 * (size_t)nbig_cap * BP_REC, st);
+  a.wscratch = P->vb ? bp_alloc(P, (size_t)P->grid * BP_NW * BPW_F * (size_t)P->vb, st) : nullptr;
   a.nbig_cap = nbig_cap;
   a.Cp = (int64_t *)bp_alloc(P, 8 * (size_t)(m + 1), st);
   a.Cj = (int32_t *)bp_alloc(P, 4 * (size_t)(P->cap > 0 ? P->cap : 1), st);
@@ -590,7 +624,7 @@ extern "C" int hs_batch_plan_create(int semiring, int64_t count, const hs_mat *A
   a.blk = (int64_t *)bp_alloc(P, 8 * (size_t)P->grid, st);
   a.ctr = (BpCounters *)bp_alloc(P, sizeof(BpCounters), st);
   a.spin_limit = 1LL << 24;  // polls of a barrier word (64 ns naps): about a second
-  if (!a.wlist[0] || !a.clist || !a.fw || !a.cbig || !a.buckets || !a.Cp || !a.Cj || (P->vb && !a.Cv) || !a.blk || !a.ctr) {
+  if (!a.wlist[0] || !a.clist || !a.fw || !a.cbig || !a.buckets || !a.Cp || !a.Cj || (P->vb && (!a.Cv || !a.wscratch)) || !a.blk || !a.ctr) {
     hs_batch_plan_destroy(P, stream);
     return HS_ENOMEM;
   }
