@@ -37,7 +37,7 @@ constexpr int BP_NT = 256, BP_NW = BP_NT / 32;
 constexpr int BPW_SYM = 2048;                    // warp tier symbolic set: f <= 1024
 constexpr int BPW_FS = 256, BPW_F = 1024;        // warp tier values: 32*8 or 32*32 sorted products
 constexpr int BPC_SYM = 8192;                    // CTA tier symbolic set: f <= 4096
-constexpr int BPC_SLOTS = 2048, BPC_CAP = 1024;  // CTA tier values: at most 1024 per column range
+constexpr int BPC_SLOTS = 4096, BPC_CAP = 1536;  // CTA tier values: at most 1536 per column range
 constexpr int BP_FMAX = 4096;                    // rows with more products are not taken
 constexpr int BP_NBUCK = 16;                     // column buckets of a row with more than BPC_CAP outputs
 constexpr int BP_REC = BP_NBUCK + 2;             // a bucket record: the counts, then the row's least and greatest column
@@ -466,7 +466,7 @@ static int bp_dispatch(int kind, BpArgs *a, int grid, cudaStream_t st, bool laun
 
 // products per row of the stacked A, their bounded sum and maximum (plan creation)
 __global__ void k_bp_bound(RowSet A, RightOp B, int64_t m, unsigned long long *stats) {
-  unsigned long long sb = 0, mx = 0;
+  unsigned long long sb = 0, mx = 0, big = 0;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x) {
     int64_t fr = 0;
     for (int64_t q = A.p[r]; q < A.p[r + 1]; ++q) {
@@ -476,12 +476,15 @@ __global__ void k_bp_bound(RowSet A, RightOp B, int64_t m, unsigned long long *s
     }
     sb += (unsigned long long)min(fr, B.n);
     mx = max(mx, (unsigned long long)fr);
+    big += fr > BPC_CAP ? 1 : 0;  // rows that may need column ranges (a bucket record each)
   }
   sb = warp_sum(sb);
   mx = warp_max(mx);
+  big = warp_sum(big);
   if (lane_id() == 0) {
     atomicAdd(stats, sb);
     atomicMax(stats + 1, mx);
+    atomicAdd(stats + 2, big);
   }
 }
 
@@ -559,16 +562,16 @@ extern "C" int hs_batch_plan_create(int semiring, int64_t count, const hs_mat *A
   }
   P->m = P->SA.m;
   const int64_t m = P->m;
-  // the flop bound of C and the largest row, once
+  // the flop bound of C, the largest row and the rows that may need column ranges, once
   unsigned long long *stats = (unsigned long long *)bp_alloc(P, 16 + 16, st);
   long long *dbg = (long long *)bp_alloc(P, 16, st);
   unsigned long long *h = nullptr;
-  if (!stats || !dbg || cudaMallocHost(&h, 16) != cudaSuccess) {
+  if (!stats || !dbg || cudaMallocHost(&h, 32) != cudaSuccess) {
     cudaGetLastError();
     hs_batch_plan_destroy(P, stream);
     return HS_ENOMEM;
   }
-  cudaMemsetAsync(stats, 0, 16, st);
+  cudaMemsetAsync(stats, 0, 24, st);
   cudaMemsetAsync(dbg, 0, 16, st);
   P->dbg = dbg;
   RowSet rs{P->SA.ptr, P->SA.idx, P->SA.val, nullptr, m, P->SA.nnz, m, dbg};
@@ -578,14 +581,14 @@ extern "C" int hs_batch_plan_create(int semiring, int64_t count, const hs_mat *A
     int64_t g = (m + 255) / 256, gc = (int64_t)sm_count() * 8;
     k_bp_bound<<<(int)(g < gc ? g : gc), 256, 0, st>>>(rs, rb, m, stats);
   }
-  cudaMemcpyAsync(h, stats, 16, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(h, stats, 24, cudaMemcpyDeviceToHost, st);
   if (cudaStreamSynchronize(st) != cudaSuccess) {
     cudaGetLastError();
     cudaFreeHost(h);
     hs_batch_plan_destroy(P, stream);
     return HS_ECUDA;
   }
-  const unsigned long long bound = h[0], fmax = h[1];
+  const unsigned long long bound = h[0], fmax = h[1], nbig = h[2];
   cudaFreeHost(h);
   if (fmax > (unsigned long long)BP_FMAX || m > 0x7fffffffLL) {  // rows this kernel does not take
     hs_batch_plan_destroy(P, stream);
@@ -597,7 +600,7 @@ extern "C" int hs_batch_plan_create(int semiring, int64_t count, const hs_mat *A
     return HS_ECUDA;
   }
   P->cap = (int64_t)bound;
-  const int nbig_cap = 1 << 16;
+  const int nbig_cap = nbig < 1 ? 1 : (nbig > 0x7fffffffULL ? 0x7fffffff : (int)nbig);
   BpArgs &a = P->args;
   a.A = rs;
   a.B = rb;
