@@ -17,7 +17,7 @@
 //   3. the row counts scanned into C's row offsets (each CTA scans a block of
 //      rows, then adds the totals of the blocks before it);
 //   4. the values, written in ascending column order at the row's offset: a
-//      warp row by sorting its products (256, 512 or 1024 keys) in the warp's
+//      warp row by sorting its products (128, 256, 512 or 1024 keys) in the warp's
 //      registers and folding equal columns (sort_row), a CTA row in a shared hash table of keys and
 //      values (with more than 2048 outputs column range by column range,
 //      ranges cut from its buckets).
@@ -35,7 +35,8 @@ namespace hs {
 
 constexpr int BP_NT = 256, BP_NW = BP_NT / 32;
 constexpr int BPW_SYM = 2048;                    // warp tier symbolic set: f <= 1024
-constexpr int BPW_FS = 256, BPW_F = 1024;        // warp tier values: 32*8 or 32*32 sorted products
+constexpr int BPW_FS = 256, BPW_F = 1024;        // warp tier values: 32*K sorted products, K = 4 .. 32
+constexpr int BPW_G = 4;                         // warp groups: rows of at most 128, 256, 512, 1024 products
 constexpr int BPC_SYM = 8192;                    // CTA tier symbolic set: f <= 4096
 constexpr int BPC_SLOTS = 4096, BPC_CAP = 1536;  // CTA tier values: at most 1536 per column range
 constexpr int BP_FMAX = 4096;                    // rows with more products are not taken
@@ -47,8 +48,8 @@ constexpr int BP_CLAIM = 4;                      // warp rows a warp claims per 
 // counters, zeroed before every execution
 struct BpCounters {
   unsigned bar[2];  // grid barrier: arrivals, generation
-  int nwarp[3], ncta;  // rows of each tier (warp rows by the keys they sort: 256, 512, 1024)
-  int sym_w, sym_c, num_w[3], num_c;  // work handed out per phase and tier
+  int nwarp[BPW_G], ncta;  // rows of each tier (warp rows by the keys they sort: 128 .. 1024)
+  int sym_w, sym_c, num_w[BPW_G], num_c;  // work handed out per phase and tier
   int nbig;                         // CTA rows that need column ranges
   int err;   // bit 0: a row outside the tiers; 1: a barrier wait expired; 2: a column range too full
   int kerr;  // consistency codes of the row routines (hash table full, count mismatch)
@@ -71,7 +72,7 @@ struct BpArgs {
   RowSet A;
   RightOp B;
   int64_t m;           // stacked rows
-  int32_t *wlist[3];   // warp-tier rows of at most 256, 512 and wf_max products
+  int32_t *wlist[BPW_G];  // warp-tier rows of at most 128, 256, 512 and wf_max products
   int wf_max;          // products of a warp-tier row at most (BPW_F, or BPW_FS for very wide problems)
   int32_t *clist;      // CTA-tier rows
   int32_t *fw;         // products per row (phase 1), read by the later phases
@@ -163,16 +164,20 @@ __global__ void __launch_bounds__(BP_NT, 3) k_batch_persist(BpArgs a) {
       a.fw[r] = (int32_t)(fr < 0x7fffffff ? fr : 0x7fffffff);
       if (fr > BP_FMAX) atomicOr(&ctr->err, 1);
     }
-    bp_append(r < a.m && fr > 0 && fr <= BPW_FS, (int)r, &ctr->nwarp[0], a.wlist[0]);
-    bp_append(r < a.m && fr > BPW_FS && fr <= 2 * BPW_FS && fr <= a.wf_max, (int)r, &ctr->nwarp[1], a.wlist[1]);
-    bp_append(r < a.m && fr > 2 * BPW_FS && fr <= a.wf_max, (int)r, &ctr->nwarp[2], a.wlist[2]);
+    bp_append(r < a.m && fr > 0 && fr <= BPW_FS / 2, (int)r, &ctr->nwarp[0], a.wlist[0]);
+    bp_append(r < a.m && fr > BPW_FS / 2 && fr <= BPW_FS, (int)r, &ctr->nwarp[1], a.wlist[1]);
+    bp_append(r < a.m && fr > BPW_FS && fr <= 2 * BPW_FS && fr <= a.wf_max, (int)r, &ctr->nwarp[2], a.wlist[2]);
+    bp_append(r < a.m && fr > 2 * BPW_FS && fr <= a.wf_max, (int)r, &ctr->nwarp[3], a.wlist[3]);
     bp_append(r < a.m && fr > a.wf_max && fr <= BP_FMAX, (int)r, &ctr->ncta, a.clist);
   }
   if (blockIdx.x == 0 && tid == 0) a.Cp[0] = 0;
   bp_grid_sync(ctr, a.spin_limit);
   bp_stamp(ctr, 1);
-  const int nw0 = *(volatile int *)&ctr->nwarp[0], nw1 = *(volatile int *)&ctr->nwarp[1];
-  const int nw_rows = nw0 + nw1 + *(volatile int *)&ctr->nwarp[2], nc_rows = *(volatile int *)&ctr->ncta;
+  int nw_pre[BPW_G + 1];  // exclusive prefix of the warp groups' sizes
+  nw_pre[0] = 0;
+#pragma unroll
+  for (int g = 0; g < BPW_G; ++g) nw_pre[g + 1] = nw_pre[g] + *(volatile int *)&ctr->nwarp[g];
+  const int nw_rows = nw_pre[BPW_G], nc_rows = *(volatile int *)&ctr->ncta;
 
   // ---- 2. distinct columns per row
   {
@@ -253,7 +258,15 @@ __global__ void __launch_bounds__(BP_NT, 3) k_batch_persist(BpArgs a) {
         iend = min(i + BP_CLAIM, nw_rows);
         if (i >= iend) break;
       }
-      const int r = i < nw0 ? a.wlist[0][i] : (i < nw0 + nw1 ? a.wlist[1][i - nw0] : a.wlist[2][i - nw0 - nw1]);
+      const int32_t *wl = a.wlist[0];
+      int off = 0;
+#pragma unroll
+      for (int t = 1; t < BPW_G; ++t)
+        if (i >= nw_pre[t]) {  // (unrolled: the prefix stays in registers)
+          wl = a.wlist[t];
+          off = nw_pre[t];
+        }
+      const int r = wl[i - off];
       const int slots = max(64, min(BPW_SYM, next_pow2(2 * a.fw[r])));  // load at most one half
       for (int s = lane; s < slots; s += 32) wkeys[s] = EMPTY;
       __syncwarp();
@@ -377,7 +390,7 @@ __global__ void __launch_bounds__(BP_NT, 3) k_batch_persist(BpArgs a) {
     T *s_val = reinterpret_cast<T *>(a.wscratch) + ((size_t)blockIdx.x * BP_NW + warp) * BPW_F;
     // rows of 1024, then 512, then 256 keys: the warps of an SM mostly run the
     // same width at a time, and the expansion has one call site for all three
-    int g = 2, i = 0, iend = 0;  // rows [i, iend) of group g claimed by this warp
+    int g = BPW_G - 1, i = 0, iend = 0;  // rows [i, iend) of group g claimed by this warp
     while (g >= 0) {
       if (i >= iend) {
         int i0 = 0;
@@ -395,13 +408,15 @@ __global__ void __launch_bounds__(BP_NT, 3) k_batch_persist(BpArgs a) {
       const int fr = a.fw[r];
       int kmn = 0, kmx = 0;
       const int got = sort_expand<SR>(A, B, A.p[r], A.p[r + 1], BPW_F, s_col, s_val, &kmn, &kmx);
-      if (got != fr || fr > (BPW_FS << g)) {
+      if (got != fr || fr > ((BPW_FS / 2) << g)) {
         if (lane == 0) atomicExch(&ctr->kerr, 12);
       } else if (HS_G(dbg, cb + c <= a.cap, 81, cb + c)) {
         T *out_v = SR::has_val ? Cv + cb : nullptr;
         if (g == 0)
-          sort_finish<SR, BPW_FS / 32, true>(fr, c, kmn, kmx, s_col, s_val, a.Cj + cb, out_v, &ctr->kerr, dbg);
+          sort_finish<SR, BPW_FS / 64, true>(fr, c, kmn, kmx, s_col, s_val, a.Cj + cb, out_v, &ctr->kerr, dbg);
         else if (g == 1)
+          sort_finish<SR, BPW_FS / 32, true>(fr, c, kmn, kmx, s_col, s_val, a.Cj + cb, out_v, &ctr->kerr, dbg);
+        else if (g == 2)
           sort_finish<SR, 2 * BPW_FS / 32, false>(fr, c, kmn, kmx, s_col, s_val, a.Cj + cb, out_v, &ctr->kerr, dbg);
         else
           sort_finish<SR, BPW_F / 32, false>(fr, c, kmn, kmx, s_col, s_val, a.Cj + cb, out_v, &ctr->kerr, dbg);
@@ -611,9 +626,8 @@ extern "C" int hs_batch_plan_create(int semiring, int64_t count, const hs_mat *A
   int64_t nmax = 0;
   for (int64_t i = 0; i < count; ++i) nmax = B[i].n > nmax ? B[i].n : nmax;
   a.wf_max = nmax >= SORT_PACKED_COLS ? BPW_FS : BPW_F;
-  a.wlist[0] = (int32_t *)bp_alloc(P, 4 * 3 * (size_t)(m > 0 ? m : 1), st);
-  a.wlist[1] = a.wlist[0] ? a.wlist[0] + (m > 0 ? m : 1) : nullptr;
-  a.wlist[2] = a.wlist[0] ? a.wlist[1] + (m > 0 ? m : 1) : nullptr;
+  a.wlist[0] = (int32_t *)bp_alloc(P, 4 * (size_t)BPW_G * (size_t)(m > 0 ? m : 1), st);
+  for (int g = 1; g < BPW_G; ++g) a.wlist[g] = a.wlist[0] ? a.wlist[g - 1] + (m > 0 ? m : 1) : nullptr;
   a.clist = (int32_t *)bp_alloc(P, 4 * (size_t)(m > 0 ? m : 1), st);
   a.fw = (int32_t *)bp_alloc(P, 4 * (size_t)(m > 0 ? m : 1), st);
   a.cbig = (int32_t *)bp_alloc(P, 4 * (size_t)(m > 0 ? m : 1), st);
