@@ -64,14 +64,16 @@ def peaks():
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch
-# of the dominant kernel, from a 1-pass ncu capture of this workload (its
-# command and counters are summarised under profiles/).  It is
+# of the dominant kernel: ncu's one-pass counters for k_num_units at R-MAT
+# scale 18 (4.2231 GB per launch, three launches within 0.05 percent), scaled
+# to scale 20 by the ratio of the launch's algorithmic bytes (24.415 / 2.6124
+# GB); the command and counters are summarised under profiles/.  It is
 # reported only while the device sources of that kernel and of the kernels
-# that write its inputs (bins, lists, segment index) still hash to the value
-# they had when it was taken; after any change there the field is null until
-# it is measured again.
-MEASURED_TRAFFIC = {"kernel": "numeric_heavy", "scale": 20, "bytes": 32.72e9 + 24.57e9,
-                    "csrc_sha256_16": "6ff06ccecf8861a9"}
+# that write its inputs (bins, lists, units, pairs, segment index) still hash
+# to the value they had when it was taken; after any change there the field
+# is null until it is measured again.
+MEASURED_TRAFFIC = {"kernel": "numeric_heavy", "scale": 20, "bytes": 4.2231e9 * 24.415 / 2.6124,
+                    "measured_at_scale": 18, "csrc_sha256_16": "31f70edbbe526d49"}
 KERNEL_SOURCES = ("analysis.cu", "common.cuh", "internal.h", "numeric.cuh", "numeric_pt.cu", "symbolic.cu")
 
 
@@ -86,10 +88,10 @@ def csrc_hash():
     return h.hexdigest()[:16]
 
 
-# row blocks of the end-to-end product: with more blocks the extra per-block work outweighed the
-# copy overlap on this workload (the device-to-host copy runs at about 190 GB/s whatever the
-# streams), and the kernels storing C straight into host memory measured 4 % slower than
-# staging it on the device and copying it
+# the end-to-end product in one row block, its numeric kernels storing C's columns and values
+# straight into the page-locked host arrays over the C2C link while they run: 231.6 ms in every
+# repetition, against 231-300 ms for staging C on the device and copying it (the copy of the
+# 28.6 GB into large pinned arrays ran at 97-193 GB/s) and more for 2, 4 or 8 row blocks
 E2E_BLOCKS = 1
 
 
@@ -848,7 +850,7 @@ def main():
             eh1.record(stream)
             M = h.DeviceCSR(A.m, A.n, rp, cj, cv, "f32")
             got = h.spgemm_to_host("plus_times", M, M, out_rp, out_j, out_v, blocks=E2E_BLOCKS,
-                                   stage_on_device=True, stream=stream)
+                                   stage_on_device=False, stream=stream)
             torch.cuda.synchronize(dev)
             dt = time.perf_counter() - t0
             assert got == nnz_c
@@ -875,7 +877,7 @@ def main():
                "h2d_ms": statistics.median(h2d_ms),
                "product_and_d2h_ms": 1000 * statistics.median(etimes) - statistics.median(h2d_ms),
                "link_d2h_gbs": statistics.median(link),
-               "api": f"spgemm_to_host, {E2E_BLOCKS} row blocks"}
+               "api": f"spgemm_to_host, {E2E_BLOCKS} row block, C written into the mapped pinned host arrays"}
         hA = out_rp = out_j = out_v = None
         torch.cuda.empty_cache()
 
