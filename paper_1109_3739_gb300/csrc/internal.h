@@ -24,7 +24,8 @@ constexpr int KEY_SORT_XS = 8;  // f <= 128 (K = 4)
 constexpr int KEY_SORT_S = 9;   // f <= 256 (K = 8)
 constexpr int KEY_SORT_M = 10;  // f <= 512 (K = 16)
 constexpr int KEY_SORT = 11;    // f <= 1024 (K = 32)
-constexpr int KEY_HEAVY = 12;   // 12 + (62 - floor(log2 f)): symbolic bitmap / numeric column parts
+constexpr int KEY_SPA = 12;     // products with few columns (BinCfg::spa): f > 32, a warp's dense accumulator
+constexpr int KEY_HEAVY = 13;   // 13 + (62 - floor(log2 f)): symbolic bitmap / numeric column parts
 constexpr int F_TINY = 32, F_WARP_S = 128, F_WARP = 512, F_MID_S = 1024, F_MID = 4096, F_LARGE = 16384;
 constexpr int F_SORT_XS = 128, F_SORT_S = 256, F_SORT_M = 512, F_SORT = 1024;
 // Sort tiers pack (column - min column) << log2(32K) | product index into 32
@@ -33,6 +34,11 @@ constexpr int F_SORT_XS = 128, F_SORT_S = 256, F_SORT_M = 512, F_SORT = 1024;
 // of more than 256 products out of them (numeric_bins).
 constexpr int SORT_WIDE_K = 8;
 constexpr int64_t SORT_PACKED_COLS = (1 << 22) - 1;
+// Products whose B has at most spa_cols(value bytes) columns take, for every
+// row of more than 32 products, one warp's dense accumulator of all n columns
+// (Figure 1's SPA as it stands: a value per column and an occupancy bitmap).
+constexpr int SPA_COLS_8 = 1024, SPA_COLS_4 = 2048;
+__host__ __device__ constexpr int spa_cols(int value_bytes) { return value_bytes == 8 ? SPA_COLS_8 : SPA_COLS_4; }
 constexpr int CAP_MID_S = 1024, CAP_MID = 2048;
 // Column segments recorded for rows that may need column parts: width SEG_W
 // (a multiple of 1024, at most every numeric table's capacity).
@@ -62,6 +68,7 @@ struct BinCfg {
   int sym_heavy_from;  // symbolic: rows with f > this take the bitmap kernel (4096..cap_large)
   int sort_max;        // numeric: rows with 32 < f <= this and 100*c >= sort_pct*f sort their products (32..1024)
   int sort_pct;        // (0..101; 101 switches the sort tiers off)
+  int spa;             // 1: B has at most spa_cols() columns; rows of more than 32 products take KEY_SPA
 };
 // Symbolic bins.  Every row that may end in the numeric heavy bin (c >
 // cap_large needs f > cap_large) takes the bitmap kernel, which also writes
@@ -69,6 +76,7 @@ struct BinCfg {
 __host__ __device__ inline int sym_key(int64_t f, const BinCfg &b) {
   if (f <= 0) return 0;
   if (f <= F_TINY) return KEY_TINY;
+  if (b.spa) return KEY_SPA;
   if (f <= F_WARP) return KEY_WARP;
   if (f <= b.sym_mid_s_max) return KEY_MID_S;
   if (f <= F_MID) return KEY_MID;
@@ -80,6 +88,7 @@ __host__ __device__ inline int sym_key(int64_t f, const BinCfg &b) {
 __host__ __device__ inline int num_key(int64_t f, int64_t c, const BinCfg &b) {
   if (c <= 0) return 0;
   if (f <= F_TINY) return KEY_TINY;
+  if (b.spa) return KEY_SPA;
   if (f <= b.sort_max && c * 100 >= f * b.sort_pct)
     return f <= F_SORT_XS ? KEY_SORT_XS : (f <= F_SORT_S ? KEY_SORT_S : (f <= F_SORT_M ? KEY_SORT_M : KEY_SORT));
   if (f <= b.warp_s_max) return KEY_WARP_S;
@@ -92,7 +101,13 @@ __host__ __device__ inline int num_key(int64_t f, int64_t c, const BinCfg &b) {
 }
 // the default thresholds for a value width, clamped tuning values otherwise
 BinCfg bin_config(int value_bytes);
-// the numeric pass's thresholds for a product with ncols columns
+// the thresholds of a product whose B has ncols columns (value_bytes: C's
+// value width): the dense-accumulator tier for narrow products, and the sort
+// tiers' 64-bit limit for very wide ones
+inline BinCfg product_bins(BinCfg b, int64_t ncols, int value_bytes) {
+  b.spa = (ncols > 0 && ncols <= spa_cols(value_bytes)) ? 1 : 0;
+  return b;
+}
 inline BinCfg numeric_bins(BinCfg b, int64_t ncols) {
   if (ncols >= SORT_PACKED_COLS && b.sort_max > F_SORT_S) b.sort_max = F_SORT_S;
   return b;
@@ -194,6 +209,7 @@ void launch_sym_mid_s(const SymArgs &a, cudaStream_t st);
 void launch_sym_mid(const SymArgs &a, cudaStream_t st);
 void launch_sym_large(const SymArgs &a, cudaStream_t st);
 void launch_sym_heavy(const SymArgs &a, cudaStream_t st);
+void launch_sym_spa(const SymArgs &a, cudaStream_t st);
 
 
 // A unit of the numeric heavy pass: one column part of one heavy row.  The
@@ -273,9 +289,10 @@ struct NumArgs {
   int pair_abytes;        // width of the left values the pairs carry (0: none)
 };
 // kind: 0 tiny, 1 warp_s, 2 warp, 3 mid_s, 4 mid, 5 large_s, 6 large,
-// 7 sort_xs, 8 sort_s, 9 sort_m, 10 sort, 11 heavy (bin key KEY_TINY + kind;
-// heavy takes every key from KEY_HEAVY on).  dtype codes as in the ABI.
-constexpr int NUM_KINDS = 12;
+// 7 sort_xs, 8 sort_s, 9 sort_m, 10 sort, 11 spa, 12 heavy (bin key
+// KEY_TINY + kind; heavy takes every key from KEY_HEAVY on).  dtype codes as
+// in the ABI.
+constexpr int NUM_KINDS = 13;
 bool launch_numeric_pt(int dtype, int kind, const NumArgs &a, cudaStream_t st);
 bool launch_numeric_mp(int dtype, int kind, const NumArgs &a, cudaStream_t st);
 bool launch_numeric_oa(int kind, const NumArgs &a, cudaStream_t st);

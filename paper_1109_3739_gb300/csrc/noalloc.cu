@@ -182,7 +182,7 @@ static int spgemm_noalloc_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat 
   if (ar.over) return HS_ESCRATCH;
   static thread_local NaBlock hb;  // host copy (ordinary memory)
 
-  const BinCfg bins = bin_config(vb);
+  const BinCfg bins = product_bins(bin_config(vb), n, vb);
   RowSet rs{A->ptr, A->idx, A->val, A->fmt == HS_DCSR ? A->ids : nullptr, nslots, A->nnz, m, sb->dbg};
   RightOp rb{B->ptr, B->idx, B->val, n, B->m, B->nnz, sb->dbg};
   NA_CK(cudaMemsetAsync(sb, 0, sizeof(NaBlock), st));
@@ -219,6 +219,8 @@ static int spgemm_noalloc_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat 
   launch_sym_mid(sa, st);
   sym_bin(KEY_LARGE, KEY_LARGE + 1);
   launch_sym_large(sa, st);
+  sym_bin(KEY_SPA, KEY_SPA + 1);
+  launch_sym_spa(sa, st);
   sym_bin(KEY_HEAVY, NKEYS);
   launch_sym_heavy(sa, st);
   if (int e = check_last()) return e;

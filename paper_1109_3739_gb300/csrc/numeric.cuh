@@ -864,6 +864,89 @@ template <class SR, int K> void launch_num_sort(const NumArgs &a, cudaStream_t s
   k<<<ngrid_cap(a.count, NSORT_WPB, fit_per_sm(k, NSORT_WPB * 32, bytes)), NSORT_WPB * 32, bytes, st>>>(a);
 }
 
+// ------------------------------------------------------------- dense SPA
+// Products whose B has at most spa_cols() columns (Figure 1's sparse
+// accumulator as it stands): one warp per row keeps a value for every column
+// and an occupancy bitmap; each product sets its bit and adds its value, and
+// the row leaves in column order by walking the bitmap (a lane owns a run of
+// consecutive words; an exclusive scan of their set bits gives each run's
+// start).  Every value is reset to the identity as it is written out, so the
+// array is cleared once per kernel, not per row.
+constexpr int NSPA_WPB = 4;
+template <typename T> struct SpaLayout {
+  static constexpr int COLS = spa_cols(vbytes<T>());
+  static constexpr size_t bits_bytes = (size_t)COLS / 8;
+  static constexpr size_t per_warp = bits_bytes + (((size_t)COLS * vbytes<T>() + 15) & ~(size_t)15);
+};
+template <class SR>
+__global__ void __launch_bounds__(NSPA_WPB * 32, 8) k_num_spa(NumArgs a) {
+  using T = typename SR::val_t;
+  using L = SpaLayout<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int w = threadIdx.x >> 5, lane = lane_id();
+  unsigned *bits = reinterpret_cast<unsigned *>(smem_raw + (size_t)w * L::per_warp);
+  T *vals = reinterpret_cast<T *>(smem_raw + (size_t)w * L::per_warp + L::bits_bytes);
+  const DevCsr A = ndev_a(a.A), B = ndev_b(a.B);
+  T *Cv = reinterpret_cast<T *>(a.Cv);
+  const int n = (int)a.B.n;
+  const int words = (n + 31) >> 5;
+  const int wpl = (words + 31) >> 5;  // words a lane walks
+  for (int i = lane; i < words; i += 32) bits[i] = 0u;
+  if constexpr (SR::has_val)
+    for (int i = lane; i < n; i += 32) vals[i] = SR::identity();
+  __syncwarp();
+  for (int idx = blockIdx.x * NSPA_WPB + w; idx < a.count; idx += gridDim.x * NSPA_WPB) {
+    const int r = a.list[idx];
+    if (!HS_G(a.A.dbg, r >= 0 && r < a.A.nslots, 35, r)) continue;
+    const int64_t o = nout_row(a.A, r);
+    const int64_t cb = a.Cp[o];
+    const int c = (int)(a.Cp[o + 1] - cb);
+    warp_products<SR>(A, B, A.p[r], A.p[r + 1], [&](int col, T v, int) {
+      if (!HS_G(a.A.dbg, col >= 0 && col < n, 85, col)) return;
+      atomicOr(bits + (col >> 5), 1u << (col & 31));
+      if constexpr (SR::has_val) SR::add_atomic(vals + col, v);
+    });
+    __syncwarp();
+    const int w0 = lane * wpl, w1 = min(words, w0 + wpl);
+    int cnt = 0;
+    for (int i = w0; i < w1; ++i) cnt += __popc(bits[i]);
+    const int incl = warp_incl_scan(cnt);
+    const int total = __shfl_sync(FULL, incl, 31);
+    if (total != c) {
+      if (lane == 0) atomicExch(a.err, 1);
+    } else {
+      int pos = incl - cnt;
+      for (int i = w0; i < w1; ++i) {
+        unsigned m = bits[i];
+        while (m) {
+          const int col = (i << 5) + __ffs(m) - 1;
+          m &= m - 1;
+          __stcs(a.Cj + cb + pos, col);
+          if constexpr (SR::has_val) {
+            __stcs(Cv + cb + pos, vals[col]);
+            vals[col] = SR::identity();
+          }
+          ++pos;
+        }
+      }
+    }
+    for (int i = w0; i < w1; ++i) bits[i] = 0u;
+    if constexpr (SR::has_val)
+      if (total != c)  // values left behind by a row that failed its check
+        for (int i = lane; i < n; i += 32) vals[i] = SR::identity();
+    __syncwarp();
+  }
+}
+
+template <class SR> void launch_num_spa(const NumArgs &a, cudaStream_t st) {
+  using T = typename SR::val_t;
+  const size_t bytes = SpaLayout<T>::per_warp * NSPA_WPB;
+  auto k = k_num_spa<SR>;
+  set_smem_attr(k, bytes);
+  count_launch();
+  k<<<ngrid_cap(a.count, NSPA_WPB, fit_per_sm(k, NSPA_WPB * 32, bytes)), NSPA_WPB * 32, bytes, st>>>(a);
+}
+
 template <class SR, int SLOTS, int CAP> void launch_num_warp(const NumArgs &a, cudaStream_t st) {
   using T = typename SR::val_t;
   const size_t bytes = WarpNumSmem<T, SLOTS, CAP>::per_warp * NWARP_WPB;
@@ -903,7 +986,8 @@ template <class SR> void launch_numeric_sr(int kind, const NumArgs &a, cudaStrea
     case 8: launch_num_sort<SR, 8>(a, st); break;
     case 9: launch_num_sort<SR, 16>(a, st); break;
     case 10: launch_num_sort<SR, 32>(a, st); break;
-    case 11: {
+    case 11: launch_num_spa<SR>(a, st); break;
+    case 12: {
       if (a.units && a.nunits > 0) {
         const size_t ub = sizeof(UnitSmem<T>);
         auto ku = k_num_units<SR>;

@@ -416,7 +416,7 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
     return check_launch();
   }
 
-  const BinCfg bins = bin_config(vb);
+  const BinCfg bins = product_bins(bin_config(vb), n, vb);
   int64_t *f = mem.tmp<int64_t>(nslots);
   int *list = mem.tmp<int>(nslots);
   int32_t *hslot = mem.tmp<int32_t>(nslots);
@@ -586,6 +586,9 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
     sym_bin(KEY_LARGE, KEY_LARGE + 1);
     { PhaseTimer t2("symbolic_large", st, sa.count > 0); launch_sym_large(sa, st); }
     if (int e = phase_check("symbolic_large", st, sb->dbg)) return e;
+    sym_bin(KEY_SPA, KEY_SPA + 1);
+    { PhaseTimer t2("symbolic_spa", st, sa.count > 0); launch_sym_spa(sa, st); }
+    if (int e = phase_check("symbolic_spa", st, sb->dbg)) return e;
     sym_bin(KEY_HEAVY, NKEYS);
     { PhaseTimer t2("symbolic_heavy", st, sa.count > 0); launch_sym_heavy(sa, st); }
     if (int e = phase_check("symbolic_heavy", st, sb->dbg)) return e;
@@ -715,7 +718,8 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
   na.pair_abytes = a_bytes;
   const char *names[NUM_KINDS] = {"numeric_tiny",   "numeric_warp_s", "numeric_warp",   "numeric_mid_s",
                                   "numeric_mid",    "numeric_large_s", "numeric_large", "numeric_sort_xs",
-                                  "numeric_sort_s", "numeric_sort_m",  "numeric_sort",  "numeric_heavy"};
+                                  "numeric_sort_s", "numeric_sort_m",  "numeric_sort",  "numeric_spa",
+                                  "numeric_heavy"};
   static_assert(KEY_TINY + NUM_KINDS - 1 == KEY_HEAVY, "one key per numeric kind before the heavy keys");
   {
     PhaseTimer t("numeric", st);

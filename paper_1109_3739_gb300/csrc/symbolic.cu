@@ -99,6 +99,35 @@ __global__ void __launch_bounds__(WARP_WPB * 32, 4) k_sym_warp(SymArgs a) {
   }
 }
 
+// ------------------------------------------------------------- dense SPA
+// Products whose B has at most SPA_COLS_4 columns: one warp per row sets a
+// bit per product in a bitmap of all n columns (the occupancy half of
+// Figure 1's sparse accumulator) and counts the set bits.
+constexpr int SPA_WPB = 8;
+__global__ void __launch_bounds__(SPA_WPB * 32) k_sym_spa(SymArgs a) {
+  __shared__ unsigned bits_all[SPA_WPB][SPA_COLS_4 / 32];
+  const int w = threadIdx.x >> 5, lane = lane_id();
+  unsigned *bits = bits_all[w];
+  const DevCsr A = dev_a(a.A), B = dev_b(a.B);
+  const int n = (int)a.B.n;
+  const int words = (n + 31) >> 5;
+  for (int idx = blockIdx.x * SPA_WPB + w; idx < a.count; idx += gridDim.x * SPA_WPB) {
+    const int r = a.list[idx];
+    if (!HS_G(a.A.dbg, r >= 0 && r < a.A.nslots, 35, r)) continue;
+    for (int i = lane; i < words; i += 32) bits[i] = 0u;
+    __syncwarp();
+    warp_products<StructSR>(A, B, A.p[r], A.p[r + 1], [&](int col, NoVal, int) {
+      if (HS_G(a.A.dbg, col >= 0 && col < n, 84, col)) atomicOr(bits + (col >> 5), 1u << (col & 31));
+    });
+    __syncwarp();
+    int cnt = 0;
+    for (int i = lane; i < words; i += 32) cnt += __popc(bits[i]);
+    cnt = warp_sum(cnt);
+    if (lane == 0) put_count(a, out_row(a.A, r), cnt);
+    __syncwarp();
+  }
+}
+
 // ----------------------------------------------------------- mid / large
 constexpr int CH = 1024;   // A entries per expansion round (heavy)
 constexpr int CHM = 256;   // the same for the hash kernels: smaller staging, more CTAs per SM
@@ -324,6 +353,11 @@ template <int SLOTS> static void launch_sym_warp_slots(const SymArgs &a, cudaStr
                       WARP_WPB * 32, bytes, st>>>(a);
 }
 void launch_sym_warp(const SymArgs &a, cudaStream_t st) { launch_sym_warp_slots<2 * F_WARP>(a, st); }
+void launch_sym_spa(const SymArgs &a, cudaStream_t st) {
+  if (a.count <= 0) return;
+  count_launch();
+  k_sym_spa<<<grid_cap(a.count, SPA_WPB, fit_per_sm(k_sym_spa, SPA_WPB * 32, 0)), SPA_WPB * 32, 0, st>>>(a);
+}
 
 template <int SLOTS, int NT> static void launch_sym_cta(const SymArgs &a, cudaStream_t st) {
   if (a.count <= 0) return;
