@@ -247,12 +247,18 @@ int hs_trim_memory(void);
  *                   in a warp's registers (expand, sort, compress) instead of
  *                   hashing them (sort_max 32..1024, 1024; sort_pct 0..101,
  *                   50; 101 switches the sort tiers off)
+ *   spa_max         products whose B has at most spa_max columns (at most
+ *                   2048, 1024 for 8-byte values) give every row of more
+ *                   than 32 products one warp's dense accumulator of all the
+ *                   columns (Figure 1's SPA) instead of the tiers above
+ *                   (0..2048; 0 = never)
  * Results do not depend on the thresholds.  hs_set_tuning(NULL) restores the
  * defaults (given last above).  Both calls return HS_OK (hs_get_tuning:
  * HS_EINVAL for NULL). */
 typedef struct hs_tuning {
   int32_t warp_s_max, mid_s_max, large_s_max, sym_mid_s_max, sym_heavy_from;
   int32_t sort_max, sort_pct;
+  int32_t spa_max;
 } hs_tuning;
 int hs_set_tuning(const hs_tuning *t);
 int hs_get_tuning(hs_tuning *t);

@@ -34,9 +34,10 @@ constexpr int F_SORT_XS = 128, F_SORT_S = 256, F_SORT_M = 512, F_SORT = 1024;
 // of more than 256 products out of them (numeric_bins).
 constexpr int SORT_WIDE_K = 8;
 constexpr int64_t SORT_PACKED_COLS = (1 << 22) - 1;
-// Products whose B has at most spa_cols(value bytes) columns take, for every
-// row of more than 32 products, one warp's dense accumulator of all n columns
-// (Figure 1's SPA as it stands: a value per column and an occupancy bitmap).
+// Products whose B has at most spa_cols(value bytes) columns may take (tuning
+// spa_max), for every row of more than 32 products, one warp's dense
+// accumulator of all n columns (Figure 1's SPA as it stands: a value per
+// column and an occupancy flag).
 constexpr int SPA_COLS_8 = 1024, SPA_COLS_4 = 2048;
 __host__ __device__ constexpr int spa_cols(int value_bytes) { return value_bytes == 8 ? SPA_COLS_8 : SPA_COLS_4; }
 constexpr int CAP_MID_S = 1024, CAP_MID = 2048;
@@ -68,7 +69,8 @@ struct BinCfg {
   int sym_heavy_from;  // symbolic: rows with f > this take the bitmap kernel (4096..cap_large)
   int sort_max;        // numeric: rows with 32 < f <= this and 100*c >= sort_pct*f sort their products (32..1024)
   int sort_pct;        // (0..101; 101 switches the sort tiers off)
-  int spa;             // 1: B has at most spa_cols() columns; rows of more than 32 products take KEY_SPA
+  int spa_max;         // products whose B has at most min(this, spa_cols()) columns take the dense tier (0: none)
+  int spa;             // set per product: rows of more than 32 products take KEY_SPA
 };
 // Symbolic bins.  Every row that may end in the numeric heavy bin (c >
 // cap_large needs f > cap_large) takes the bitmap kernel, which also writes
@@ -105,7 +107,8 @@ BinCfg bin_config(int value_bytes);
 // value width): the dense-accumulator tier for narrow products, and the sort
 // tiers' 64-bit limit for very wide ones
 inline BinCfg product_bins(BinCfg b, int64_t ncols, int value_bytes) {
-  b.spa = (ncols > 0 && ncols <= spa_cols(value_bytes)) ? 1 : 0;
+  const int lim = b.spa_max < spa_cols(value_bytes) ? b.spa_max : spa_cols(value_bytes);
+  b.spa = (ncols > 0 && ncols <= lim) ? 1 : 0;
   return b;
 }
 inline BinCfg numeric_bins(BinCfg b, int64_t ncols) {

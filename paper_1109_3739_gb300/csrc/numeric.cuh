@@ -867,31 +867,49 @@ template <class SR, int K> void launch_num_sort(const NumArgs &a, cudaStream_t s
 // ------------------------------------------------------------- dense SPA
 // Products whose B has at most spa_cols() columns (Figure 1's sparse
 // accumulator as it stands): one warp per row keeps a value for every column
-// and an occupancy bitmap; each product sets its bit and adds its value, and
-// the row leaves in column order by walking the bitmap (a lane owns a run of
-// consecutive words; an exclusive scan of their set bits gives each run's
-// start).  Every value is reset to the identity as it is written out, so the
-// array is cleared once per kernel, not per row.
+// and an occupancy flag per column (a byte, set by a plain store, so lanes
+// that hit one column do not queue on an atomic); lanes whose products share
+// a column fold their values first (__match_any_sync) and one of them adds
+// the sum.  The row leaves in column order by walking the flags (a lane owns
+// a run of consecutive flag words; an exclusive scan of their counts gives
+// each run's start).  Every value is reset to the identity and every flag
+// cleared as it is written out, so the arrays are cleared once per kernel.
 constexpr int NSPA_WPB = 4;
 template <typename T> struct SpaLayout {
   static constexpr int COLS = spa_cols(vbytes<T>());
-  static constexpr size_t bits_bytes = (size_t)COLS / 8;
-  static constexpr size_t per_warp = bits_bytes + (((size_t)COLS * vbytes<T>() + 15) & ~(size_t)15);
+  static constexpr size_t flag_bytes = (size_t)COLS;
+  static constexpr size_t per_warp = flag_bytes + (((size_t)COLS * vbytes<T>() + 15) & ~(size_t)15);
 };
+// the semiring's add folded over the lanes of `grp` (lanes with one column);
+// every lane of the group returns the fold, in lane order
+template <class SR>
+__device__ __forceinline__ typename SR::val_t group_fold(unsigned grp, typename SR::val_t v) {
+  using T = typename SR::val_t;
+  T acc = v;
+  bool first = true;
+  for (unsigned m = grp; m; m &= m - 1) {
+    const int src = __ffs(m) - 1;
+    const T x = __shfl_sync(grp, v, src);
+    acc = first ? x : SR::add(acc, x);
+    first = false;
+  }
+  return acc;
+}
 template <class SR>
 __global__ void __launch_bounds__(NSPA_WPB * 32, 8) k_num_spa(NumArgs a) {
   using T = typename SR::val_t;
   using L = SpaLayout<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int w = threadIdx.x >> 5, lane = lane_id();
-  unsigned *bits = reinterpret_cast<unsigned *>(smem_raw + (size_t)w * L::per_warp);
-  T *vals = reinterpret_cast<T *>(smem_raw + (size_t)w * L::per_warp + L::bits_bytes);
+  unsigned char *flag = smem_raw + (size_t)w * L::per_warp;
+  T *vals = reinterpret_cast<T *>(smem_raw + (size_t)w * L::per_warp + L::flag_bytes);
+  unsigned *flag4 = reinterpret_cast<unsigned *>(flag);
   const DevCsr A = ndev_a(a.A), B = ndev_b(a.B);
   T *Cv = reinterpret_cast<T *>(a.Cv);
   const int n = (int)a.B.n;
-  const int words = (n + 31) >> 5;
-  const int wpl = (words + 31) >> 5;  // words a lane walks
-  for (int i = lane; i < words; i += 32) bits[i] = 0u;
+  const int fwords = (n + 3) >> 2;         // flag words of 4 columns
+  const int wpl = (fwords + 31) >> 5;      // flag words a lane walks
+  for (int i = lane; i < (L::COLS >> 2); i += 32) flag4[i] = 0u;
   if constexpr (SR::has_val)
     for (int i = lane; i < n; i += 32) vals[i] = SR::identity();
   __syncwarp();
@@ -902,14 +920,20 @@ __global__ void __launch_bounds__(NSPA_WPB * 32, 8) k_num_spa(NumArgs a) {
     const int64_t cb = a.Cp[o];
     const int c = (int)(a.Cp[o + 1] - cb);
     warp_products<SR>(A, B, A.p[r], A.p[r + 1], [&](int col, T v, int) {
-      if (!HS_G(a.A.dbg, col >= 0 && col < n, 85, col)) return;
-      atomicOr(bits + (col >> 5), 1u << (col & 31));
-      if constexpr (SR::has_val) SR::add_atomic(vals + col, v);
+      const bool ok = HS_G(a.A.dbg, col >= 0 && col < n, 85, col);
+      if (ok) flag[col] = 1;
+      if constexpr (SR::has_val) {
+        const unsigned grp = __match_any_sync(__activemask(), ok ? col : -1);
+        if (ok) {
+          const T sum = (grp & (grp - 1)) ? group_fold<SR>(grp, v) : v;
+          if (lane == __ffs(grp) - 1) SR::add_atomic(vals + col, sum);
+        }
+      }
     });
     __syncwarp();
-    const int w0 = lane * wpl, w1 = min(words, w0 + wpl);
+    const int w0 = lane * wpl, w1 = min(fwords, w0 + wpl);
     int cnt = 0;
-    for (int i = w0; i < w1; ++i) cnt += __popc(bits[i]);
+    for (int i = w0; i < w1; ++i) cnt += __popc(flag4[i] & 0x01010101u);
     const int incl = warp_incl_scan(cnt);
     const int total = __shfl_sync(FULL, incl, 31);
     if (total != c) {
@@ -917,10 +941,12 @@ __global__ void __launch_bounds__(NSPA_WPB * 32, 8) k_num_spa(NumArgs a) {
     } else {
       int pos = incl - cnt;
       for (int i = w0; i < w1; ++i) {
-        unsigned m = bits[i];
-        while (m) {
-          const int col = (i << 5) + __ffs(m) - 1;
-          m &= m - 1;
+        const unsigned fw = flag4[i];
+        if (!fw) continue;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (!((fw >> (8 * k)) & 0xffu)) continue;
+          const int col = (i << 2) + k;
           __stcs(a.Cj + cb + pos, col);
           if constexpr (SR::has_val) {
             __stcs(Cv + cb + pos, vals[col]);
@@ -930,7 +956,7 @@ __global__ void __launch_bounds__(NSPA_WPB * 32, 8) k_num_spa(NumArgs a) {
         }
       }
     }
-    for (int i = w0; i < w1; ++i) bits[i] = 0u;
+    for (int i = w0; i < w1; ++i) flag4[i] = 0u;
     if constexpr (SR::has_val)
       if (total != c)  // values left behind by a row that failed its check
         for (int i = lane; i < n; i += 32) vals[i] = SR::identity();

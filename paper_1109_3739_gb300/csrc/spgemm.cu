@@ -303,7 +303,7 @@ static bool numeric_supported(int sr, int adt, int bdt, int &out_dt) {
 
 // ----------------------------------------------------------------- tuning
 static std::mutex g_tune_mu;
-static const hs_tuning k_tune_default = {F_WARP_S, CAP_MID_S, 4096, F_MID_S, 0, F_SORT, 50};
+static const hs_tuning k_tune_default = {F_WARP_S, CAP_MID_S, 4096, F_MID_S, 0, F_SORT, 50, 0};
 static hs_tuning g_tune = k_tune_default;
 
 static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -323,6 +323,8 @@ BinCfg bin_config(int value_bytes) {
   b.sym_heavy_from = t.sym_heavy_from <= 0 ? b.cap_large : clampi(t.sym_heavy_from, F_MID, b.cap_large);
   b.sort_max = clampi(t.sort_max, F_TINY, F_SORT);
   b.sort_pct = clampi(t.sort_pct, 0, 101);
+  b.spa_max = clampi(t.spa_max, 0, SPA_COLS_4);
+  b.spa = 0;
   return b;
 }
 

@@ -100,28 +100,33 @@ __global__ void __launch_bounds__(WARP_WPB * 32, 4) k_sym_warp(SymArgs a) {
 }
 
 // ------------------------------------------------------------- dense SPA
-// Products whose B has at most SPA_COLS_4 columns: one warp per row sets a
-// bit per product in a bitmap of all n columns (the occupancy half of
-// Figure 1's sparse accumulator) and counts the set bits.
+// Products whose B has at most SPA_COLS_4 columns: one warp per row sets an
+// occupancy flag per product (a byte per column of all n columns, plain
+// stores: lanes that hit one column do not queue on an atomic) and counts
+// the flags (the occupancy half of Figure 1's sparse accumulator).
 constexpr int SPA_WPB = 8;
 __global__ void __launch_bounds__(SPA_WPB * 32) k_sym_spa(SymArgs a) {
-  __shared__ unsigned bits_all[SPA_WPB][SPA_COLS_4 / 32];
+  __shared__ unsigned flags_all[SPA_WPB][SPA_COLS_4 / 4];
   const int w = threadIdx.x >> 5, lane = lane_id();
-  unsigned *bits = bits_all[w];
+  unsigned *flag4 = flags_all[w];
+  unsigned char *flag = reinterpret_cast<unsigned char *>(flag4);
   const DevCsr A = dev_a(a.A), B = dev_b(a.B);
   const int n = (int)a.B.n;
-  const int words = (n + 31) >> 5;
+  const int fwords = (n + 3) >> 2;
+  for (int i = lane; i < fwords; i += 32) flag4[i] = 0u;
+  __syncwarp();
   for (int idx = blockIdx.x * SPA_WPB + w; idx < a.count; idx += gridDim.x * SPA_WPB) {
     const int r = a.list[idx];
     if (!HS_G(a.A.dbg, r >= 0 && r < a.A.nslots, 35, r)) continue;
-    for (int i = lane; i < words; i += 32) bits[i] = 0u;
-    __syncwarp();
     warp_products<StructSR>(A, B, A.p[r], A.p[r + 1], [&](int col, NoVal, int) {
-      if (HS_G(a.A.dbg, col >= 0 && col < n, 84, col)) atomicOr(bits + (col >> 5), 1u << (col & 31));
+      if (HS_G(a.A.dbg, col >= 0 && col < n, 84, col)) flag[col] = 1;
     });
     __syncwarp();
     int cnt = 0;
-    for (int i = lane; i < words; i += 32) cnt += __popc(bits[i]);
+    for (int i = lane; i < fwords; i += 32) {
+      cnt += __popc(flag4[i] & 0x01010101u);
+      flag4[i] = 0u;
+    }
     cnt = warp_sum(cnt);
     if (lane == 0) put_count(a, out_row(a.A, r), cnt);
     __syncwarp();

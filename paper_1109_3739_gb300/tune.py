@@ -27,6 +27,7 @@ CANDIDATES = {
     "sym_heavy_from": (4096, 6144, 0),
     "sort_pct": (101, 25, 50, 75, 90),
     "sort_max": (256, 512, 1024),
+    "spa_max": (0, 2048),
 }
 
 

@@ -1,7 +1,7 @@
 """The dense-accumulator tier (Figure 1's sparse accumulator as it stands: a
-value per column and an occupancy bitmap, one warp per row) serves products
-whose B has at most 2048 columns (1024 for 8-byte values): every row of more
-than 32 products takes it.  Against the CPU oracle for every semiring and
+value per column and an occupancy flag, one warp per row) serves, when the
+tuning's spa_max allows, products whose B has at most 2048 columns (1024 for
+8-byte values): every row of more than 32 products takes it.  Against the CPU oracle for every semiring and
 value type, at the tier's column limits and just past them, with a DCSR left
 operand, and a plan's numeric replay.  Structure
 bit-exact; values bit-exact for the exact semirings, within tol * sum |a||b|
@@ -31,7 +31,7 @@ def run(sr, A, B, dcsr=False):
     h = H()
     dA = h.DeviceCSR.from_host(A, dcsr=dcsr)
     dB = h.DeviceCSR.from_host(B)
-    h.set_tuning(None)
+    h.set_tuning({"spa_max": 2048})
     h.profile_enable(True)
     h.profile_reset()
     try:
@@ -39,6 +39,7 @@ def run(sr, A, B, dcsr=False):
         ran = {k for k, (_, launches) in h.profile_read().items() if launches > 0}
     finally:
         h.profile_enable(False)
+        h.set_tuning(None)
     return C, ran
 
 
@@ -93,8 +94,11 @@ def test_plan_replay():
     h = H()
     A, B = operands("f32", 1500, seed=5)
     dA, dB = h.DeviceCSR.from_host(A), h.DeviceCSR.from_host(B)
-    h.set_tuning(None)
-    P = h.Plan("plus_times", dA, dB)
+    h.set_tuning({"spa_max": 2048})
+    try:
+        P = h.Plan("plus_times", dA, dB)
+    finally:
+        h.set_tuning(None)
     try:
         ref = P.C.val.clone()
         P.C.val.zero_()
