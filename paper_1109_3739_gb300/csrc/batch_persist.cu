@@ -43,7 +43,7 @@ constexpr int BP_FMAX = 4096;                    // rows with more products are 
 constexpr int BP_NBUCK = 16;                     // column buckets of a row with more than BPC_CAP outputs
 constexpr int BP_REC = BP_NBUCK + 2;             // a bucket record: the counts, then the row's least and greatest column
 constexpr int BP_CH = 256;                       // A entries staged per round (CTA tier)
-constexpr int BP_CLAIM = 16;                     // warp rows a warp claims per atomic
+constexpr int BP_CLAIM = 4;                      // warp rows a warp claims per atomic
 
 // counters, zeroed before every execution
 struct BpCounters {
