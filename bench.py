@@ -73,7 +73,7 @@ def peaks():
 # to the value they had when it was taken; after any change there the field
 # is null until it is measured again.
 MEASURED_TRAFFIC = {"kernel": "numeric_heavy", "scale": 20, "bytes": 4.2235e9 * 24.415 / 2.6124,
-                    "measured_at_scale": 18, "csrc_sha256_16": "f6bfe8373b94ef15"}
+                    "measured_at_scale": 18, "heavy_part_kb": 16, "csrc_sha256_16": "f6bfe8373b94ef15"}
 KERNEL_SOURCES = ("analysis.cu", "common.cuh", "internal.h", "numeric.cuh", "numeric_pt.cu", "symbolic.cu")
 
 
@@ -968,7 +968,8 @@ def main():
     alg_bytes = a_bytes + b_bytes + c_bytes
     achieved = alg_bytes / (dom_ms / 1000.0) / 1e9
     mt = MEASURED_TRAFFIC
-    traffic = mt["bytes"] if (dom == mt["kernel"] and args.scale == mt["scale"]
+    part_kb = h.get_tuning().get("heavy_part_kb", 16)  # the setting the timed steps ran with
+    traffic = mt["bytes"] if (dom == mt["kernel"] and args.scale == mt["scale"] and part_kb == mt["heavy_part_kb"]
                               and csrc_hash() == mt["csrc_sha256_16"]) else None
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,

@@ -252,6 +252,9 @@ int hs_trim_memory(void);
  *                   than 32 products one warp's dense accumulator of all the
  *                   columns (Figure 1's SPA) instead of the tiers above
  *                   (0..2048; 0 = never)
+ *   heavy_part_kb   shared memory of values a column part of a heavy row
+ *                   holds: 16 (four CTAs per SM) or 32 (half the parts,
+ *                   three CTAs per SM); 16
  * Results do not depend on the thresholds.  hs_set_tuning(NULL) restores the
  * defaults (given last above).  Both calls return HS_OK (hs_get_tuning:
  * HS_EINVAL for NULL). */
@@ -259,6 +262,7 @@ typedef struct hs_tuning {
   int32_t warp_s_max, mid_s_max, large_s_max, sym_mid_s_max, sym_heavy_from;
   int32_t sort_max, sort_pct;
   int32_t spa_max;
+  int32_t heavy_part_kb;
 } hs_tuning;
 int hs_set_tuning(const hs_tuning *t);
 int hs_get_tuning(hs_tuning *t);

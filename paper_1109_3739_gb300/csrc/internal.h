@@ -70,6 +70,7 @@ struct BinCfg {
   int sort_max;        // numeric: rows with 32 < f <= this and 100*c >= sort_pct*f sort their products (32..1024)
   int sort_pct;        // (0..101; 101 switches the sort tiers off)
   int spa_max;         // products whose B has at most min(this, spa_cols()) columns take the dense tier (0: none)
+  int unit_kb;         // numeric heavy units hold this many KB of values (16 or 32)
   int spa;             // set per product: rows of more than 32 products take KEY_SPA
 };
 // Symbolic bins.  Every row that may end in the numeric heavy bin (c >
@@ -235,10 +236,11 @@ struct alignas(16) HeavyUnit {
 // outputs a heavy column part holds at most, by value width (the part's
 // values live in shared memory)
 inline int heavy_part_cap(int value_bytes) { return value_bytes == 8 ? 4096 : (value_bytes == 0 ? 16384 : 8192); }
-// the same for the unit kernel: 16 KB of values, and never less than one
-// segment's SEG_W columns (structure only: 2^16 outputs)
-inline int unit_part_cap(int value_bytes) {
-  return value_bytes == 0 ? 65536 : (16384 / value_bytes > SEG_W ? 16384 / value_bytes : SEG_W);
+// the same for the unit kernel: kb KB of values (16 or 32, the tuning's
+// heavy_part_kb), and never less than one segment's SEG_W columns (structure
+// only: 2^16 outputs)
+inline int unit_part_cap(int value_bytes, int kb = 16) {
+  return value_bytes == 0 ? 65536 : (kb * 1024 / value_bytes > SEG_W ? kb * 1024 / value_bytes : SEG_W);
 }
 // parts per heavy row (numeric heavy bin, in list order) into cnt[0..nmax),
 // 0 for rows without a sorted column list (loff < 0), and the room the row's
@@ -290,6 +292,7 @@ struct NumArgs {
   const int32_t *ppre;
   const void *paval;
   int pair_abytes;        // width of the left values the pairs carry (0: none)
+  int unit_kb;            // the units' value capacity in KB (16 or 32): which unit kernel runs
 };
 // kind: 0 tiny, 1 warp_s, 2 warp, 3 mid_s, 4 mid, 5 large_s, 6 large,
 // 7 sort_xs, 8 sort_s, 9 sort_m, 10 sort, 11 spa, 12 heavy (bin key

@@ -672,20 +672,20 @@ __global__ void __launch_bounds__(HV_NT, 2) k_num_heavy(NumArgs a) {
 // part's occupancy bitmap and word ranks; the products add their value at
 // rank(col) = wpre[word] + popcount(bits below col), spread evenly over the
 // warps by their prefix; the values leave in column order.  Parts span at
-// most 2^17 columns and hold 16 KB of values (a whole segment's 4096 for
-// 8-byte values), so four CTAs of 256 threads share an SM (three for 8-byte
-// values).
+// most 2^17 columns and hold KB kilobytes of values (16 or 32, at least a
+// whole segment's 4096 outputs), so four CTAs of 256 threads share an SM
+// with 16 KB parts (three for 8-byte values or 32 KB parts).
 constexpr int HU_NT = 256;
 constexpr int HU_WMAX = HU_SPAN_SEGS * SEG_W;
 constexpr int HU_WORDS = HU_WMAX / 32;
 constexpr int HU_PB = 384;  // B segments copied per batch
-// as unit_part_cap(): 16 KB of values, at least one segment's SEG_W outputs
-template <typename T> constexpr int unit_cap() {
-  return vbytes<T>() == 0 ? 65536 : (16384 / vbytes<T>() > SEG_W ? 16384 / vbytes<T>() : SEG_W);
+// as unit_part_cap(): KB kilobytes of values, at least one segment's SEG_W outputs
+template <typename T, int KB> constexpr int unit_cap() {
+  return vbytes<T>() == 0 ? 65536 : (KB * 1024 / vbytes<T>() > SEG_W ? KB * 1024 / vbytes<T>() : SEG_W);
 }
 
-template <typename T> struct UnitSmem {
-  static constexpr int CAP = vbytes<T>() ? unit_cap<T>() : 1;
+template <typename T, int KB> struct UnitSmem {
+  static constexpr int CAP = vbytes<T>() ? unit_cap<T, KB>() : 1;
   // the part's values; first the list slice lands here (4-byte column ids
   // plus the copy's 32 bytes of alignment room)
   static constexpr size_t VBYTES = ((size_t)CAP * (vbytes<T>() > 4 ? vbytes<T>() : 4) + 32 + 15) & ~(size_t)15;
@@ -699,11 +699,11 @@ template <typename T> struct UnitSmem {
   int unit;
 };
 
-template <class SR>
-__global__ void __launch_bounds__(HU_NT, 4) k_num_units(NumArgs a) {
+template <class SR, int KB>
+__global__ void __launch_bounds__(HU_NT, KB > 16 ? 3 : 4) k_num_units(NumArgs a) {
   using T = typename SR::val_t;
-  using L = UnitSmem<T>;
-  constexpr int CAP = unit_cap<T>();
+  using L = UnitSmem<T, KB>;
+  constexpr int CAP = unit_cap<T, KB>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto &sm = *reinterpret_cast<L *>(smem_raw);
   const DevCsr B = ndev_b(a.B);
@@ -991,6 +991,16 @@ template <class SR, int SLOTS, int CAP, int NT> void launch_num_cta(const NumArg
   k<<<ngrid_cap(a.count, 1, fit_per_sm(k, NT, L::bytes)), NT, L::bytes, st>>>(a);
 }
 
+template <class SR, int KB> void launch_num_units(const NumArgs &a, cudaStream_t st) {
+  using T = typename SR::val_t;
+  const size_t ub = sizeof(UnitSmem<T, KB>);
+  auto ku = k_num_units<SR, KB>;
+  set_smem_attr(ku, ub);
+  count_launch();
+  const int items = a.nunits < (1 << 30) ? (int)a.nunits : (1 << 30);
+  ku<<<ngrid_cap(items, 1, fit_per_sm(ku, HU_NT, ub)), HU_NT, ub, st>>>(a);
+}
+
 template <class SR> void launch_numeric_sr(int kind, const NumArgs &a, cudaStream_t st) {
   using T = typename SR::val_t;
   if (a.count <= 0) return;
@@ -1015,12 +1025,8 @@ template <class SR> void launch_numeric_sr(int kind, const NumArgs &a, cudaStrea
     case 11: launch_num_spa<SR>(a, st); break;
     case 12: {
       if (a.units && a.nunits > 0) {
-        const size_t ub = sizeof(UnitSmem<T>);
-        auto ku = k_num_units<SR>;
-        set_smem_attr(ku, ub);
-        count_launch();
-        const int items = a.nunits < (1 << 30) ? (int)a.nunits : (1 << 30);
-        ku<<<ngrid_cap(items, 1, fit_per_sm(ku, HU_NT, ub)), HU_NT, ub, st>>>(a);
+        if (a.unit_kb > 16) launch_num_units<SR, 32>(a, st);
+        else launch_num_units<SR, 16>(a, st);
       }
       if (!a.units || a.lists_partial) {  // rows without a list: one CTA per row
         const size_t bytes = sizeof(HeavySmem<T>);

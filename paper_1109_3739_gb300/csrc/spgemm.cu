@@ -303,7 +303,7 @@ static bool numeric_supported(int sr, int adt, int bdt, int &out_dt) {
 
 // ----------------------------------------------------------------- tuning
 static std::mutex g_tune_mu;
-static const hs_tuning k_tune_default = {F_WARP_S, CAP_MID_S, 4096, F_MID_S, 0, F_SORT, 50, 0};
+static const hs_tuning k_tune_default = {F_WARP_S, CAP_MID_S, 4096, F_MID_S, 0, F_SORT, 50, 0, 16};
 static hs_tuning g_tune = k_tune_default;
 
 static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -324,6 +324,7 @@ BinCfg bin_config(int value_bytes) {
   b.sort_max = clampi(t.sort_max, F_TINY, F_SORT);
   b.sort_pct = clampi(t.sort_pct, 0, 101);
   b.spa_max = clampi(t.spa_max, 0, SPA_COLS_4);
+  b.unit_kb = t.heavy_part_kb >= 32 ? 32 : 16;
   b.spa = 0;
   return b;
 }
@@ -614,7 +615,7 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
   // subset of the symbolic heavy rows, whose number bounds the count array
   int64_t *pcnt = nullptr, *pcap = nullptr;
   const int64_t nsh_rows = key_off[NKEYS] - key_off[KEY_HEAVY];
-  const int ucap = unit_part_cap(vb);
+  const int ucap = unit_part_cap(vb, bins.unit_kb);
   if (glist && nsh_rows > 0) {
     pcnt = mem.tmp<int64_t>((size_t)nsh_rows);
     pcap = pcnt ? mem.tmp<int64_t>((size_t)nsh_rows) : nullptr;
@@ -718,6 +719,7 @@ static int spgemm_impl(int sr, const hs_mat *A, const hs_mat *B, hs_mat *C, Mem 
   na.ppre = ppre;
   na.paval = paval;
   na.pair_abytes = a_bytes;
+  na.unit_kb = bins.unit_kb;
   const char *names[NUM_KINDS] = {"numeric_tiny",   "numeric_warp_s", "numeric_warp",   "numeric_mid_s",
                                   "numeric_mid",    "numeric_large_s", "numeric_large", "numeric_sort_xs",
                                   "numeric_sort_s", "numeric_sort_m",  "numeric_sort",  "numeric_spa",

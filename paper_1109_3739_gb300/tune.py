@@ -28,6 +28,7 @@ CANDIDATES = {
     "sort_pct": (101, 25, 50, 75, 90),
     "sort_max": (256, 512, 1024),
     "spa_max": (0, 2048),
+    "heavy_part_kb": (16, 32),
 }
 
 

@@ -19,7 +19,7 @@ SETTINGS = [
     {"warp_s_max": 32, "mid_s_max": 0, "large_s_max": 2048, "sym_mid_s_max": 512, "sym_heavy_from": 0,
      "sort_max": 1024, "sort_pct": 0},
     {"warp_s_max": 64, "mid_s_max": 768, "large_s_max": 3072, "sym_mid_s_max": 768, "sym_heavy_from": 4096,
-     "sort_max": 256, "sort_pct": 75},
+     "sort_max": 256, "sort_pct": 75, "heavy_part_kb": 32},
     {"warp_s_max": 128, "mid_s_max": 512, "large_s_max": 4096, "sym_mid_s_max": 1024, "sym_heavy_from": 6144,
      "sort_max": 1024, "sort_pct": 101},
 ]
@@ -85,5 +85,29 @@ def test_out_of_range_thresholds_are_clamped():
         assert torch.equal(C.rowptr, ref.rowptr) and torch.equal(C.col, ref.col)
         R, bound = oracle.spgemm("plus_times", A, A, with_bound=True, nthreads=NT)
         assert_within(C.to_host(), R, bound, "f32", "clamped thresholds")
+    finally:
+        h.set_tuning(None)
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64", "bool"])
+def test_heavy_parts_of_32_kb(dt):
+    """Heavy rows (R-MAT scale 16) cut into column parts of 32 KB of values:
+    half the units of the 16 KB parts, the same result."""
+    import torch
+    h = H()
+    A = I.rmat_matrix(16, 8, seed=4, dtype=dt)
+    sr = "or_and" if dt == "bool" else "plus_times"
+    dA = h.DeviceCSR.from_host(A)
+    h.set_tuning(None)
+    ref = h.spgemm(sr, dA, dA)
+    try:
+        h.set_tuning({"heavy_part_kb": 32})
+        C = h.spgemm(sr, dA, dA, validate=True)
+        assert torch.equal(C.rowptr, ref.rowptr) and torch.equal(C.col, ref.col)
+        if sr == "plus_times":
+            R, bound = oracle.spgemm(sr, A, A, with_bound=True, nthreads=NT)
+            assert_within(C.to_host(), R, bound, dt, "32 KB parts")
+        else:
+            assert_bitexact(C.to_host(), oracle.spgemm(sr, A, A, nthreads=NT), "32 KB parts")
     finally:
         h.set_tuning(None)
