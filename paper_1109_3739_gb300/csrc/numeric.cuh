@@ -678,7 +678,7 @@ __global__ void __launch_bounds__(HV_NT, 2) k_num_heavy(NumArgs a) {
 constexpr int HU_NT = 256;
 constexpr int HU_WMAX = HU_SPAN_SEGS * SEG_W;
 constexpr int HU_WORDS = HU_WMAX / 32;
-constexpr int HU_PB = 384;  // B segments copied per batch
+constexpr int HU_PB = 256;  // B segments copied per batch
 // as unit_part_cap(): KB kilobytes of values, at least one segment's SEG_W outputs
 template <typename T, int KB> constexpr int unit_cap() {
   return vbytes<T>() == 0 ? 65536 : (KB * 1024 / vbytes<T>() > SEG_W ? KB * 1024 / vbytes<T>() : SEG_W);
@@ -700,7 +700,7 @@ template <typename T, int KB> struct UnitSmem {
 };
 
 template <class SR, int KB>
-__global__ void __launch_bounds__(HU_NT, KB > 16 ? 3 : 4) k_num_units(NumArgs a) {
+__global__ void __launch_bounds__(HU_NT, (KB > 16 || vbytes<typename SR::val_t>() == 8) ? 3 : 5) k_num_units(NumArgs a) {
   using T = typename SR::val_t;
   using L = UnitSmem<T, KB>;
   constexpr int CAP = unit_cap<T, KB>();
