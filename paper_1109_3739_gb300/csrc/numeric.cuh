@@ -673,8 +673,8 @@ __global__ void __launch_bounds__(HV_NT, 2) k_num_heavy(NumArgs a) {
 // rank(col) = wpre[word] + popcount(bits below col), spread evenly over the
 // warps by their prefix; the values leave in column order.  Parts span at
 // most 2^17 columns and hold KB kilobytes of values (16 or 32, at least a
-// whole segment's 4096 outputs), so four CTAs of 256 threads share an SM
-// with 16 KB parts (three for 8-byte values or 32 KB parts).
+// whole segment's 4096 outputs), so five CTAs of 256 threads share an SM
+// with 16 KB parts (48 registers; three for 8-byte values or 32 KB parts).
 constexpr int HU_NT = 256;
 constexpr int HU_WMAX = HU_SPAN_SEGS * SEG_W;
 constexpr int HU_WORDS = HU_WMAX / 32;
