@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(1024, 1) k_sym_heavy(SymArgs a) {
               }
             }
             __syncwarp();
-            for (int i = lane; i < tot; i += 32) lst[at0 + i] = buf[i];
+            for (int i = lane; i < tot; i += 32) __stcs(lst + at0 + i, buf[i]);  // evict-first: B stays in L2
             __syncwarp();
           } else {  // dense segments: each lane's columns are one long run
             int64_t at = at0 + incl - pcl;
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(1024, 1) k_sym_heavy(SymArgs a) {
             for (int q = 0; q < 4; ++q) {
               unsigned long long bb = b[q];
               while (bb) {
-                lst[at++] = cbase + 64 * q + __ffsll(bb) - 1;
+                __stcs(lst + at++, cbase + 64 * q + __ffsll(bb) - 1);
                 bb &= bb - 1;
               }
             }
