@@ -616,9 +616,11 @@ __global__ void k_build_pairs(RowSet A, RightOp B, HeavyUnit *units, int64_t nun
       const int incl = warp_incl_scan(len);
       if (len > 0) {
         const int64_t at = u.poff + out + __popc(m & ((1u << lane) - 1u));
-        pstart[at] = s0;
-        ppre[at] = (int32_t)(prod + incl - len);
-        if constexpr (AB > 0) reinterpret_cast<VT *>(paval)[at] = av;
+        // evict-first: the pairs are read once, later; B and the segment
+        // index stay in L2 for this kernel and the unit kernel after it
+        __stcs(reinterpret_cast<long long *>(pstart) + at, (long long)s0);
+        __stcs(ppre + at, (int32_t)(prod + incl - len));
+        if constexpr (AB > 0) __stcs(reinterpret_cast<VT *>(paval) + at, av);
       }
       out += __popc(m);
       prod += __shfl_sync(FULL, incl, 31);
