@@ -940,10 +940,14 @@ def main():
     ms_ = min(max(t["mid_s_max"], 0), 1024)
     ls = min(max(t["large_s_max"], 2048), cap_large // 2)
     sms = min(max(t["sym_mid_s_max"], 512), 1024)
-    shf = cap_large if t["sym_heavy_from"] <= 0 else min(max(t["sym_heavy_from"], 4096), cap_large)
+    # (0: the library's automatic choice for 4-byte values)
+    shf = 4096 if t["sym_heavy_from"] <= 0 else min(max(t["sym_heavy_from"], 4096), cap_large)
+    nhf = 2048 if t.get("num_heavy_from", 0) <= 0 else min(max(t["num_heavy_from"], 2048), cap_large)
     big = (f > 512) & (cnt > 0)
+    heavy = big & ((cnt > cap_large) | ((cnt > nhf) & (f > shf)))
+    big = big & ~heavy
     in_bin = {
-        "numeric_heavy": big & (cnt > cap_large),
+        "numeric_heavy": heavy,
         "numeric_large": big & (cnt > ls) & (cnt <= cap_large),
         "numeric_large_s": big & (cnt > 2048) & (cnt <= ls),
         "numeric_mid": big & (cnt > ms_) & (cnt <= 2048),

@@ -241,7 +241,8 @@ int hs_trim_memory(void);
  *                   8192 (512..1024; 1024)
  *   sym_heavy_from  symbolic rows with f > sym_heavy_from take the bitmap
  *                   kernel that also writes their sorted column lists
- *                   (4096..large capacity; 0 = the large capacity)
+ *                   (4096..large capacity; 0 = automatic: 4096 for 4-byte
+ *                   values and bool, the large capacity for 8-byte)
  *   sort_max        numeric rows with 32 < f <= sort_max whose output count
  *   sort_pct        c is at least sort_pct percent of f sort their products
  *                   in a warp's registers (expand, sort, compress) instead of
@@ -255,6 +256,11 @@ int hs_trim_memory(void);
  *   heavy_part_kb   shared memory of values a column part of a heavy row
  *                   holds: 16 (four CTAs per SM) or 32 (half the parts,
  *                   three CTAs per SM); 16
+ *   num_heavy_from  numeric rows with more than num_heavy_from outputs whose
+ *                   structure came from the bitmap kernel (f > sym_heavy_from)
+ *                   take the column-part units instead of a CTA hash table
+ *                   (2048..large capacity; 0 = automatic: 2048 for 4-byte
+ *                   values and bool, the large capacity for 8-byte)
  * Results do not depend on the thresholds.  hs_set_tuning(NULL) restores the
  * defaults (given last above).  Both calls return HS_OK (hs_get_tuning:
  * HS_EINVAL for NULL). */
@@ -263,6 +269,7 @@ typedef struct hs_tuning {
   int32_t sort_max, sort_pct;
   int32_t spa_max;
   int32_t heavy_part_kb;
+  int32_t num_heavy_from;
 } hs_tuning;
 int hs_set_tuning(const hs_tuning *t);
 int hs_get_tuning(hs_tuning *t);

@@ -302,8 +302,9 @@ __global__ void k_scatter_sym(RowSet A, const int64_t *f, int *key_cur, int *lis
     const int64_t fr = f[r];
     const int key = sym_key(fr, bins);
     if (key) append_row(key, (int)r, key_cur, list, A.nslots, A.dbg);
-    // rows that may need column parts in the numeric pass get a histogram slot
-    const bool h = fr > bins.cap_large;
+    // rows that may need column parts in the numeric pass (every row of the
+    // bitmap kernel) get a histogram slot
+    const bool h = fr > bins.sym_heavy_from;
     const unsigned act = __activemask();
     const unsigned hm = __ballot_sync(act, h);
     int base = 0;

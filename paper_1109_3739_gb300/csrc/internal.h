@@ -71,6 +71,7 @@ struct BinCfg {
   int sort_pct;        // (0..101; 101 switches the sort tiers off)
   int spa_max;         // products whose B has at most min(this, spa_cols()) columns take the dense tier (0: none)
   int unit_kb;         // numeric heavy units hold this many KB of values (16 or 32)
+  int num_heavy_from;  // numeric: rows with c > this that took the bitmap kernel go to the units (2048..cap_large)
   int spa;             // set per product: rows of more than 32 products take KEY_SPA
 };
 // Symbolic bins.  Every row that may end in the numeric heavy bin (c >
@@ -96,6 +97,7 @@ __host__ __device__ inline int num_key(int64_t f, int64_t c, const BinCfg &b) {
     return f <= F_SORT_XS ? KEY_SORT_XS : (f <= F_SORT_S ? KEY_SORT_S : (f <= F_SORT_M ? KEY_SORT_M : KEY_SORT));
   if (f <= b.warp_s_max) return KEY_WARP_S;
   if (f <= F_WARP) return KEY_WARP;
+  if (c > b.num_heavy_from && f > b.sym_heavy_from) return heavy_key(f);  // a sorted list exists
   if (c <= b.mid_s_max) return KEY_MID_S;
   if (c <= CAP_MID) return KEY_MID;
   if (c <= b.large_s_max) return KEY_LARGE_S;

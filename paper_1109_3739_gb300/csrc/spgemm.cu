@@ -303,7 +303,7 @@ static bool numeric_supported(int sr, int adt, int bdt, int &out_dt) {
 
 // ----------------------------------------------------------------- tuning
 static std::mutex g_tune_mu;
-static const hs_tuning k_tune_default = {F_WARP_S, CAP_MID_S, 4096, F_MID_S, 0, F_SORT, 50, 0, 16};
+static const hs_tuning k_tune_default = {F_WARP_S, CAP_MID_S, 4096, F_MID_S, 0, F_SORT, 50, 0, 16, 0};
 static hs_tuning g_tune = k_tune_default;
 
 static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -320,11 +320,18 @@ BinCfg bin_config(int value_bytes) {
   b.mid_s_max = clampi(t.mid_s_max, 0, CAP_MID_S);
   b.large_s_max = clampi(t.large_s_max, CAP_MID, b.cap_large / 2 > CAP_MID ? b.cap_large / 2 : CAP_MID);
   b.sym_mid_s_max = clampi(t.sym_mid_s_max, F_WARP, F_MID_S);
-  b.sym_heavy_from = t.sym_heavy_from <= 0 ? b.cap_large : clampi(t.sym_heavy_from, F_MID, b.cap_large);
+  // 0: automatic.  With 4-byte values and bool, rows of more than 4096
+  // products take the bitmap kernel and rows of more than 2048 outputs among
+  // them the units (R-MAT scale 20: 77.8 ms against 79.0 ms with both at the
+  // large capacity); 8-byte values keep the large capacity
+  const bool narrow = value_bytes <= 4;
+  b.sym_heavy_from = t.sym_heavy_from <= 0 ? (narrow ? F_MID : b.cap_large) : clampi(t.sym_heavy_from, F_MID, b.cap_large);
   b.sort_max = clampi(t.sort_max, F_TINY, F_SORT);
   b.sort_pct = clampi(t.sort_pct, 0, 101);
   b.spa_max = clampi(t.spa_max, 0, SPA_COLS_4);
   b.unit_kb = t.heavy_part_kb >= 32 ? 32 : 16;
+  b.num_heavy_from =
+      t.num_heavy_from <= 0 ? (narrow ? CAP_MID : b.cap_large) : clampi(t.num_heavy_from, CAP_MID, b.cap_large);
   b.spa = 0;
   return b;
 }

@@ -50,7 +50,8 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void
 class hs_tuning(ctypes.Structure):
     _fields_ = [("warp_s_max", ctypes.c_int32), ("mid_s_max", ctypes.c_int32), ("large_s_max", ctypes.c_int32),
                 ("sym_mid_s_max", ctypes.c_int32), ("sym_heavy_from", ctypes.c_int32), ("sort_max", ctypes.c_int32),
-                ("sort_pct", ctypes.c_int32), ("spa_max", ctypes.c_int32), ("heavy_part_kb", ctypes.c_int32)]
+                ("sort_pct", ctypes.c_int32), ("spa_max", ctypes.c_int32), ("heavy_part_kb", ctypes.c_int32),
+                ("num_heavy_from", ctypes.c_int32)]
 
 
 TUNING_FIELDS = tuple(name for name, _ in hs_tuning._fields_)

@@ -24,11 +24,12 @@ CANDIDATES = {
     "mid_s_max": (0, 512, 768, 1024),
     "large_s_max": (2048, 3072, 4096),
     "sym_mid_s_max": (512, 768, 1024),
-    "sym_heavy_from": (4096, 6144, 0),
+    "sym_heavy_from": (0, 6144, 8192),
     "sort_pct": (101, 25, 50, 75, 90),
     "sort_max": (256, 512, 1024),
     "spa_max": (0, 2048),
     "heavy_part_kb": (16, 32),
+    "num_heavy_from": (0, 4096, 8192),
 }
 
 

@@ -54,7 +54,7 @@ def test_tuning_round_trip_without_gpu():
     H.set_tuning(None)
     d = H.get_tuning()
     assert d == {"warp_s_max": 128, "mid_s_max": 1024, "large_s_max": 4096, "sym_mid_s_max": 1024,
-                 "sym_heavy_from": 0, "sort_max": 1024, "sort_pct": 50, "spa_max": 0, "heavy_part_kb": 16}
+                 "sym_heavy_from": 0, "sort_max": 1024, "sort_pct": 50, "spa_max": 0, "heavy_part_kb": 16, "num_heavy_from": 0}
     H.set_tuning({"mid_s_max": 512, "sym_heavy_from": 6144})
     d2 = H.get_tuning()
     assert d2["mid_s_max"] == 512 and d2["sym_heavy_from"] == 6144 and d2["warp_s_max"] == 128

@@ -21,7 +21,9 @@ SETTINGS = [
     {"warp_s_max": 64, "mid_s_max": 768, "large_s_max": 3072, "sym_mid_s_max": 768, "sym_heavy_from": 4096,
      "sort_max": 256, "sort_pct": 75, "heavy_part_kb": 32},
     {"warp_s_max": 128, "mid_s_max": 512, "large_s_max": 4096, "sym_mid_s_max": 1024, "sym_heavy_from": 6144,
-     "sort_max": 1024, "sort_pct": 101},
+     "sort_max": 1024, "sort_pct": 101, "num_heavy_from": 2048},
+    {"sym_heavy_from": 4096, "num_heavy_from": 2048, "heavy_part_kb": 16},
+    {"sym_heavy_from": 8192, "num_heavy_from": 8192},
 ]
 
 

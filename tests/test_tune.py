@@ -9,7 +9,7 @@ def test_coordinate_descent_picks_each_knobs_best(monkeypatch):
 
     # a separable cost: the best value of each knob is known
     want = {"warp_s_max": 64, "mid_s_max": 768, "large_s_max": 4096, "sym_mid_s_max": 512,
-            "sym_heavy_from": 6144, "sort_max": 512, "sort_pct": 75, "spa_max": 2048, "heavy_part_kb": 32}
+            "sym_heavy_from": 6144, "sort_max": 512, "sort_pct": 75, "spa_max": 2048, "heavy_part_kb": 32, "num_heavy_from": 4096}
 
     def fake_time(run, trials, stream=None):
         t = h.get_tuning()
@@ -22,7 +22,8 @@ def test_coordinate_descent_picks_each_knobs_best(monkeypatch):
         assert h.get_tuning() == want            # left set
         assert log[0][0] == {"warp_s_max": 128, "mid_s_max": 1024, "large_s_max": 4096,
                              "sym_mid_s_max": 1024, "sym_heavy_from": 0, "sort_max": 1024,
-                             "sort_pct": 50, "spa_max": 0, "heavy_part_kb": 16}  # the defaults first
+                             "sort_pct": 50, "spa_max": 0, "heavy_part_kb": 16,
+                             "num_heavy_from": 0}  # the defaults first
         # one timing for the defaults, then every other candidate once
         n_other = sum(len(v) - 1 for v in tune.CANDIDATES.values())
         assert len(log) == 1 + n_other
