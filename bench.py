@@ -65,15 +65,16 @@ def peaks():
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch
 # of the dominant kernel: ncu's one-pass counters for k_num_units at R-MAT
-# scale 18 (4.2183 GB per launch, three launches within 0.05 percent), scaled
-# to scale 20 by the ratio of the launch's algorithmic bytes (24.415 / 2.6124
-# GB); the command and counters are summarised under profiles/.  It is
+# scale 18 (5.3628 GB per launch, three launches within 0.05 percent), scaled
+# to scale 20 by the ratio of the launch's algorithmic bytes (26.438 / 3.3377
+# GB: the rows of the numeric heavy bin, with the default routing of 4-byte
+# values); the command and counters are summarised under profiles/.  It is
 # reported only while the device sources of that kernel and of the kernels
 # that write its inputs (bins, lists, units, pairs, segment index) still hash
-# to the value they had when it was taken; after any change there the field
-# is null until it is measured again.
-MEASURED_TRAFFIC = {"kernel": "numeric_heavy", "scale": 20, "bytes": 4.2183e9 * 24.415 / 2.6124,
-                    "measured_at_scale": 18, "heavy_part_kb": 16, "csrc_sha256_16": "32576ee20002875d"}
+# to the value they had when it was taken, and only for the part capacity it
+# was taken with; otherwise the field is null until it is measured again.
+MEASURED_TRAFFIC = {"kernel": "numeric_heavy", "scale": 20, "bytes": 5.3628e9 * 26.438 / 3.3377,
+                    "measured_at_scale": 18, "heavy_part_kb": 16, "csrc_sha256_16": "8b7bc73a9d55609c"}
 KERNEL_SOURCES = ("analysis.cu", "common.cuh", "internal.h", "numeric.cuh", "numeric_pt.cu", "symbolic.cu")
 
 
