@@ -362,9 +362,10 @@ int hs_batch_plan_phase_ms(hs_batch_plan *plan, double *ms, void *stream);
  * library, which every GPU that loads the library holds until the process
  * exits; host-side readbacks use ordinary host memory.
  *   - HS_ESCRATCH: the product needs more scratch than the maximum (roughly
- *     16 bytes per row of A, plus 4 bytes per 4096 columns for every row with
- *     more than 4096 (8-byte values) or 8192 (other types) products and 8
- *     bytes per entry of A when such rows exist); nothing is written but
+ *     16 bytes per row of A, plus 4 bytes per 4096 columns for every row of
+ *     the symbolic bitmap kernel (more than sym_heavy_from products: 4096 by
+ *     default) and 8 bytes per entry of A when such rows exist); nothing is
+ *     written but
  *     C->ptr, and C->nnz is 0.
  *   - HS_EINVAL: besides the checks of hs_spgemm, a missing A->ptr or B->ptr
  *     (operand with rows), A->idx or B->idx (operand with entries), C->ptr,
