@@ -180,7 +180,13 @@ __global__ void __launch_bounds__(NT) k_sym_cta(SymArgs a) {
 // on the step's word l, so each step's columns also run in lane order and
 // gather in the buffer (per-lane stores of the long runs measured 2.3 ms
 // slower on R-MAT scale 20).
-constexpr int SH_SEGS = BITMAP_COLS / SEG_W;  // segments per chunk (256)
+constexpr int SH_COLS = BITMAP_COLS;          // columns per chunk (one bitmap)
+constexpr int SH_SEGS = SH_COLS / SEG_W;      // segments per chunk (256)
+constexpr int SH_NT = 1024;                   // threads of the heavy symbolic CTA
+constexpr int SH_WARPS = SH_NT / 32;
+constexpr int SH_PPW = SH_SEGS / 2 / SH_WARPS;  // segment pairs per warp (4)
+constexpr int SH_MINB = 1;                    // CTAs per SM the registers are sized for
+static_assert(SH_PPW * SH_WARPS * 2 == SH_SEGS, "the warps' pairs cover a chunk's segments");
 constexpr int SH_BUF = 384;                   // per-warp list staging entries
 static_assert(SEG_W == 4096, "two segments are 256 words: eight per lane");
 
@@ -205,12 +211,10 @@ struct SymHeavySmem {
   int row;
   long long loff;        // the row's list in the pool, or -1
   int scnt[SH_SEGS + 1];  // new columns per segment of the chunk, then their exclusive scan
-  int wbuf[32][SH_BUF];
-  alignas(16) unsigned bitmap[BITMAP_COLS / 32];
+  int wbuf[SH_WARPS][SH_BUF];
+  alignas(16) unsigned bitmap[SH_COLS / 32];
 };
 
-constexpr int SH_NT = 1024;                      // threads of the heavy symbolic CTA
-constexpr int SH_PPW = SH_SEGS / 2 / (SH_NT / 32);  // segment pairs per warp (4)
 
 // The eight bitmap words of a lane in a segment pair (words w0 .. w0 + 7),
 // zero past the chunk's last word.
@@ -240,18 +244,18 @@ __device__ __forceinline__ void sh_clear8(unsigned *bitmap, int w0, int words) {
   }
 }
 
-__global__ void __launch_bounds__(SH_NT, 1) k_sym_heavy(SymArgs a) {
+__global__ void __launch_bounds__(SH_NT, SH_MINB) k_sym_heavy(SymArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto &sm = *reinterpret_cast<SymHeavySmem *>(smem_raw);
   const DevCsr A = dev_a(a.A), B = dev_b(a.B);
   const int64_t n = a.B.n;
-  const int nchunk = (int)((n + BITMAP_COLS - 1) / BITMAP_COLS);
-  const int lane = lane_id(), warp = threadIdx.x >> 5, nw = SH_NT / 32;
+  const int nchunk = (int)((n + SH_COLS - 1) / SH_COLS);
+  const int lane = lane_id(), warp = threadIdx.x >> 5, nw = SH_WARPS;
   int *buf = sm.wbuf[warp];
   // the first chunk is the widest: clearing its words once leaves the whole
   // bitmap empty, and every chunk clears the words it read afterwards
   {
-    const int words0 = (int)((min(n, (int64_t)BITMAP_COLS) + 31) >> 5);
+    const int words0 = (int)((min(n, (int64_t)SH_COLS) + 31) >> 5);
     for (int wd = threadIdx.x; wd < words0; wd += SH_NT) sm.bitmap[wd] = 0u;
   }
   while (true) {
@@ -281,8 +285,8 @@ __global__ void __launch_bounds__(SH_NT, 1) k_sym_heavy(SymArgs a) {
     const int64_t lmax = r_ok ? min(a.f[r], n) : 0;  // the list's room
     int64_t written = 0;  // columns of the earlier chunks
     for (int ch = 0; ch < (r_ok ? nchunk : 0); ++ch) {
-      const int lo = ch * BITMAP_COLS;
-      const int hi = (int)min((int64_t)lo + BITMAP_COLS, n);
+      const int lo = ch * SH_COLS;
+      const int hi = (int)min((int64_t)lo + SH_COLS, n);
       const int words = (hi - lo + 31) >> 5;
       const int nsc = (hi - lo + SEG_W - 1) / SEG_W;
       cta_products<StructSR, CH, 4>(A, B, A.p[r], A.p[r + 1], nchunk > 1, lo, hi, sm.ex, sm.wtmp,
@@ -333,14 +337,25 @@ __global__ void __launch_bounds__(SH_NT, 1) k_sym_heavy(SymArgs a) {
           if (!HS_G(a.A.dbg, at0 + tot <= lmax, 34, at0 + tot)) {
             // nothing is written; the words are still cleared below
           } else if (tot <= SH_BUF) {
-            int p = incl - pcl;
+            // the lane's columns one per iteration over all eight words (the
+            // warp runs as many iterations as its fullest lane has columns);
+            // the next non-empty word is read again when the current one is spent
+            unsigned m = 0u;  // the lane's non-empty words
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              unsigned long long bb = b[q];
-              while (bb) {
-                buf[p++] = cbase + 64 * q + __ffsll(bb) - 1;
-                bb &= bb - 1;
+            for (int q = 0; q < 4; ++q)
+              m |= ((unsigned)((unsigned)b[q] != 0u) << (2 * q)) | ((unsigned)((unsigned)(b[q] >> 32) != 0u) << (2 * q + 1));
+            int p = incl - pcl;
+            unsigned cur = 0u;
+            int cw = 0;
+            for (int k = 0; k < pcl; ++k) {
+              if (cur == 0u) {
+                const int j = __ffs(m) - 1;
+                m &= m - 1;
+                cur = sm.bitmap[wb + j];
+                cw = cbase + 32 * j;
               }
+              buf[p++] = cw + __ffs(cur) - 1;
+              cur &= cur - 1;
             }
             __syncwarp();
             for (int i2 = lane; i2 < tot; i2 += 32) __stcs(lst + at0 + i2, buf[i2]);  // evict-first: B stays in L2
@@ -452,10 +467,10 @@ void launch_sym_heavy(const SymArgs &a, cudaStream_t st) {
   if (a.count <= 0) return;
   const int64_t words = (a.B.n + 31) / 32;
   const size_t bytes = offsetof(SymHeavySmem, bitmap) +
-                       sizeof(unsigned) * (size_t)(words < BITMAP_COLS / 32 ? words : BITMAP_COLS / 32);
+                       sizeof(unsigned) * (size_t)(words < SH_COLS / 32 ? words : SH_COLS / 32);
   set_smem_attr(k_sym_heavy, sizeof(SymHeavySmem));
   count_launch();
-  k_sym_heavy<<<grid_cap(a.count, 1, 1), SH_NT, bytes, st>>>(a);
+  k_sym_heavy<<<grid_cap(a.count, 1, fit_per_sm(k_sym_heavy, SH_NT, bytes)), SH_NT, bytes, st>>>(a);
 }
 
 }  // namespace hs
