@@ -166,7 +166,8 @@ __device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
 }
 
 // Exclusive scan of a[0..n) in shared memory by a whole group; returns the
-// total.  tmp needs 33 ints (CTA groups only).
+// total.  tmp needs 32 ints (CTA groups only); the closing barrier also ends
+// every read of tmp.
 template <class G> __device__ int group_excl_scan(int *a, int n, int *tmp) {
   const int gs = G::size(), r = G::rank();
   const int per = (n + gs - 1) / gs;
@@ -178,17 +179,14 @@ template <class G> __device__ int group_excl_scan(int *a, int n, int *tmp) {
   if (G::nwarps() == 1) {
     total = __shfl_sync(FULL, incl, 31);
   } else {
+    // the warp totals are published once and every warp scans them itself
+    // (nwarps <= 32), so one barrier separates the two levels
     if (lane_id() == 31) tmp[G::warp()] = incl;
     G::sync();
-    if (G::warp() == 0) {
-      int w = lane_id() < G::nwarps() ? tmp[lane_id()] : 0;
-      int wi = warp_incl_scan(w);
-      if (lane_id() < G::nwarps()) tmp[lane_id()] = wi - w;
-      if (lane_id() == 31) tmp[32] = wi;  // total (nwarps <= 32)
-    }
-    G::sync();
-    incl += tmp[G::warp()];
-    total = tmp[32];
+    const int w = lane_id() < G::nwarps() ? tmp[lane_id()] : 0;
+    const int wi = warp_incl_scan(w);
+    total = __shfl_sync(FULL, wi, 31);
+    incl += __shfl_sync(FULL, wi - w, G::warp());
   }
   int run = incl - s;
   for (int i = b; i < e; ++i) {
@@ -575,11 +573,10 @@ __device__ __forceinline__ void cta_products(const DevCsr &A, const DevCsr &B, i
       sm.excl[e] = (int)(en - s);
       sm.sbeg[e] = s;
     }
+    if (tid == 0) sm.excl[n] = 0;  // scanned with the entries, it becomes the round's total
     __syncthreads();
     // only the staged entries are scanned (a short row costs what it holds)
-    const int total = group_excl_scan<CtaGroup>(sm.excl, n, wtmp);
-    if (tid == 0) sm.excl[n] = total;
-    __syncthreads();
+    const int total = group_excl_scan<CtaGroup>(sm.excl, n + 1, wtmp);
     cta_expand_staged<SR, U, 32>(B, sm.sbeg, sm.excl, sm.aval, n, total, visit);
     __syncthreads();
   }

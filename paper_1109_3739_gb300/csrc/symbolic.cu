@@ -210,7 +210,7 @@ struct SymHeavySmem {
   int wtmp[33];
   int row;
   long long loff;        // the row's list in the pool, or -1
-  int scnt[SH_SEGS + 1];  // new columns per segment of the chunk, then their exclusive scan
+  int scnt[SH_SEGS + 1];  // new columns per segment of the chunk, then their exclusive scan and total
   int wbuf[SH_WARPS][SH_BUF];
   alignas(16) unsigned bitmap[SH_COLS / 32];
 };
@@ -316,10 +316,28 @@ __global__ void __launch_bounds__(SH_NT, SH_MINB) k_sym_heavy(SymArgs a) {
         }
       }
       __syncthreads();
-      if (hist)
-        for (int g = threadIdx.x; g < nsc; g += SH_NT)
-          if (HS_G(a.A.dbg, lo / SEG_W + g < a.nseg, 32, g)) hist[lo / SEG_W + g] = (uint32_t)sm.scnt[g];
-      const int ctotal = group_excl_scan<CtaGroup>(sm.scnt, nsc, sm.wtmp);
+      // one warp: the counts out to the segment histogram, then their
+      // exclusive scan (at most eight per lane), the chunk's total in the last slot
+      if (warp == 0) {
+        const int per = (nsc + 31) / 32;
+        const int gb = min(nsc, lane * per), ge = min(nsc, gb + per);
+        int cs = 0;
+        for (int g = gb; g < ge; ++g) {
+          const int c = sm.scnt[g];
+          cs += c;
+          if (hist && HS_G(a.A.dbg, lo / SEG_W + g < a.nseg, 32, g)) hist[lo / SEG_W + g] = (uint32_t)c;
+        }
+        const int ci = warp_incl_scan(cs);
+        int run = ci - cs;
+        for (int g = gb; g < ge; ++g) {
+          const int c = sm.scnt[g];
+          sm.scnt[g] = run;
+          run += c;
+        }
+        if (lane == 31) sm.scnt[SH_SEGS] = ci;
+      }
+      __syncthreads();
+      const int ctotal = sm.scnt[SH_SEGS];
       // list: the same pairs, read again
       if (lst) {
 #pragma unroll
