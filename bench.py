@@ -942,7 +942,7 @@ def main():
     ls = min(max(t["large_s_max"], 2048), cap_large // 2)
     sms = min(max(t["sym_mid_s_max"], 512), 1024)
     # (0: the library's automatic choice for 4-byte values)
-    shf = 4096 if t["sym_heavy_from"] <= 0 else min(max(t["sym_heavy_from"], 4096), cap_large)
+    shf = 4096 if t["sym_heavy_from"] <= 0 else min(max(t["sym_heavy_from"], 2048), cap_large)
     nhf = 2048 if t.get("num_heavy_from", 0) <= 0 else min(max(t["num_heavy_from"], 2048), cap_large)
     big = (f > 512) & (cnt > 0)
     heavy = big & ((cnt > cap_large) | ((cnt > nhf) & (f > shf)))
@@ -958,7 +958,7 @@ def main():
         "numeric_tiny": (f > 0) & (f <= 32),
         "symbolic_heavy": f > shf,
         "symbolic_large": (f > 4096) & (f <= shf),
-        "symbolic_mid": (f > sms) & (f <= 4096),
+        "symbolic_mid": (f > sms) & (f <= min(4096, shf)),
         "symbolic_mid_s": (f > 512) & (f <= sms),
         "symbolic_warp": (f > 32) & (f <= 512),
         "symbolic_tiny": (f > 0) & (f <= 32),

@@ -241,7 +241,7 @@ int hs_trim_memory(void);
  *                   8192 (512..1024; 1024)
  *   sym_heavy_from  symbolic rows with f > sym_heavy_from take the bitmap
  *                   kernel that also writes their sorted column lists
- *                   (4096..large capacity; 0 = automatic: 4096 for 4-byte
+ *                   (2048..large capacity; 0 = automatic: 4096 for 4-byte
  *                   values and bool, the large capacity for 8-byte)
  *   sort_max        numeric rows with 32 < f <= sort_max whose output count
  *   sort_pct        c is at least sort_pct percent of f sort their products

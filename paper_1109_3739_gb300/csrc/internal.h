@@ -25,7 +25,7 @@ constexpr int KEY_SORT_S = 9;   // f <= 256 (K = 8)
 constexpr int KEY_SORT_M = 10;  // f <= 512 (K = 16)
 constexpr int KEY_SORT = 11;    // f <= 1024 (K = 32)
 constexpr int KEY_SPA = 12;     // products with few columns (BinCfg::spa): f > 32, a warp's dense accumulator
-constexpr int KEY_HEAVY = 13;   // 13 + (62 - floor(log2 f)): symbolic bitmap / numeric column parts
+constexpr int KEY_HEAVY = 13;   // 13 + min(50, 62 - floor(log2 f)): symbolic bitmap / numeric column parts
 constexpr int F_TINY = 32, F_WARP_S = 128, F_WARP = 512, F_MID_S = 1024, F_MID = 4096, F_LARGE = 16384;
 constexpr int F_SORT_XS = 128, F_SORT_S = 256, F_SORT_M = 512, F_SORT = 1024;
 // Sort tiers pack (column - min column) << log2(32K) | product index into 32
@@ -56,7 +56,13 @@ __host__ __device__ inline int floor_log2_u64(uint64_t x) {
   return 63 - __builtin_clzll(x);
 #endif
 }
-__host__ __device__ inline int heavy_key(int64_t f) { return KEY_HEAVY + (62 - floor_log2_u64((uint64_t)f)); }
+// Largest rows first: one key per power of two of f down to 2^12; smaller
+// heavy rows (a bitmap threshold below 4096) share the last key, so every key
+// stays below NKEYS.
+__host__ __device__ inline int heavy_key(int64_t f) {
+  const int k = 62 - floor_log2_u64((uint64_t)f);
+  return KEY_HEAVY + (k < NKEYS - 1 - KEY_HEAVY ? k : NKEYS - 1 - KEY_HEAVY);
+}
 // Bin thresholds.  The tier capacities (table sizes) are fixed by the
 // kernels; which rows take which tier is set here, at run time (defaults
 // below, or a tuning chosen by measurement), within those capacities.
@@ -83,7 +89,7 @@ __host__ __device__ inline int sym_key(int64_t f, const BinCfg &b) {
   if (b.spa) return KEY_SPA;
   if (f <= F_WARP) return KEY_WARP;
   if (f <= b.sym_mid_s_max) return KEY_MID_S;
-  if (f <= F_MID) return KEY_MID;
+  if (f <= F_MID && f <= b.sym_heavy_from) return KEY_MID;
   if (f <= F_LARGE && f <= b.sym_heavy_from) return KEY_LARGE;
   return heavy_key(f);
 }

@@ -325,7 +325,7 @@ BinCfg bin_config(int value_bytes) {
   // them the units (R-MAT scale 20: 77.8 ms against 79.0 ms with both at the
   // large capacity); 8-byte values keep the large capacity
   const bool narrow = value_bytes <= 4;
-  b.sym_heavy_from = t.sym_heavy_from <= 0 ? (narrow ? F_MID : b.cap_large) : clampi(t.sym_heavy_from, F_MID, b.cap_large);
+  b.sym_heavy_from = t.sym_heavy_from <= 0 ? (narrow ? F_MID : b.cap_large) : clampi(t.sym_heavy_from, 2 * F_MID_S, b.cap_large);
   b.sort_max = clampi(t.sort_max, F_TINY, F_SORT);
   b.sort_pct = clampi(t.sort_pct, 0, 101);
   b.spa_max = clampi(t.spa_max, 0, SPA_COLS_4);

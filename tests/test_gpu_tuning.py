@@ -24,6 +24,7 @@ SETTINGS = [
      "sort_max": 1024, "sort_pct": 101, "num_heavy_from": 2048},
     {"sym_heavy_from": 4096, "num_heavy_from": 2048, "heavy_part_kb": 16},
     {"sym_heavy_from": 8192, "num_heavy_from": 8192},
+    {"sym_heavy_from": 2048, "num_heavy_from": 2048},  # bitmap rows below 4096 products share the last heavy key
 ]
 
 
