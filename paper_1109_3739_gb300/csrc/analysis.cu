@@ -466,38 +466,47 @@ void launch_validate(const int64_t *p, const int32_t *j, int64_t rows, int64_t n
 // span within `span` segments (a segment holds at most SEG_W <= caph
 // outputs, so every segment fits a part of its own; were one to hold more,
 // its part would carry its true count, which the numeric kernel rejects);
-// parts without outputs are dropped.  One warp walks one row's segment
-// counts, 32 at a time, the greedy state kept identical in every lane;
-// `emit(part, seg_lo, seg_hi, pc, done)` runs on lane 0 (done: the row's
-// outputs before the part).
+// parts without outputs are dropped.  One warp per row: the warp stages the
+// row's segment counts in shared memory, WP_STAGE at a time, and lane 0 walks
+// them (the greedy cut is sequential; plain shared loads keep its chain
+// short); `emit(part, seg_lo, seg_hi, pc, done)` runs on lane 0 (done: the
+// row's outputs before the part).  Every lane returns the part count.
+constexpr int WP_NT = 256;     // threads of the planning kernels
+constexpr int WP_STAGE = 256;  // segment counts staged per warp at a time
 template <class Emit>
-__device__ __forceinline__ int walk_parts(const uint32_t *hist, int nseg, int caph, int span, Emit &&emit) {
+__device__ __forceinline__ int walk_parts(const uint32_t *hist, int nseg, int caph, int span, uint32_t *stage,
+                                          Emit &&emit) {
   const int lane = lane_id();
   int start = 0, sum = 0, parts = 0;
   long long done = 0;
-  for (int g0 = 0; g0 < nseg; g0 += 32) {
-    const int v = g0 + lane < nseg ? (int)hist[g0 + lane] : 0;
-    const int lim = min(32, nseg - g0);
-    for (int j = 0; j < lim; ++j) {
-      const int x = __shfl_sync(FULL, v, j);
-      const int g = g0 + j;
-      if (g - start >= span || sum + x > caph) {
-        if (sum > 0) {
-          if (lane == 0) emit(parts, start, g, sum, done);
-          ++parts;
-          done += sum;
+  for (int g0 = 0; g0 < nseg; g0 += WP_STAGE) {
+    const int lim = min(WP_STAGE, nseg - g0);
+    __syncwarp();  // lane 0 is done with the previous counts
+    for (int j = lane; j < lim; j += 32) stage[j] = hist[g0 + j];
+    __syncwarp();
+    if (lane == 0) {
+#pragma unroll 8
+      for (int j = 0; j < lim; ++j) {
+        const int x = (int)stage[j];
+        const int g = g0 + j;
+        if (g - start >= span || sum + x > caph) {
+          if (sum > 0) {
+            emit(parts, start, g, sum, done);
+            ++parts;
+            done += sum;
+          }
+          start = g;
+          sum = 0;
         }
-        start = g;
-        sum = 0;
+        sum += x;
       }
-      sum += x;
     }
   }
-  if (sum > 0) {
-    if (lane == 0) emit(parts, start, nseg, sum, done);
+  if (lane == 0 && sum > 0) {
+    emit(parts, start, nseg, sum, done);
     ++parts;
   }
-  return parts;
+  return __shfl_sync(FULL, parts, 0);
 }
 
 __global__ void k_count_parts(RowSet A, const int *list, const int *key_off, int key_lo, const int32_t *hslot,
@@ -508,13 +517,15 @@ __global__ void k_count_parts(RowSet A, const int *list, const int *key_off, int
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int lo = key_off[key_lo];
   const int64_t count = key_off[NKEYS] - lo;
+  __shared__ uint32_t s_stage[WP_NT / 32][WP_STAGE];
+  uint32_t *stage = s_stage[threadIdx.x >> 5];
   for (int64_t w = wid; w < nmax; w += nw) {
     int64_t parts = 0, room = 0;
     if (w < count) {
       const int r = list[lo + w];
       const int h = (r >= 0 && r < A.nslots) ? hslot[r] : -1;
       if (h >= 0 && loff[r] >= 0) {
-        parts = walk_parts(hist + (int64_t)h * nseg, nseg, caph, span, [](int, int, int, int, long long) {});
+        parts = walk_parts(hist + (int64_t)h * nseg, nseg, caph, span, stage, [](int, int, int, int, long long) {});
         room = parts * (A.p[r + 1] - A.p[r]);
       }
     }
@@ -530,7 +541,7 @@ void launch_count_parts(const RowSet &A, const int *list, const int *key_off, in
                         int64_t *cnt, int64_t *cap, cudaStream_t st) {
   if (nmax <= 0) return;
   count_launch();
-  k_count_parts<<<grid_for(nmax, 8, 16), 256, 0, st>>>(A, list, key_off, key_lo, hslot, hist, loff, nseg, caph,
+  k_count_parts<<<grid_for(nmax, WP_NT / 32, 16), WP_NT, 0, st>>>(A, list, key_off, key_lo, hslot, hist, loff, nseg, caph,
                                                        span, nmax, cnt, cap);
 }
 
@@ -539,6 +550,8 @@ __global__ void k_plan_parts(RowSet A, const int *list, int count, const int32_t
                              const int64_t *off, const int64_t *poff, HeavyUnit *units) {
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  __shared__ uint32_t s_stage[WP_NT / 32][WP_STAGE];
+  uint32_t *stage = s_stage[threadIdx.x >> 5];
   for (int64_t w = wid; w < count; w += nw) {
     const int r = list[w];
     const int h = (r >= 0 && r < A.nslots) ? hslot[r] : -1;
@@ -549,7 +562,7 @@ __global__ void k_plan_parts(RowSet A, const int *list, int count, const int32_t
     const int64_t nq = A.p[r + 1] - A.p[r];
     const int64_t o = A.ids ? (int64_t)A.ids[r] : (int64_t)r;
     const int64_t cb = Cp[o], c = Cp[o + 1] - cb, lb = loff[r];
-    walk_parts(hist + (int64_t)h * nseg, nseg, caph, span, [&](int p, int s0, int s1, int pc, long long done) {
+    walk_parts(hist + (int64_t)h * nseg, nseg, caph, span, stage, [&](int p, int s0, int s1, int pc, long long done) {
       // a part must lie inside its row (else pc 0: the numeric kernel rejects the unit)
       const bool fits = HS_G(A.dbg, done + pc <= c, 74, done);
       if (base + p < end)
@@ -563,7 +576,7 @@ void launch_plan_parts(const RowSet &A, const int *list, int count, const int32_
                        const int64_t *poff, HeavyUnit *units, cudaStream_t st) {
   if (count <= 0) return;
   count_launch();
-  k_plan_parts<<<grid_for(count, 8, 16), 256, 0, st>>>(A, list, count, hslot, hist, loff, Cp, nseg, caph, span, off,
+  k_plan_parts<<<grid_for(count, WP_NT / 32, 16), WP_NT, 0, st>>>(A, list, count, hslot, hist, loff, Cp, nseg, caph, span, off,
                                                        poff, units);
 }
 
