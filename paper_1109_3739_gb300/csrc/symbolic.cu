@@ -259,19 +259,7 @@ __global__ void __launch_bounds__(SH_NT, SH_MINB) k_sym_heavy(SymArgs a) {
     for (int wd = threadIdx.x; wd < words0; wd += SH_NT) sm.bitmap[wd] = 0u;
   }
   while (true) {
-    if (threadIdx.x == 0) {
-      sm.row = atomicAdd(a.dyn, 1);
-      sm.loff = -1;
-      if (sm.row < a.count && a.glist) {
-        // room for the row's list: min(f, n) entries bound its output
-        const int r = a.list[sm.row];
-        if (r >= 0 && r < a.A.nslots) {
-          const long long need = (long long)min(a.f[r], n);
-          const unsigned long long at = atomicAdd(a.lpool, (unsigned long long)need);
-          if ((long long)at + need <= a.lcap) sm.loff = (long long)at;
-        }
-      }
-    }
+    if (threadIdx.x == 0) sm.row = atomicAdd(a.dyn, 1);
     __syncthreads();
     const int idx = sm.row;
     if (idx >= a.count) break;
@@ -281,8 +269,8 @@ __global__ void __launch_bounds__(SH_NT, SH_MINB) k_sym_heavy(SymArgs a) {
     const int r = r_ok ? r0 : 0;
     const int h = r_ok ? a.hslot[r] : -1;
     uint32_t *hist = h >= 0 ? a.hist + (int64_t)h * a.nseg : nullptr;
-    int32_t *lst = (r_ok && sm.loff >= 0) ? a.glist + sm.loff : nullptr;
-    const int64_t lmax = r_ok ? min(a.f[r], n) : 0;  // the list's room
+    int32_t *lst = nullptr;  // the row's list, once its room is taken (first chunk)
+    const int64_t lmax = r_ok ? min(a.f[r], n) : 0;  // the list's room: min(f, n) entries bound its output
     int64_t written = 0;  // columns of the earlier chunks
     for (int ch = 0; ch < (r_ok ? nchunk : 0); ++ch) {
       const int lo = ch * SH_COLS;
@@ -293,7 +281,12 @@ __global__ void __launch_bounds__(SH_NT, SH_MINB) k_sym_heavy(SymArgs a) {
                                     SymHeavyBit{sm.bitmap, lo, (unsigned)(hi - lo), a.A.dbg});
       // columns per segment, by pairs of segments (8192 columns, eight words
       // per lane; warp w takes pairs w, w + 32, ...): each lane's count and
-      // its inclusive scan over the warp are kept for the list pass
+      // its inclusive scan over the warp are kept for the list pass.  The
+      // row's list room is taken from the pool meanwhile (thread 0 issues the
+      // atomic first and reads its answer after its counts)
+      unsigned long long at_l = 0ull;
+      const bool take = threadIdx.x == 0 && ch == 0 && a.glist;
+      if (take) at_l = atomicAdd(a.lpool, (unsigned long long)lmax);
       int keep[SH_PPW];  // (inclusive scan << 16) | lane count
 #pragma unroll
       for (int i = 0; i < SH_PPW; ++i) {
@@ -312,10 +305,12 @@ __global__ void __launch_bounds__(SH_NT, SH_MINB) k_sym_heavy(SymArgs a) {
             if (g + 1 < nsc) sm.scnt[g + 1] = tot - first;
           }
           keep[i] = (incl << 16) | pcl;
-          if (!lst) sh_clear8(sm.bitmap, wb, words);  // no list pass reads them again
+          if (!a.glist) sh_clear8(sm.bitmap, wb, words);  // no list pass reads them again
         }
       }
+      if (threadIdx.x == 0 && ch == 0) sm.loff = (take && (long long)at_l + lmax <= a.lcap) ? (long long)at_l : -1;
       __syncthreads();
+      if (ch == 0 && sm.loff >= 0) lst = a.glist + sm.loff;
       // one warp: the counts out to the segment histogram, then their
       // exclusive scan (at most eight per lane), the chunk's total in the last slot
       if (warp == 0) {
@@ -338,7 +333,15 @@ __global__ void __launch_bounds__(SH_NT, SH_MINB) k_sym_heavy(SymArgs a) {
       }
       __syncthreads();
       const int ctotal = sm.scnt[SH_SEGS];
-      // list: the same pairs, read again
+      // list: the same pairs, read again (a row that found no room in the
+      // pool only clears them)
+      if (!lst && a.glist) {
+#pragma unroll
+        for (int i = 0; i < SH_PPW; ++i) {
+          const int g = 2 * (warp + nw * i);
+          if (g < nsc) sh_clear8(sm.bitmap, g * (SEG_W / 32) + 8 * lane, words);
+        }
+      }
       if (lst) {
 #pragma unroll
         for (int i = 0; i < SH_PPW; ++i) {
