@@ -672,6 +672,60 @@ def time_device(fn, steps, warmup, flush, stream):
     return statistics.median(ts), (h.launch_count() - l0) // max(1, steps), out
 
 
+def bin_rows(t, f, cnt, cap_large=8192):
+    """Masks over A's rows of every symbolic and numeric bin, as the library bins
+    a product with 4-byte values whose B is too wide for the dense accumulator:
+    the tuning values clamped as the library clamps them, then the row keys taken
+    in the library's order (f: products per row, cnt: outputs per row)."""
+    def clamp(x, lo, hi):
+        return min(max(int(x), lo), hi)
+    ws = clamp(t["warp_s_max"], 32, 128)
+    ms_ = clamp(t["mid_s_max"], 0, 1024)
+    ls = clamp(t["large_s_max"], 2048, max(cap_large // 2, 2048))
+    sms = clamp(t["sym_mid_s_max"], 512, 1024)
+    # (0: the library's automatic choice for 4-byte values)
+    shf = 4096 if t["sym_heavy_from"] <= 0 else clamp(t["sym_heavy_from"], 2048, cap_large)
+    nhf = 2048 if t.get("num_heavy_from", 0) <= 0 else clamp(t["num_heavy_from"], 2048, cap_large)
+    smax = clamp(t.get("sort_max", 1024), 32, 1024)
+    spct = clamp(t.get("sort_pct", 50), 0, 101)
+    f = np.asarray(f, dtype=np.int64)
+    cnt = np.asarray(cnt, dtype=np.int64)
+    out = {}
+
+    def take(name, cond):  # the rows still unbinned that meet cond
+        nonlocal rest
+        out[name] = rest & cond
+        rest = rest & ~cond
+
+    # symbolic, by products (the order of the library's symbolic key)
+    rest = f > 0
+    take("symbolic_tiny", f <= 32)
+    take("symbolic_warp", f <= 512)
+    take("symbolic_mid_s", f <= sms)
+    take("symbolic_mid", (f <= 4096) & (f <= shf))
+    take("symbolic_large", (f <= 16384) & (f <= shf))
+    out["symbolic_heavy"] = rest
+    # numeric, by products and outputs (the order of the numeric key)
+    rest = cnt > 0
+    take("numeric_tiny", f <= 32)
+    sort = (f <= smax) & (cnt * 100 >= f * spct)
+    take("numeric_sort_xs", sort & (f <= 128))
+    take("numeric_sort_s", sort & (f <= 256))
+    take("numeric_sort_m", sort & (f <= 512))
+    take("numeric_sort", sort)
+    take("numeric_warp_s", f <= ws)
+    take("numeric_warp", f <= 512)
+    listed = (cnt > nhf) & (f > shf)  # a sorted column list exists: the units
+    heavy = rest & listed
+    rest = rest & ~listed
+    take("numeric_mid_s", cnt <= ms_)
+    take("numeric_mid", cnt <= 2048)
+    take("numeric_large_s", cnt <= ls)
+    take("numeric_large", cnt <= cap_large)
+    out["numeric_heavy"] = heavy | rest
+    return out
+
+
 def csr_bytes(m, nnz, vb):
     return (m + 1) * 8 + nnz * (4 + vb)
 
@@ -935,34 +989,8 @@ def main():
     # offsets once
     cnt = np.diff(c_rowptr)
     deg = np.diff(A.rowptr)
-    cap_large = 8192  # f32 values
-    t = h.get_tuning()  # the thresholds in force (clamped as the library clamps them)
-    ws = min(max(t["warp_s_max"], 32), 128)
-    ms_ = min(max(t["mid_s_max"], 0), 1024)
-    ls = min(max(t["large_s_max"], 2048), cap_large // 2)
-    sms = min(max(t["sym_mid_s_max"], 512), 1024)
-    # (0: the library's automatic choice for 4-byte values)
-    shf = 4096 if t["sym_heavy_from"] <= 0 else min(max(t["sym_heavy_from"], 2048), cap_large)
-    nhf = 2048 if t.get("num_heavy_from", 0) <= 0 else min(max(t["num_heavy_from"], 2048), cap_large)
-    big = (f > 512) & (cnt > 0)
-    heavy = big & ((cnt > cap_large) | ((cnt > nhf) & (f > shf)))
-    big = big & ~heavy
-    in_bin = {
-        "numeric_heavy": heavy,
-        "numeric_large": big & (cnt > ls) & (cnt <= cap_large),
-        "numeric_large_s": big & (cnt > 2048) & (cnt <= ls),
-        "numeric_mid": big & (cnt > ms_) & (cnt <= 2048),
-        "numeric_mid_s": big & (cnt <= ms_),
-        "numeric_warp": (f > ws) & (f <= 512),
-        "numeric_warp_s": (f > 32) & (f <= ws),
-        "numeric_tiny": (f > 0) & (f <= 32),
-        "symbolic_heavy": f > shf,
-        "symbolic_large": (f > 4096) & (f <= shf),
-        "symbolic_mid": (f > sms) & (f <= min(4096, shf)),
-        "symbolic_mid_s": (f > 512) & (f <= sms),
-        "symbolic_warp": (f > 32) & (f <= 512),
-        "symbolic_tiny": (f > 0) & (f <= 32),
-    }[dom]
+    t = h.get_tuning()  # the thresholds in force
+    in_bin = bin_rows(t, f, cnt)[dom]
     vb = 4
     b_bytes = (A.m + 1) * 8 + A.nnz * (4 + vb)
     a_bytes = int(in_bin.sum()) * 8 + int(deg[in_bin].sum()) * (4 + vb)

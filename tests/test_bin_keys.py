@@ -69,3 +69,92 @@ def test_bin_keys_stay_inside_the_key_arrays(tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
     assert out.returncode == 0, out.stdout + out.stderr
     assert "bad 0 order 0 below 0" in out.stdout
+
+
+PAIRS_PROGRAM = r"""
+#include <cstdio>
+#include <cstdlib>
+#include "hspgemm.h"
+#include "internal.h"
+using namespace hs;
+// argv: warp_s_max mid_s_max large_s_max sym_mid_s_max sym_heavy_from sort_max sort_pct num_heavy_from;
+// stdin: "f c" pairs; stdout: the key constants, then "sym_key num_key" per pair
+int main(int argc, char **argv) {
+  if (argc != 9) return 2;
+  hs_tuning t;
+  hs_get_tuning(&t);
+  t.warp_s_max = atoi(argv[1]); t.mid_s_max = atoi(argv[2]); t.large_s_max = atoi(argv[3]);
+  t.sym_mid_s_max = atoi(argv[4]); t.sym_heavy_from = atoi(argv[5]); t.sort_max = atoi(argv[6]);
+  t.sort_pct = atoi(argv[7]); t.num_heavy_from = atoi(argv[8]);
+  hs_set_tuning(&t);
+  const BinCfg b = bin_config(4);
+  const BinCfg bs = product_bins(b, 1 << 20, 4), bn = numeric_bins(bs, 1 << 20);
+  printf("%d %d %d %d %d %d %d %d %d %d %d %d\n", KEY_TINY, KEY_WARP_S, KEY_WARP, KEY_MID_S, KEY_MID, KEY_LARGE_S,
+         KEY_LARGE, KEY_SORT_XS, KEY_SORT_S, KEY_SORT_M, KEY_SORT, KEY_HEAVY);
+  long long f, c;
+  while (scanf("%lld %lld", &f, &c) == 2) printf("%d %d\n", sym_key(f, bs), num_key(f, c, bn));
+  return 0;
+}
+"""
+
+SETTINGS = [
+    (128, 1024, 4096, 1024, 0, 1024, 50, 0),       # the library's defaults
+    (32, 0, 2048, 512, 2048, 256, 75, 2048),
+    (64, 768, 3072, 768, 3072, 512, 101, 4096),
+    (128, 512, 4096, 1024, 6144, 1024, 0, 8192),
+    (100000, -5, 1 << 30, 0, 1, 1 << 20, -3, 0),  # out of range: clamped
+]
+
+
+def test_bench_bins_follow_the_library(tmp_path):
+    """bench.py rebuilds in Python which rows each bin holds, to count the
+    dominant kernel's algorithmic bytes; it must bin every row as the library
+    does, for any tuning."""
+    import numpy as np
+    import bench
+    from paper_1109_3739_gb300 import build
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    lib = build.build()
+    src = tmp_path / "pairs.cu"
+    src.write_text(PAIRS_PROGRAM)
+    exe = tmp_path / "pairs"
+    libdir = os.path.dirname(lib)
+    cmd = [nvcc, "-std=c++17", "-O1", *build.ARCH, "-I", os.path.join(ROOT, "paper_1109_3739_gb300", "csrc"),
+           "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe), "-L", libdir, "-lhspgemm",
+           "-Xlinker", f"-rpath={libdir}"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+    # row sizes around every threshold, output counts from 1 to f
+    edges = [1, 32, 128, 256, 512, 768, 1024, 2048, 3072, 4096, 6144, 8192, 16384, 1 << 20]
+    fs = sorted({max(1, e + d) for e in edges for d in (-1, 0, 1)} | {5000, 20000, 100000})
+    pairs = []
+    for fv in fs:
+        for cv in sorted({1, fv // 3 + 1, fv // 2, fv // 2 + 1, fv, *[e + d for e in edges for d in (-1, 0, 1)]}):
+            if 1 <= cv <= fv:
+                pairs.append((fv, cv))
+    f = np.array([p[0] for p in pairs], dtype=np.int64)
+    c = np.array([p[1] for p in pairs], dtype=np.int64)
+    stdin = "".join(f"{a} {b}\n" for a, b in pairs)
+    names = ["warp_s_max", "mid_s_max", "large_s_max", "sym_mid_s_max", "sym_heavy_from", "sort_max", "sort_pct",
+             "num_heavy_from"]
+    for st in SETTINGS:
+        out = subprocess.run([str(exe), *map(str, st)], input=stdin, capture_output=True, text=True, timeout=120)
+        assert out.returncode == 0, out.stderr
+        lines = out.stdout.split("\n")
+        (kt, kws, kw, kms, km, kls, kl, ksx, kss, ksm, ks, kh) = map(int, lines[0].split())
+        keys = np.array([list(map(int, ln.split())) for ln in lines[1:] if ln.strip()])
+        assert len(keys) == len(pairs)
+        sym, num = keys[:, 0], keys[:, 1]
+        t = dict(zip(names, st))
+        got = bench.bin_rows(t, f, c)
+        want = {"symbolic_tiny": sym == kt, "symbolic_warp": sym == kw, "symbolic_mid_s": sym == kms,
+                "symbolic_mid": sym == km, "symbolic_large": sym == kl, "symbolic_heavy": sym >= kh,
+                "numeric_tiny": num == kt, "numeric_warp_s": num == kws, "numeric_warp": num == kw,
+                "numeric_mid_s": num == kms, "numeric_mid": num == km, "numeric_large_s": num == kls,
+                "numeric_large": num == kl, "numeric_sort_xs": num == ksx, "numeric_sort_s": num == kss,
+                "numeric_sort_m": num == ksm, "numeric_sort": num == ks, "numeric_heavy": num >= kh}
+        for name, mask in want.items():
+            bad = np.nonzero(got[name] != mask)[0]
+            assert bad.size == 0, (st, name, [pairs[i] for i in bad[:5]])
