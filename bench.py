@@ -69,23 +69,54 @@ def peaks():
 # to scale 20 by the ratio of the launch's algorithmic bytes (26.438 / 3.3377
 # GB: the rows of the numeric heavy bin, with the default routing of 4-byte
 # values); the command and counters are summarised under profiles/.  It is
-# reported only while the device sources of that kernel and of the kernels
-# that write its inputs (bins, lists, units, pairs, segment index) still hash
-# to the value they had when it was taken, and only for the part capacity it
-# was taken with; otherwise the field is null until it is measured again.
+# reported only while the device code of that kernel and of the kernels that
+# write its inputs (bins, lists, units, pairs, segment index) still hashes to
+# the value it had when it was taken (comments and blank lines do not count),
+# and only for the part capacity it was taken with; otherwise the field is
+# null until it is measured again.
 MEASURED_TRAFFIC = {"kernel": "numeric_heavy", "scale": 20, "bytes": 5.3626e9 * 26.4383 / 3.33774,
-                    "measured_at_scale": 18, "heavy_part_kb": 16, "csrc_sha256_16": "2c0047ca80d6f406"}
+                    "measured_at_scale": 18, "heavy_part_kb": 16, "csrc_code_sha256_16": "cfcf5a7f65d676f6"}
 KERNEL_SOURCES = ("analysis.cu", "common.cuh", "internal.h", "numeric.cuh", "numeric_pt.cu", "symbolic.cu")
 
 
-def csrc_hash():
+def strip_comments(text: str) -> str:
+    """C/C++ source without its comments, trailing blanks and blank lines
+    (string and character literals kept as they are)."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        ch = text[i]
+        if ch in "\"'":  # a literal: copied up to its closing quote
+            j = i + 1
+            while j < n and text[j] != ch:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(ch)
+            i += 1
+    lines = (ln.rstrip() for ln in "".join(out).split("\n"))
+    return "\n".join(ln for ln in lines if ln)
+
+
+def csrc_hash(read=None):
+    """Hash of the device code that the traffic record depends on; `read(name)`
+    gives a source's text (default: the files in the package)."""
     import hashlib
     d = os.path.join(ROOT, "paper_1109_3739_gb300", "csrc")
+    if read is None:
+        def read(fn):
+            with open(os.path.join(d, fn), encoding="utf-8") as f:
+                return f.read()
     h = hashlib.sha256()
     for fn in KERNEL_SOURCES:
         h.update(fn.encode())
-        with open(os.path.join(d, fn), "rb") as f:
-            h.update(f.read())
+        h.update(strip_comments(read(fn)).encode())
     return h.hexdigest()[:16]
 
 
@@ -1003,7 +1034,7 @@ def main():
     mt = MEASURED_TRAFFIC
     part_kb = h.get_tuning().get("heavy_part_kb", 16)  # the setting the timed steps ran with
     traffic = mt["bytes"] if (dom == mt["kernel"] and args.scale == mt["scale"] and part_kb == mt["heavy_part_kb"]
-                              and csrc_hash() == mt["csrc_sha256_16"]) else None
+                              and csrc_hash() == mt["csrc_code_sha256_16"]) else None
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
                 "alg_bytes_per_launch": alg_bytes, "ms_per_launch": dom_ms}

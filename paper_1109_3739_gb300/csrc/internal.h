@@ -72,7 +72,7 @@ struct BinCfg {
   int mid_s_max;       // numeric: rows with c <= this take the 1024-capacity CTA tier (0..1024)
   int large_s_max;     // numeric: rows with CAP_MID < c <= this take the half-capacity large tier
   int sym_mid_s_max;   // symbolic: rows with 512 < f <= this take the warp's 2048-slot tier (512..1024)
-  int sym_heavy_from;  // symbolic: rows with f > this take the bitmap kernel (4096..cap_large)
+  int sym_heavy_from;  // symbolic: rows with f > this take the bitmap kernel (2048..cap_large)
   int sort_max;        // numeric: rows with 32 < f <= this and 100*c >= sort_pct*f sort their products (32..1024)
   int sort_pct;        // (0..101; 101 switches the sort tiers off)
   int spa_max;         // products whose B has at most min(this, spa_cols()) columns take the dense tier (0: none)

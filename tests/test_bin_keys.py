@@ -158,3 +158,20 @@ def test_bench_bins_follow_the_library(tmp_path):
         for name, mask in want.items():
             bad = np.nonzero(got[name] != mask)[0]
             assert bad.size == 0, (st, name, [pairs[i] for i in bad[:5]])
+
+
+def test_code_hash_ignores_comments_only():
+    """The traffic record is tied to the device code by a hash that skips
+    comments and blank lines but not code, nor text inside literals."""
+    import bench
+    a = 'int a = 1;  // one\n\n/* two\n   lines */\nconst char *s = "// kept /* kept */";\n'
+    b = 'int a = 1;\nconst char *s = "// kept /* kept */";   \n'
+    assert bench.strip_comments(a) == bench.strip_comments(b)
+    assert bench.strip_comments('x = "a\\"//b"; // c') == 'x = "a\\"//b";'
+    assert bench.strip_comments("int a = 2;") != bench.strip_comments("int a = 1;")
+    srcs = {fn: "int k = 0;\n" for fn in bench.KERNEL_SOURCES}
+    h0 = bench.csrc_hash(srcs.__getitem__)
+    srcs[bench.KERNEL_SOURCES[0]] = "int k = 0;  // a note\n"
+    assert bench.csrc_hash(srcs.__getitem__) == h0
+    srcs[bench.KERNEL_SOURCES[0]] = "int k = 1;\n"
+    assert bench.csrc_hash(srcs.__getitem__) != h0
