@@ -158,6 +158,10 @@ def test_bench_bins_follow_the_library(tmp_path):
         for name, mask in want.items():
             bad = np.nonzero(got[name] != mask)[0]
             assert bad.size == 0, (st, name, [pairs[i] for i in bad[:5]])
+        # every row in exactly one symbolic and one numeric bin
+        for side in ("symbolic_", "numeric_"):
+            k = sum(v.astype(int) for name, v in got.items() if name.startswith(side))
+            assert (k == 1).all(), (st, side)
 
 
 def test_code_hash_ignores_comments_only():
